@@ -1,0 +1,429 @@
+"""Benchmark of the circuit-cutting hot path on one GB300 (or N replicas).
+
+One step = one pass over every stage of the path for one synthetic circuit:
+  T_pre    host preprocessing (Algorithm 1) + upload of the plan tables
+  T_sub    subcircuit simulation of all 2^{c_i} variants (Algorithm 2)
+  T_merge  full-state reconstruction of the 2^q vector (Algorithm 3)
+  T_orig   uncut simulation of the same circuit (pass planning + HBM passes)
+  verify   FP64 device reductions between the cut and uncut states
+The reported value is T_cut = T_pre + T_sub + T_merge in seconds (Eq. 3),
+the workload q = 30 random U3+CZ brickwork, depth 16, two 15-qubit segments,
+c_total = 6 cuts, complex64.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch under torch.distributed.run; each rank runs an independent
+replica (its own seed) and the slowest rank's time is reported.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "q=30 cut-sim wall s (per stage) & merge GB/s vs HBM peak; cut vs uncut, 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--q", type=int, default=30)
+    p.add_argument("--depth", type=int, default=16)
+    p.add_argument("--n", type=int, default=2)
+    p.add_argument("--ctotal", type=int, default=6)
+    p.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    p.add_argument("--decomp", choices=["projector", "s_sdg"], default="projector")
+    p.add_argument("--merge-form", default="auto", choices=["auto", "fma", "tf32x3", "bf16x3"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+def workload_config(a):
+    import workload as w
+
+    segs = w.equal_partition(a.q, a.n)
+    cpb = w.split_cuts(a.ctotal, a.n)
+    return segs, cpb, {
+        "workload": (f"random U3+CZ brickwork q={a.q} depth={a.depth}, n={a.n} equal segments "
+                     f"{'/'.join(map(str, segs))}, c_total={a.ctotal}, {a.prec}, {a.decomp} split"),
+        "q": a.q, "depth": a.depth, "n_seg": a.n, "seg_qubits": segs, "c_total": a.ctotal,
+        "cuts_per_boundary": cpb, "precision": a.prec, "decomp": a.decomp,
+        "merge_form": a.merge_form, "seed": a.seed,
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", FALLBACK_BF16_TFLOPS)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
+
+
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2603_01443_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel]
+    except Exception:
+        return None
+    try:
+        if d.get("source_hash") != kernel_source_hash(d["sources"]):
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "samples": len(mhz),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline_sample(a, steps_budget_s=20.0):
+    """Time the FP64 oracle on a bounded sample of the workload, in a fresh
+    single-threaded interpreter, and extrapolate to T_cut seconds."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+import workload as w
+from oracle import cutting as ct, statevector as sv
+q, depth, n, ctot, seed, decomp, n_sub_sample, n_amp = %d, %d, %d, %d, %d, %r, %d, %d
+segs = w.equal_partition(q, n)
+gates = w.brickwork_cut(q, depth, seed, segs, w.split_cuts(ctot, n))
+t0 = time.perf_counter(); pre = ct.preprocess(q, gates, segs, decomp); t_pre = time.perf_counter() - t0
+subs = [(i, r) for i in range(n) for r in range(len(pre.subcircuits[i]))]
+pick = subs[:: max(1, len(subs) // n_sub_sample)][:n_sub_sample]
+states = [[None] * len(pre.subcircuits[i]) for i in range(n)]
+t0 = time.perf_counter()
+for i, r in pick:
+    states[i][r] = sv.simulate_ops(segs[i], pre.subcircuits[i][r])
+t_sub_sample = time.perf_counter() - t0
+# unsampled subcircuits only feed the timing of the merge sum: any vector will do
+for i in range(n):
+    for r in range(len(states[i])):
+        if states[i][r] is None:
+            states[i][r] = sv.zero_state(segs[i])
+xs = w.sample_indices(q, n_amp, 7)
+t0 = time.perf_counter(); ct.amplitudes(pre, states, xs); t_merge_sample = time.perf_counter() - t0
+t_sub = t_sub_sample * len(subs) / len(pick)
+t_merge = t_merge_sample * (2 ** q) / n_amp
+print(json.dumps({"t_pre": t_pre, "t_sub": t_sub, "t_merge": t_merge,
+                  "sample_s": t_pre + t_sub_sample + t_merge_sample,
+                  "n_sub": len(subs), "n_sub_sample": len(pick), "n_amp": n_amp}))
+"""
+    n_sub_sample = 48
+    n_amp = 1 << 21
+    src = code % (ROOT, a.q, a.depth, a.n, a.ctotal, a.seed, a.decomp, n_sub_sample, n_amp)
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    value = d["t_pre"] + d["t_sub"] + d["t_merge"]
+    return {
+        "value": value, "unit": "s", "cores": 1, "kind": "oracle",
+        "sample": (f"Algorithm 1 in full, Algorithm 2 on {d['n_sub_sample']} of {d['n_sub']} "
+                   f"subcircuits, the Algorithm 3 sum at {d['n_amp']} of 2^{a.q} amplitudes "
+                   f"(per-amplitude form); scaled to the whole workload"),
+        "sample_seconds": d["sample_s"],
+        "stages": {"pre_s": d["t_pre"], "sub_s": d["t_sub"], "merge_s": d["t_merge"]},
+    }
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    segs, cpb, cfg = workload_config(a)
+    vals, secs = [], []
+    last = None
+    for i in range(a.warmup + a.steps):
+        r = cpu_baseline_sample(a)
+        if "error" in r:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r["error"]}))
+            return 0
+        if i >= a.warmup:
+            vals.append(r["value"])
+            secs.append(r["sample_seconds"])
+            last = r
+    value = statistics.mean(vals)
+    cpu = dict(last)
+    cpu["value"] = value
+    out = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg, "impl": "reference", "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        return reference_arm(a)
+
+    import torch
+    import torch.distributed as dist
+
+    import workload as w
+    from paper_2603_01443_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    segs, cpb, cfg = workload_config(a)
+    seed = a.seed + rank
+    gates = w.brickwork_cut(a.q, a.depth, seed, segs, cpb)
+    stream = torch.cuda.current_stream()
+
+    probe = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
+    assert probe.info["c_total"] == a.ctotal
+    seg = probe.alloc_seg_buf(dev)
+    psi = probe.alloc_psi(dev)
+    ws = probe.alloc_workspace(dev)
+    up_probe = api.UncutPlan(gates, a.q, a.prec)
+    psi_u = up_probe.alloc_psi(dev)
+    info = dict(probe.info)
+    uinfo = dict(up_probe.info)
+    probe.close()
+    up_probe.close()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    rec = {"pre": [], "sub": [], "merge": [], "orig": [], "orig_host": [], "verify": [], "cmp": []}
+
+    def step(record):
+        t0 = time.perf_counter()
+        plan = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
+        t_pre = time.perf_counter() - t0
+        ev[0].record(stream)
+        plan.simulate_segments(seg, stream)
+        ev[1].record(stream)
+        plan.merge(seg, psi, ws, a.merge_form, stream)
+        ev[2].record(stream)
+        t1 = time.perf_counter()
+        up = api.UncutPlan(gates, a.q, a.prec)
+        t_uplan = time.perf_counter() - t1
+        ev[3].record(stream)
+        up.simulate(psi_u, stream)
+        ev[4].record(stream)
+        cmp = api.compare(psi, psi_u, a.prec, stream)  # synchronizes
+        t_verify_end = time.perf_counter()
+        if record:
+            rec["pre"].append(t_pre)
+            rec["sub"].append(ev[0].elapsed_time(ev[1]) / 1e3)
+            rec["merge"].append(ev[1].elapsed_time(ev[2]) / 1e3)
+            rec["orig_host"].append(t_uplan)
+            rec["orig"].append(t_uplan + ev[3].elapsed_time(ev[4]) / 1e3)
+            rec["cmp"].append(cmp)
+        plan.close()
+        up.close()
+        return t_verify_end
+
+    for _ in range(a.warmup):
+        step(False)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    for _ in range(a.steps):
+        step(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = time.perf_counter() - t_start
+    clk = clocks.stop()
+
+    mean = {k: statistics.mean(v) for k, v in rec.items() if k != "cmp"}
+    t_cut = mean["pre"] + mean["sub"] + mean["merge"]
+    if world > 1:
+        t = torch.tensor([elapsed, t_cut], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed, t_cut = float(t[0]), float(t[1])
+
+    # e2e: host circuit in, host state out (pinned), copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        host_psi = torch.empty(psi.numel(), dtype=psi.dtype, pin_memory=True)
+        times = []
+        h2d = 0
+        for i in range(a.warmup + a.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
+            plan.simulate_segments(seg, stream)
+            plan.merge(seg, psi, ws, a.merge_form, stream)
+            host_psi.copy_(psi, non_blocking=True)
+            torch.cuda.synchronize()
+            if i >= a.warmup:
+                times.append(time.perf_counter() - t0)
+            h2d = plan.info["table_bytes"]
+            plan.close()
+        e2e_v = statistics.mean(times)
+        if world > 1:
+            t = torch.tensor([e2e_v], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_v = float(t[0])
+        e2e = {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(info["psi_bytes"])}
+        del host_psi
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    hbm, bf16, peak_src = measured_peaks()
+    amp = 8 if a.prec == "c64" else 16
+    n_amp = 1 << a.q
+    K = 1 << a.ctotal
+    # merge: the output written once plus the factors read once
+    merge_bytes = amp * n_amp + amp * sum(
+        (1 << (info["seg_cuts"][i] + info["seg_qubits"][i])) for i in range(info["n_seg"]))
+    merge_gbs = merge_bytes / mean["merge"] / 1e9
+    # uncut passes: the first only writes the vector, every later one reads and writes it
+    n_pass = uinfo["n_passes"]
+    orig_dev = mean["orig"] - mean["orig_host"]
+    pass_bytes = amp * n_amp * (2 * n_pass - 1) / n_pass
+    pass_s = orig_dev / n_pass
+    pass_gbs = pass_bytes / pass_s / 1e9
+    merge_rf = {"bound": "hbm", "achieved": merge_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": merge_gbs / hbm, "traffic": recorded_traffic("merge"),
+                "kernel": "cut_merge", "bytes_per_launch": merge_bytes,
+                "launch_s": mean["merge"], "peak_source": peak_src}
+    pass_rf = {"bound": "hbm", "achieved": pass_gbs, "peak": hbm, "unit": "GB/s",
+               "frac": pass_gbs / hbm, "traffic": recorded_traffic("uncut_pass"),
+               "kernel": "sv_pass (uncut)", "bytes_per_launch": pass_bytes,
+               "launch_s": pass_s, "peak_source": peak_src}
+    dominant = pass_rf if orig_dev > mean["merge"] else merge_rf
+    launches = sum(info["seg_passes"]) + 1 + n_pass + 2
+    cmp = rec["cmp"][-1]
+    cpu = None if a.no_cpu_baseline else cpu_baseline_sample(a)
+    out = {
+        "metric": METRIC,
+        "value": t_cut,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": 1000.0 * elapsed / a.steps,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if a.prec == "c64" else "f64",
+        "data": "synthetic",
+        "config": dict(cfg, l2=("not flushed explicitly: every step writes the 2^q uncut vector "
+                                "and reads both 2^q vectors (>> 129 MB L2) between merges")),
+        "stages": {"pre_s": mean["pre"], "sub_s": mean["sub"], "merge_s": mean["merge"],
+                   "cut_s": t_cut, "orig_s": mean["orig"], "orig_plan_s": mean["orig_host"],
+                   "delta": (t_cut - mean["orig"]) / mean["orig"]},
+        "merge_gbs": merge_gbs,
+        "gate_pass_gbs": pass_gbs,
+        "uncut_passes": n_pass,
+        "seg_passes": info["seg_passes"],
+        "merge_terms": K,
+        "threshold_n2": a.q / 2 if a.n == 2 else None,
+        "parity": {"max_abs_diff_over_max": cmp["max_abs_diff"] / cmp["max_abs_b"],
+                   "fidelity": cmp["fidelity"], "norm2_cut": cmp["norm2_a"],
+                   "norm2_uncut": cmp["norm2_b"]},
+        "roofline": dominant,
+        "rooflines": {"merge": merge_rf, "uncut_pass": pass_rf},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches * a.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * cutsim.h -- C ABI of the GB300 (sm_103a) circuit-cutting state-vector engine.
+ *
+ * The engine computes, for a circuit C on q qubits and a partition of the
+ * qubits into n contiguous segments, the full 2^q-amplitude state C|0...0>
+ * in two ways:
+ *
+ *   cut   : cc_plan_create        -- preprocessing, Algorithm 1 (T_pre)
+ *           cc_simulate_segments  -- subcircuit simulation, Algorithm 2 (T_sub)
+ *           cc_merge              -- merging, Algorithm 3 (T_merge)
+ *   uncut : cc_uncut_create + cc_simulate_uncut   -- T_orig of Eq. 3
+ *
+ * and verifies results with FP64 device reductions (cc_compare, cc_gather).
+ *
+ * Conventions (shared by every entry point)
+ *   - Amplitude index x = sum_j x_j 2^j: qubit j is bit j (little-endian).
+ *   - Segment i holds the contiguous qubits [seg_start[i], seg_start[i]+q_i),
+ *     segment 0 the lowest; all (sub)circuits start in |0...0>.
+ *   - State vectors are interleaved complex: float2 (CC_C64, 8 bytes per
+ *     amplitude) or double2 (CC_C128, 16 bytes per amplitude).
+ *   - Every device pointer must be 16-byte aligned device memory of the
+ *     current device; `stream` is a cudaStream_t (NULL = legacy default
+ *     stream) and every launch is asynchronous on it unless stated otherwise.
+ *   - The caller owns every buffer it passes.  The library owns the plan
+ *     objects, their small device tables, and a per-device scratch area for
+ *     reductions.
+ *   - Errors: every call returns a cc_status; nothing throws across the ABI.
+ *     Arguments are validated before any launch.  cc_last_error() returns a
+ *     thread-local message describing the last failure on the calling thread.
+ *
+ * Only sm_103 devices are accepted (CC_EDEVICE otherwise): the kernels are
+ * compiled for sm_103a alone.
+ */
+#ifndef CUTSIM_H
+#define CUTSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_MAX_QUBITS 34   /* 2^34 complex64 = 128 GiB */
+#define CC_MAX_SEGMENTS 8
+#define CC_MAX_CUTS 24     /* c_total <= 24, at most 2^24 merge terms */
+
+typedef enum {
+  CC_OK = 0,
+  CC_EINVAL = 1,        /* malformed argument: NULL pointer, unknown enum, qubit out of range, q0 == q1 */
+  CC_ERANGE = 2,        /* size beyond the supported range (q, segment count, c_total, index) */
+  CC_EUNSUPPORTED = 3,  /* the cutter cannot decompose the circuit (see cc_plan_create) */
+  CC_ENOMEM = 4,        /* host or device allocation of library-owned tables failed */
+  CC_EBUFSIZE = 5,      /* a caller buffer is smaller than required */
+  CC_ECUDA = 6,         /* a CUDA runtime call or launch failed (see cc_last_error) */
+  CC_ETIMEOUT = 7,      /* a bounded device-side wait gave up; outputs are undefined */
+  CC_EDEVICE = 8        /* the current device is not an sm_103 GPU */
+} cc_status;
+
+typedef enum { CC_C64 = 0, CC_C128 = 1 } cc_precision;
+
+/* Rank-2 decompositions of a cut CZ (Eq. 1 with k = 2).
+ * CC_DECOMP_PROJECTOR: CZ = |0><0| (x) I + |1><1| (x) Z, coefficients 1 and 1.
+ * CC_DECOMP_S_SDG    : Eq. 2, CZ = [S (x) S + i S^dag (x) S^dag] / (1 + i).
+ * A boundary CX is first rewritten as (I (x) H) CZ (I (x) H) (Sec. II.A.2). */
+typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
+
+/* Merge arithmetic (cc_merge).
+ * CC_MERGE_FMA     : complex FMA on CUDA cores in the plan's precision.
+ * CC_MERGE_TF32X3  : tcgen05 tensor cores, kind::tf32, each operand split
+ *                    x = hi + lo and hi*hi + hi*lo + lo*hi accumulated in FP32
+ *                    (CC_C64 plans only).
+ * CC_MERGE_BF16X3  : tcgen05 tensor cores, kind::f16 with bf16 operands, the
+ *                    same three-product split, FP32 accumulation (CC_C64 only).
+ * CC_MERGE_AUTO    : FMA when the merge is bandwidth-bound (few terms) or the
+ *                    plan is CC_C128, else TF32X3. */
+typedef enum {
+  CC_MERGE_AUTO = 0,
+  CC_MERGE_FMA = 1,
+  CC_MERGE_TF32X3 = 2,
+  CC_MERGE_BF16X3 = 3
+} cc_merge_form;
+
+typedef enum {
+  CC_GATE_U3 = 0,  /* U3(theta,phi,lambda) = [[c, -e^{i l} s], [e^{i p} s, e^{i(p+l)} c]], c=cos(theta/2), s=sin(theta/2) */
+  CC_GATE_H = 1,
+  CC_GATE_X = 2,
+  CC_GATE_Z = 3,
+  CC_GATE_S = 4,   /* diag(1, i) */
+  CC_GATE_SDG = 5, /* diag(1, -i) */
+  CC_GATE_T = 6,   /* diag(1, e^{i pi/4}) */
+  CC_GATE_TDG = 7, /* diag(1, e^{-i pi/4}) */
+  CC_GATE_CZ = 8,  /* diag(1, 1, 1, -1) on (q0, q1) */
+  CC_GATE_CX = 9   /* control q0, target q1 */
+} cc_gate_kind;
+
+/* One gate.  q1 = -1 for one-qubit gates; theta, phi, lambda are read for U3
+ * only.  40 bytes, natural alignment. */
+typedef struct {
+  int32_t kind;
+  int32_t q0;
+  int32_t q1;
+  int32_t reserved;  /* must be 0 */
+  double theta, phi, lambda;
+} cc_gate;
+
+typedef struct cc_plan cc_plan;    /* opaque, library-owned */
+typedef struct cc_uncut cc_uncut;  /* opaque, library-owned */
+
+typedef struct {
+  int32_t q, n_seg, c_total, precision, decomp;
+  int32_t seg_qubits[CC_MAX_SEGMENTS];  /* q_i */
+  int32_t seg_start[CC_MAX_SEGMENTS];   /* first qubit of segment i */
+  int32_t seg_cuts[CC_MAX_SEGMENTS];    /* c_i: cuts adjacent to segment i */
+  int32_t seg_passes[CC_MAX_SEGMENTS];  /* gate passes of segment i's program */
+  int32_t seg_ops[CC_MAX_SEGMENTS];     /* fused gate operations of segment i */
+  int64_t seg_offset[CC_MAX_SEGMENTS];  /* amplitude offset of segment i in seg_buf */
+  int64_t n_sub;                        /* N_sub = sum_i 2^{c_i} */
+  uint64_t seg_buf_bytes;               /* bytes of seg_buf: sum_i 2^{c_i} 2^{q_i} amplitudes */
+  uint64_t psi_bytes;                   /* bytes of the 2^q output */
+  uint64_t workspace_bytes;             /* device workspace cc_merge needs (any form) */
+  uint64_t table_bytes;                 /* device bytes of the plan's own tables */
+} cc_plan_info_t;
+
+/* cc_plan_create -- preprocessing, Algorithm 1 (T_pre).
+ *   gates[n_gates]  host array, read during the call only.
+ *   q               1..CC_MAX_QUBITS.
+ *   seg_sizes[n_seg] host array, positive, summing to q; n_seg in 1..CC_MAX_SEGMENTS.
+ *   decomp          cc_decomp;  precision  cc_precision.
+ *   out             receives a plan the caller frees with cc_plan_destroy.
+ * Every two-qubit gate whose qubits lie in different segments becomes cut j
+ * (j in circuit order).  Segment i gets one shared gate program whose 2^{c_i}
+ * variants differ only in the diagonal local term selected by the variant's
+ * bit for each adjacent cut; the coefficient of cut j is folded into the term
+ * on the segment of the gate's first qubit, so merging needs no alpha_m.
+ * The plan's tables are uploaded to the current device (synchronously).
+ * Errors: CC_EINVAL (NULL, bad enum, bad qubit, sizes not summing to q),
+ * CC_ERANGE (q, n_seg or c_total too large, a segment too large to simulate),
+ * CC_EUNSUPPORTED (for n_seg >= 3, a cut between non-adjacent segments),
+ * CC_ENOMEM, CC_ECUDA, CC_EDEVICE. */
+cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32_t q,
+                         const int32_t* seg_sizes, int32_t n_seg, int32_t decomp,
+                         int32_t precision, cc_plan** out);
+
+/* cc_plan_info -- sizes and counts of a plan (host only, no device work). */
+cc_status cc_plan_info(const cc_plan* plan, cc_plan_info_t* info);
+
+/* cc_plan_cut -- the j-th cut: its two qubits (first, second as in the gate),
+ * its kind (CC_GATE_CZ or CC_GATE_CX) and the two segments. */
+cc_status cc_plan_cut(const cc_plan* plan, int32_t j, int32_t* q0, int32_t* q1,
+                      int32_t* kind, int32_t* seg0, int32_t* seg1);
+
+void cc_plan_destroy(cc_plan* plan);
+
+/* cc_simulate_segments -- subcircuit simulation, Algorithm 2 (T_sub).
+ * Writes |psi_i^(r)> = S_i^(r)|0> for every segment i and variant r into
+ * seg_buf: segment i occupies amplitudes [seg_offset[i], seg_offset[i] +
+ * 2^{c_i} 2^{q_i}), variant r at seg_offset[i] + r 2^{q_i}.  Bit t of r
+ * selects the term of the t-th cut adjacent to segment i (circuit order).
+ * seg_buf_bytes must be >= info.seg_buf_bytes (else CC_EBUFSIZE).
+ * Asynchronous on `stream`. */
+cc_status cc_simulate_segments(const cc_plan* plan, void* seg_buf, uint64_t seg_buf_bytes,
+                               void* stream);
+
+/* cc_merge -- merging, Algorithm 3 (T_merge).
+ * psi[x] = sum_m prod_i psi_i^(r_i(m))[x restricted to segment i] over all
+ * 2^{c_total} global cut combinations m (bit j of m = term of cut j).
+ * n_seg = 2 is one pass over psi; n_seg >= 3 absorbs one segment at a time
+ * through `workspace` (>= info.workspace_bytes, may be NULL when that is 0);
+ * the tensor-core forms also stage their split operands there.
+ * seg_buf is read only; psi (>= info.psi_bytes) is fully overwritten.
+ * Errors: CC_EBUFSIZE, CC_EINVAL (form not available for the precision).
+ * Asynchronous on `stream`. */
+cc_status cc_merge(const cc_plan* plan, const void* seg_buf, uint64_t seg_buf_bytes,
+                   void* psi, uint64_t psi_bytes, void* workspace, uint64_t workspace_bytes,
+                   int32_t form, void* stream);
+
+/* cc_uncut_create -- pass planning for the uncut simulation of C (host work,
+ * tables uploaded synchronously).  Same gate rules as cc_plan_create. */
+cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int32_t q, int32_t precision,
+                          cc_uncut** out);
+
+/* cc_uncut_info -- number of gate passes over the 2^q vector and of fused ops. */
+cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops, int32_t* tile_bits);
+
+/* cc_simulate_uncut -- psi = C|0...0> over the full 2^q vector (T_orig).
+ * psi_bytes >= 2^q * amplitude size.  Asynchronous on `stream`. */
+cc_status cc_simulate_uncut(const cc_uncut* u, void* psi, uint64_t psi_bytes, void* stream);
+
+void cc_uncut_destroy(cc_uncut* u);
+
+/* cc_compare -- FP64 verification reductions over two device vectors of
+ * n_amp amplitudes in `precision`:
+ *   out[0] = max_x |a[x] - b[x]|     out[1] = max_x |b[x]|
+ *   out[2] = Re <a|b>                out[3] = Im <a|b>
+ *   out[4] = <a|a>                   out[5] = <b|b>
+ * `out` is host memory.  Uses the library's per-device scratch area and
+ * synchronizes `stream` before returning. */
+cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precision,
+                     double* out, void* stream);
+
+/* cc_gather -- out[i] = psi[idx[i]] for i < n_idx (the sampled-amplitude
+ * check).  idx (int64) and out (n_idx amplitudes of `precision`) are HOST
+ * memory; every index must lie in [0, n_amp) (else CC_ERANGE before any
+ * launch).  n_idx <= 1<<20.  Synchronizes `stream`. */
+cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision, const int64_t* idx,
+                    int64_t n_idx, void* out, void* stream);
+
+/* cc_last_error -- thread-local message of the last failure (never NULL). */
+const char* cc_last_error(void);
+
+/* cc_version -- library version string. */
+const char* cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUTSIM_H */

@@ -1,0 +1,194 @@
+"""Python face of the C ABI: plans, device buffers (torch) and streams.
+
+Nothing here computes: every step of the path is a call into
+``libcutsim.so``.  Torch only allocates device memory and provides the stream
+handle passed to each call.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int32, c_int64, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import capi
+
+TORCH_DTYPE = {"c64": torch.complex64, "c128": torch.complex128}
+NUMPY_DTYPE = {"c64": np.complex64, "c128": np.complex128}
+AMP_BYTES = {"c64": 8, "c128": 16}
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _nbytes(t: Optional[torch.Tensor]) -> int:
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+class CutPlan:
+    """Preprocessing (Algorithm 1) of one circuit and partition."""
+
+    def __init__(self, gates: Sequence, q: int, seg_sizes: Sequence[int],
+                 decomp: str = "projector", precision: str = "c64"):
+        L = capi.lib()
+        self.q = q
+        self.precision = precision
+        self.decomp = decomp
+        arr = capi.gate_array(gates)
+        sizes = (c_int32 * len(seg_sizes))(*seg_sizes)
+        h = c_void_p()
+        capi.check(L.cc_plan_create(arr, len(gates), q, sizes, len(seg_sizes),
+                                    capi.DECOMP[decomp], capi.PRECISION[precision], byref(h)),
+                   "cc_plan_create")
+        self._h = h
+        info = capi.CPlanInfo()
+        capi.check(L.cc_plan_info(self._h, byref(info)), "cc_plan_info")
+        n = info.n_seg
+        self.info = {
+            "q": info.q, "n_seg": n, "c_total": info.c_total,
+            "seg_qubits": list(info.seg_qubits[:n]), "seg_start": list(info.seg_start[:n]),
+            "seg_cuts": list(info.seg_cuts[:n]), "seg_passes": list(info.seg_passes[:n]),
+            "seg_ops": list(info.seg_ops[:n]), "seg_offset": list(info.seg_offset[:n]),
+            "n_sub": info.n_sub, "seg_buf_bytes": info.seg_buf_bytes,
+            "psi_bytes": info.psi_bytes, "workspace_bytes": info.workspace_bytes,
+            "table_bytes": info.table_bytes,
+        }
+
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.lib().cc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cut(self, j: int):
+        vals = [c_int32() for _ in range(5)]
+        capi.check(capi.lib().cc_plan_cut(self._h, j, *[byref(v) for v in vals]), "cc_plan_cut")
+        q0, q1, kind, s0, s1 = (v.value for v in vals)
+        return {"q0": q0, "q1": q1, "kind": kind, "seg0": s0, "seg1": s1}
+
+    # buffers ------------------------------------------------------------
+    def _alloc(self, nbytes: int, device) -> torch.Tensor:
+        n = max(1, nbytes // AMP_BYTES[self.precision])
+        return torch.empty(n, dtype=TORCH_DTYPE[self.precision], device=device)
+
+    def alloc_seg_buf(self, device="cuda"):
+        return self._alloc(self.info["seg_buf_bytes"], device)
+
+    def alloc_psi(self, device="cuda"):
+        return self._alloc(self.info["psi_bytes"], device)
+
+    def alloc_workspace(self, device="cuda"):
+        if self.info["workspace_bytes"] == 0:
+            return None
+        return self._alloc(self.info["workspace_bytes"], device)
+
+    def segment_view(self, seg_buf: torch.Tensor, i: int) -> torch.Tensor:
+        """Segment i's variants as a [2^{c_i}, 2^{q_i}] view of seg_buf."""
+        off = self.info["seg_offset"][i]
+        nv, na = 1 << self.info["seg_cuts"][i], 1 << self.info["seg_qubits"][i]
+        return seg_buf[off:off + nv * na].view(nv, na)
+
+    # stages -------------------------------------------------------------
+    def simulate_segments(self, seg_buf: torch.Tensor, stream=None) -> None:
+        capi.check(capi.lib().cc_simulate_segments(self._h, _ptr(seg_buf), _nbytes(seg_buf),
+                                                   _stream(stream)), "cc_simulate_segments")
+
+    def merge(self, seg_buf: torch.Tensor, psi: torch.Tensor, workspace=None, form="auto",
+              stream=None) -> None:
+        capi.check(capi.lib().cc_merge(self._h, _ptr(seg_buf), _nbytes(seg_buf), _ptr(psi),
+                                       _nbytes(psi), _ptr(workspace), _nbytes(workspace),
+                                       capi.MERGE_FORM[form], _stream(stream)), "cc_merge")
+
+
+class UncutPlan:
+    """Pass plan of the uncut simulation (T_orig)."""
+
+    def __init__(self, gates: Sequence, q: int, precision: str = "c64"):
+        L = capi.lib()
+        self.q = q
+        self.precision = precision
+        arr = capi.gate_array(gates)
+        h = c_void_p()
+        capi.check(L.cc_uncut_create(arr, len(gates), q, capi.PRECISION[precision], byref(h)),
+                   "cc_uncut_create")
+        self._h = h
+        npass, nops, tb = c_int32(), c_int32(), c_int32()
+        capi.check(L.cc_uncut_info(self._h, byref(npass), byref(nops), byref(tb)), "cc_uncut_info")
+        self.info = {"n_passes": npass.value, "n_ops": nops.value, "tile_bits": tb.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.lib().cc_uncut_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_psi(self, device="cuda"):
+        return torch.empty(1 << self.q, dtype=TORCH_DTYPE[self.precision], device=device)
+
+    def simulate(self, psi: torch.Tensor, stream=None) -> None:
+        capi.check(capi.lib().cc_simulate_uncut(self._h, _ptr(psi), _nbytes(psi), _stream(stream)),
+                   "cc_simulate_uncut")
+
+
+def compare(a: torch.Tensor, b: torch.Tensor, precision: str, stream=None) -> dict:
+    """FP64 device reductions between two state vectors (synchronizes)."""
+    if a.numel() != b.numel():
+        raise ValueError("size mismatch")
+    out = (c_double * 6)()
+    capi.check(capi.lib().cc_compare(_ptr(a), _ptr(b), a.numel(), capi.PRECISION[precision], out,
+                                     _stream(stream)), "cc_compare")
+    re, im, na, nb = out[2], out[3], out[4], out[5]
+    return {
+        "max_abs_diff": out[0], "max_abs_b": out[1], "inner_re": re, "inner_im": im,
+        "norm2_a": na, "norm2_b": nb,
+        "fidelity": (re * re + im * im) / (na * nb) if na > 0 and nb > 0 else 0.0,
+    }
+
+
+def gather(psi: torch.Tensor, idx: Sequence[int], precision: str, stream=None) -> np.ndarray:
+    """psi[idx] copied to the host (synchronizes)."""
+    idx_arr = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.empty(len(idx_arr), dtype=NUMPY_DTYPE[precision])
+    capi.check(capi.lib().cc_gather(
+        _ptr(psi), psi.numel(), capi.PRECISION[precision],
+        idx_arr.ctypes.data_as(ctypes.POINTER(c_int64)), len(idx_arr),
+        out.ctypes.data_as(c_void_p), _stream(stream)), "cc_gather")
+    return out
+
+
+def cut_simulate(gates, q, seg_sizes, decomp="projector", precision="c64", form="auto",
+                 stream=None):
+    """Preprocess, simulate segments and merge; returns (psi on the device, plan)."""
+    plan = CutPlan(gates, q, seg_sizes, decomp, precision)
+    seg = plan.alloc_seg_buf()
+    psi = plan.alloc_psi()
+    ws = plan.alloc_workspace()
+    plan.simulate_segments(seg, stream)
+    plan.merge(seg, psi, ws, form, stream)
+    return psi, plan

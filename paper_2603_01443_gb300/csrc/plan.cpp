@@ -1,0 +1,335 @@
+// Preprocessing (Algorithm 1) and the host side of the C ABI.
+//
+// Algorithm 1 builds one subcircuit per segment and per bit string b of the
+// segment's adjacent cuts.  With either rank-2 CZ split the local terms are
+// diagonal (projectors / Z^b, or S / S^dag), and a cut CX only adds shared
+// Hadamards on its target (CX = (I (x) H) CZ (I (x) H)).  All 2^{c_i} variants
+// of segment i therefore share every non-diagonal gate, and the plan keeps a
+// single gate program per segment in which each cut term is a diagonal factor
+// selected by one bit of the variant number.  The cut's coefficient (1 for
+// the projector split, 1/(1+i) and i/(1+i) for Eq. 2) is folded into the term
+// on the segment of the gate's first qubit, so the merge sums plain products
+// (alpha_m = prod_j coef_j[m_j] is carried by the first factor).
+//
+// The merge index table M of Algorithm 1 is bit slicing: segment i's variant
+// number is r_i(m) = sum_t bit(m, j_t) 2^t over its adjacent cuts j_0 < j_1 <
+// ... .  For n >= 3 segments on a line, the merge absorbs one segment at a
+// time (see merge stages below), which needs every cut between neighbouring
+// segments.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "plan.h"
+
+using namespace cc;
+
+namespace {
+
+int amp_bytes(int precision) { return precision == CC_C128 ? 16 : 8; }
+
+int seg_of_qubit(const cc_plan* p, int qb) {
+  for (int i = 0; i < p->n_seg; ++i)
+    if (qb >= p->seg_start[i] && qb < p->seg_start[i] + p->seg_q[i]) return i;
+  return -1;
+}
+
+// Local term of cut j on one side, as a variant-selected diagonal factor.
+Item cut_item(int decomp, bool first_side, int local_qubit, int slot) {
+  Item it;
+  it.kind = IT_VAR;
+  it.a = local_qubit;
+  it.slot = slot;
+  const cd I(0.0, 1.0);
+  if (decomp == CC_DECOMP_PROJECTOR) {
+    if (first_side) {  // |b><b|, coefficient 1
+      it.d[0][0] = 1.0; it.d[0][1] = 0.0;
+      it.d[1][0] = 0.0; it.d[1][1] = 1.0;
+    } else {           // Z^b
+      it.var_sign = true;
+    }
+  } else {             // Eq. 2: S for b = 0, S^dag for b = 1
+    cd coef[2] = {1.0, 1.0};
+    if (first_side) {
+      coef[0] = 1.0 / (1.0 + I);
+      coef[1] = I / (1.0 + I);
+    }
+    it.d[0][0] = coef[0]; it.d[0][1] = coef[0] * I;
+    it.d[1][0] = coef[1]; it.d[1][1] = -coef[1] * I;
+  }
+  return it;
+}
+
+Item hadamard(int a) {
+  Item h;
+  h.kind = IT_DENSE;
+  h.a = a;
+  const double r = 1.0 / std::sqrt(2.0);
+  h.u[0] = r; h.u[1] = r; h.u[2] = r; h.u[3] = -r;
+  return h;
+}
+
+}  // namespace
+
+cc_plan::~cc_plan() {
+  for (auto& d : dprog) free_program(d);
+  if (tables_dev) device_free(tables_dev);
+}
+
+extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32_t q,
+                                    const int32_t* seg_sizes, int32_t n_seg, int32_t decomp,
+                                    int32_t precision, cc_plan** out) {
+  try {
+    if (!out) return fail(CC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (q < 1 || q > CC_MAX_QUBITS) return fail(CC_ERANGE, "q must be in 1..34");
+    if (n_seg < 1 || n_seg > CC_MAX_SEGMENTS) return fail(CC_ERANGE, "n_seg must be in 1..8");
+    if (!seg_sizes) return fail(CC_EINVAL, "seg_sizes is NULL");
+    if (decomp != CC_DECOMP_PROJECTOR && decomp != CC_DECOMP_S_SDG)
+      return fail(CC_EINVAL, "unknown decomposition");
+    if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+    int sum = 0;
+    for (int i = 0; i < n_seg; ++i) {
+      if (seg_sizes[i] < 1) return fail(CC_EINVAL, "segment sizes must be positive");
+      sum += seg_sizes[i];
+    }
+    if (sum != q) return fail(CC_EINVAL, "segment sizes do not sum to q");
+    cc_status st = check_gates(gates, n_gates, q);
+    if (st != CC_OK) return st;
+
+    std::unique_ptr<cc_plan> p(new cc_plan());
+    p->q = q;
+    p->n_seg = n_seg;
+    p->precision = precision;
+    p->decomp = decomp;
+    int acc = 0;
+    for (int i = 0; i < n_seg; ++i) {
+      p->seg_q.push_back(seg_sizes[i]);
+      p->seg_start.push_back(acc);
+      acc += seg_sizes[i];
+    }
+
+    // Scan the circuit for boundary gates (cut j in circuit order).
+    std::vector<std::vector<Item>> items(n_seg);
+    p->seg_cut_ids.assign(n_seg, {});
+    for (int g = 0; g < n_gates; ++g) {
+      const cc_gate& gt = gates[g];
+      const bool two = gt.kind == CC_GATE_CZ || gt.kind == CC_GATE_CX;
+      const int s0 = seg_of_qubit(p.get(), gt.q0);
+      const int s1 = two ? seg_of_qubit(p.get(), gt.q1) : s0;
+      if (s0 == s1) {
+        st = gate_items(gt, p->seg_start[s0], items[s0]);
+        if (st != CC_OK) return st;
+        continue;
+      }
+      if ((int)p->cuts.size() >= CC_MAX_CUTS)
+        return fail(CC_ERANGE, "more than 24 cut gates");
+      if (n_seg >= 3 && std::abs(s0 - s1) != 1)
+        return fail(CC_EUNSUPPORTED, "gate " + std::to_string(g) +
+                                         " crosses non-adjacent segments; the chained merge needs "
+                                         "every cut between neighbouring segments");
+      const int j = (int)p->cuts.size();
+      p->cuts.push_back({gt.q0, gt.q1, gt.kind, s0, s1});
+      const int slot0 = (int)p->seg_cut_ids[s0].size();
+      const int slot1 = (int)p->seg_cut_ids[s1].size();
+      p->seg_cut_ids[s0].push_back(j);
+      p->seg_cut_ids[s1].push_back(j);
+      const int l0 = gt.q0 - p->seg_start[s0], l1 = gt.q1 - p->seg_start[s1];
+      items[s0].push_back(cut_item(decomp, true, l0, slot0));
+      if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
+      items[s1].push_back(cut_item(decomp, false, l1, slot1));
+      if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
+    }
+    p->c_total = (int)p->cuts.size();
+
+    const int ab = amp_bytes(precision);
+    int64_t off = 0;
+    p->n_sub = 0;
+    for (int i = 0; i < n_seg; ++i) {
+      const int ci = (int)p->seg_cut_ids[i].size();
+      p->seg_c.push_back(ci);
+      if (p->seg_q[i] + ci > CC_MAX_QUBITS)
+        return fail(CC_ERANGE, "segment " + std::to_string(i) + " needs 2^" +
+                                   std::to_string(p->seg_q[i] + ci) + " amplitudes");
+      p->seg_off.push_back(off);
+      off += int64_t(1) << (p->seg_q[i] + ci);
+      p->n_sub += int64_t(1) << ci;
+    }
+    p->seg_buf_bytes = (uint64_t)off * ab;
+    p->psi_bytes = (uint64_t(1) << q) * ab;
+
+    // One shared program per segment.
+    for (int i = 0; i < n_seg; ++i) {
+      HostProgram hp = compile_program(items[i], p->seg_q[i], p->seg_c[i],
+                                       max_tile_bits(precision), low_tile_bits(precision));
+      if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
+      p->hprog.push_back(std::move(hp));
+    }
+    // Everything above is host work; the device is needed from here on.
+    st = check_device();
+    if (st != CC_OK) return st;
+    for (int i = 0; i < n_seg; ++i) {
+      DeviceProgram dp;
+      st = upload_program(p->hprog[i], precision, dp);
+      if (st != CC_OK) return st;
+      p->dprog.push_back(dp);
+    }
+
+    // Merge stages: stage s absorbs segment s into the product of segments < s.
+    //   U_s[z][x_s * N_{<s} + x_{<s}] = sum_k U_{s-1}[k][x_{<s}] * seg_s[r_s(k, z)][x_s]
+    // k runs over the cut bits of boundary (s-1, s), z over those of (s, s+1).
+    std::vector<int32_t> tab;
+    if (n_seg >= 2) {
+      std::vector<std::vector<int>> bcuts(n_seg - 1);
+      for (int j = 0; j < p->c_total; ++j)
+        bcuts[std::min(p->cuts[j].s0, p->cuts[j].s1)].push_back(j);
+      int qa = p->seg_q[0];
+      uint64_t u_max = 0;
+      for (int s = 1; s < n_seg; ++s) {
+        cc_plan::Stage sg;
+        sg.seg = s;
+        sg.qa = qa;
+        sg.qb = p->seg_q[s];
+        const std::vector<int>& kc = bcuts[s - 1];
+        const std::vector<int> none;
+        const std::vector<int>& zc = (s + 1 < n_seg) ? bcuts[s] : none;
+        sg.K = int64_t(1) << kc.size();
+        sg.Z = int64_t(1) << zc.size();
+        sg.aidx_off = (int64_t)tab.size();
+        for (int64_t z = 0; z < sg.Z; ++z)
+          for (int64_t k = 0; k < sg.K; ++k) {
+            int32_t ra = (int32_t)k;
+            if (s == 1) {  // r_0 from the global combination
+              uint64_t m = 0;
+              for (size_t t = 0; t < kc.size(); ++t) m |= uint64_t((k >> t) & 1) << kc[t];
+              ra = 0;
+              for (size_t t = 0; t < p->seg_cut_ids[0].size(); ++t)
+                ra |= int32_t((m >> p->seg_cut_ids[0][t]) & 1) << t;
+            }
+            tab.push_back(ra);
+          }
+        sg.bidx_off = (int64_t)tab.size();
+        for (int64_t z = 0; z < sg.Z; ++z)
+          for (int64_t k = 0; k < sg.K; ++k) {
+            uint64_t m = 0;
+            for (size_t t = 0; t < kc.size(); ++t) m |= uint64_t((k >> t) & 1) << kc[t];
+            for (size_t t = 0; t < zc.size(); ++t) m |= uint64_t((z >> t) & 1) << zc[t];
+            int32_t rb = 0;
+            for (size_t t = 0; t < p->seg_cut_ids[s].size(); ++t)
+              rb |= int32_t((m >> p->seg_cut_ids[s][t]) & 1) << t;
+            tab.push_back(rb);
+          }
+        if (s + 1 < n_seg) u_max = std::max(u_max, (uint64_t)sg.Z << (qa + sg.qb));
+        qa += sg.qb;
+        p->stages.push_back(sg);
+      }
+      p->chain_ws_amps = u_max;
+      p->workspace_bytes = 2 * u_max * ab;
+      if (n_seg == 2) {
+        const auto& sg = p->stages[0];
+        uint64_t w = std::max(merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_TF32X3),
+                              merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_BF16X3));
+        p->workspace_bytes = std::max(p->workspace_bytes, w);
+      }
+    }
+    if (!tab.empty()) {
+      p->tables_dev = device_alloc_copy(tab.data(), tab.size() * sizeof(int32_t));
+      if (!p->tables_dev) return fail(CC_ENOMEM, "device allocation of merge tables failed");
+      p->table_bytes += tab.size() * sizeof(int32_t);
+    }
+    for (auto& d : p->dprog) p->table_bytes += d.bytes;
+    *out = p.release();
+    return CC_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(CC_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CC_EINVAL, "internal error in cc_plan_create");
+  }
+}
+
+extern "C" cc_status cc_plan_info(const cc_plan* p, cc_plan_info_t* info) {
+  if (!p || !info) return fail(CC_EINVAL, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->q = p->q;
+  info->n_seg = p->n_seg;
+  info->c_total = p->c_total;
+  info->precision = p->precision;
+  info->decomp = p->decomp;
+  for (int i = 0; i < p->n_seg; ++i) {
+    info->seg_qubits[i] = p->seg_q[i];
+    info->seg_start[i] = p->seg_start[i];
+    info->seg_cuts[i] = p->seg_c[i];
+    info->seg_offset[i] = p->seg_off[i];
+    info->seg_passes[i] = (int32_t)p->hprog[i].passes.size();
+    info->seg_ops[i] = (int32_t)p->hprog[i].ops.size();
+  }
+  info->n_sub = p->n_sub;
+  info->seg_buf_bytes = p->seg_buf_bytes;
+  info->psi_bytes = p->psi_bytes;
+  info->workspace_bytes = p->workspace_bytes;
+  info->table_bytes = p->table_bytes;
+  return CC_OK;
+}
+
+extern "C" cc_status cc_plan_cut(const cc_plan* p, int32_t j, int32_t* q0, int32_t* q1,
+                                 int32_t* kind, int32_t* seg0, int32_t* seg1) {
+  if (!p) return fail(CC_EINVAL, "plan is NULL");
+  if (j < 0 || j >= p->c_total) return fail(CC_ERANGE, "cut index out of range");
+  const auto& c = p->cuts[j];
+  if (q0) *q0 = c.q0;
+  if (q1) *q1 = c.q1;
+  if (kind) *kind = c.kind;
+  if (seg0) *seg0 = c.s0;
+  if (seg1) *seg1 = c.s1;
+  return CC_OK;
+}
+
+extern "C" void cc_plan_destroy(cc_plan* p) { delete p; }
+
+// ------------------------------------------------------------------ uncut
+cc_uncut::~cc_uncut() { free_program(dprog); }
+
+extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int32_t q,
+                                     int32_t precision, cc_uncut** out) {
+  try {
+    if (!out) return fail(CC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (q < 1 || q > CC_MAX_QUBITS) return fail(CC_ERANGE, "q must be in 1..34");
+    if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+    cc_status st = check_gates(gates, n_gates, q);
+    if (st != CC_OK) return st;
+    std::unique_ptr<cc_uncut> u(new cc_uncut());
+    u->q = q;
+    u->precision = precision;
+    std::vector<Item> items;
+    for (int g = 0; g < n_gates; ++g) {
+      st = gate_items(gates[g], 0, items);
+      if (st != CC_OK) return st;
+    }
+    u->hprog = compile_program(items, q, 0, uncut_tile_bits(precision), low_tile_bits(precision));
+    if (u->hprog.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
+    st = check_device();
+    if (st != CC_OK) return st;
+    st = upload_program(u->hprog, precision, u->dprog);
+    if (st != CC_OK) return st;
+    *out = u.release();
+    return CC_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(CC_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CC_EINVAL, "internal error in cc_uncut_create");
+  }
+}
+
+extern "C" cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops,
+                                   int32_t* tile_bits) {
+  if (!u) return fail(CC_EINVAL, "NULL argument");
+  if (n_passes) *n_passes = (int32_t)u->hprog.passes.size();
+  if (n_ops) *n_ops = (int32_t)u->hprog.ops.size();
+  if (tile_bits) *tile_bits = u->hprog.passes.empty() ? 0 : u->hprog.passes[0].k;
+  return CC_OK;
+}
+
+extern "C" void cc_uncut_destroy(cc_uncut* u) { delete u; }

@@ -1,0 +1,49 @@
+// Library-owned plan objects behind the opaque cc_plan / cc_uncut handles.
+#pragma once
+
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+
+namespace cc {
+void* device_alloc_copy(const void* host, size_t bytes);  // NULL on failure
+void device_free(void* p);
+int uncut_tile_bits(int precision);
+}  // namespace cc
+
+struct cc_plan {
+  struct Cut {
+    int q0, q1, kind, s0, s1;
+  };
+  // Merge stage s: U_s = sum_k U_{s-1}[aidx] (x) seg_s[bidx], batched over z.
+  struct Stage {
+    int seg = 0;
+    int qa = 0, qb = 0;  // log2 sizes of the accumulated factor and of segment s
+    int64_t K = 1, Z = 1;
+    int64_t aidx_off = 0, bidx_off = 0;  // offsets (int32 entries) into tables_dev
+  };
+
+  int q = 0, n_seg = 0, c_total = 0, precision = 0, decomp = 0;
+  std::vector<int> seg_q, seg_start, seg_c;
+  std::vector<int64_t> seg_off;
+  std::vector<std::vector<int>> seg_cut_ids;
+  std::vector<Cut> cuts;
+  std::vector<cc::HostProgram> hprog;
+  std::vector<cc::DeviceProgram> dprog;
+  std::vector<Stage> stages;
+  void* tables_dev = nullptr;
+  int64_t n_sub = 0;
+  uint64_t seg_buf_bytes = 0, psi_bytes = 0, workspace_bytes = 0, table_bytes = 0;
+  uint64_t chain_ws_amps = 0;  // amplitudes of one chained-merge intermediate buffer
+
+  ~cc_plan();
+};
+
+struct cc_uncut {
+  int q = 0, precision = 0;
+  cc::HostProgram hprog;
+  cc::DeviceProgram dprog;
+  ~cc_uncut();
+};

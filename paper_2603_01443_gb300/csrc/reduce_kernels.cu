@@ -1,0 +1,129 @@
+// FP64 verification reductions (max |a - b|, max |b|, <a|b>, <a|a>, <b|b>) and
+// the sampled-amplitude gather.  Every product and sum is taken in double
+// precision whatever the storage precision; complex64 inputs are widened
+// exactly before use.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace cc {
+
+namespace {
+
+constexpr int RB = 256;  // threads per reduction block
+
+struct Acc6 {
+  double d2, b2, re, im, na, nb;  // max |a-b|^2, max |b|^2, Re<a|b>, Im<a|b>, <a|a>, <b|b>
+};
+
+__device__ __forceinline__ void combine(Acc6& x, const Acc6& y) {
+  x.d2 = fmax(x.d2, y.d2);
+  x.b2 = fmax(x.b2, y.b2);
+  x.re += y.re;
+  x.im += y.im;
+  x.na += y.na;
+  x.nb += y.nb;
+}
+
+__device__ __forceinline__ Acc6 shfl_xor(const Acc6& a, int m) {
+  Acc6 r;
+  r.d2 = __shfl_xor_sync(0xffffffffu, a.d2, m);
+  r.b2 = __shfl_xor_sync(0xffffffffu, a.b2, m);
+  r.re = __shfl_xor_sync(0xffffffffu, a.re, m);
+  r.im = __shfl_xor_sync(0xffffffffu, a.im, m);
+  r.na = __shfl_xor_sync(0xffffffffu, a.na, m);
+  r.nb = __shfl_xor_sync(0xffffffffu, a.nb, m);
+  return r;
+}
+
+__device__ Acc6 block_reduce(Acc6 v) {
+  __shared__ Acc6 sh[RB / 32];
+  for (int m = 16; m >= 1; m >>= 1) combine(v, shfl_xor(v, m));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < RB / 32) ? sh[lane] : Acc6{0, 0, 0, 0, 0, 0};
+    for (int m = 16; m >= 1; m >>= 1) combine(v, shfl_xor(v, m));
+  }
+  return v;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(RB)
+    compare_partial(const C* __restrict__ a, const C* __restrict__ b, int64_t n,
+                    double* __restrict__ partials) {
+  Acc6 v{0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    const C x = a[i], y = b[i];
+    const double ar = x.x, ai = x.y, br = y.x, bi = y.y;
+    const double dr = ar - br, di = ai - bi;
+    v.d2 = fmax(v.d2, dr * dr + di * di);
+    v.b2 = fmax(v.b2, br * br + bi * bi);
+    v.re += ar * br + ai * bi;  // conj(a) b
+    v.im += ar * bi - ai * br;
+    v.na += ar * ar + ai * ai;
+    v.nb += br * br + bi * bi;
+  }
+  v = block_reduce(v);
+  if (threadIdx.x == 0) {
+    double* p = partials + 8 * blockIdx.x;
+    p[0] = v.d2; p[1] = v.b2; p[2] = v.re; p[3] = v.im; p[4] = v.na; p[5] = v.nb;
+  }
+}
+
+__global__ void __launch_bounds__(RB) compare_final(const double* __restrict__ partials,
+                                                    int n_blocks, double* __restrict__ out) {
+  Acc6 v{0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < n_blocks; i += RB) {
+    const double* p = partials + 8 * i;
+    combine(v, Acc6{p[0], p[1], p[2], p[3], p[4], p[5]});
+  }
+  v = block_reduce(v);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(v.d2);
+    out[1] = sqrt(v.b2);
+    out[2] = v.re;
+    out[3] = v.im;
+    out[4] = v.na;
+    out[5] = v.nb;
+  }
+}
+
+template <typename C>
+__global__ void gather_kernel(const C* __restrict__ psi, const int64_t* __restrict__ idx,
+                              int64_t n, C* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = psi[idx[i]];
+}
+
+}  // namespace
+
+cc_status launch_compare(const void* a, const void* b, int64_t n, int precision, double* out_dev,
+                         double* partials, int n_blocks, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == CC_C128)
+    compare_partial<double2><<<n_blocks, RB, 0, s>>>((const double2*)a, (const double2*)b, n, partials);
+  else
+    compare_partial<float2><<<n_blocks, RB, 0, s>>>((const float2*)a, (const float2*)b, n, partials);
+  compare_final<<<1, RB, 0, s>>>(partials, n_blocks, out_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("compare launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
+
+cc_status launch_gather(const void* psi, int precision, const int64_t* idx_dev, int64_t n,
+                        void* out_dev, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = (int)((n + 255) / 256);
+  if (precision == CC_C128)
+    gather_kernel<double2><<<blocks, 256, 0, s>>>((const double2*)psi, idx_dev, n, (double2*)out_dev);
+  else
+    gather_kernel<float2><<<blocks, 256, 0, s>>>((const float2*)psi, idx_dev, n, (float2*)out_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("gather launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
+
+}  // namespace cc

@@ -1,0 +1,336 @@
+// Device runtime and the device-side C ABI entry points: errors, device
+// checks, library scratch, program upload, and the launches behind
+// cc_simulate_segments, cc_merge, cc_simulate_uncut, cc_compare, cc_gather.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace cc {
+
+namespace {
+thread_local std::string g_error = "no error";
+
+struct DeviceState {
+  bool checked = false;
+  cc_status status = CC_OK;
+  int sms = 0;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+std::mutex g_mu;
+DeviceState g_dev[64];
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return -1;
+  return d;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+}  // namespace
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+cc_status fail(cc_status s, const std::string& msg) {
+  g_error = msg;
+  return s;
+}
+
+cc_status check_device() {
+  const int d = current_device();
+  if (d < 0 || d >= 64) return fail(CC_ECUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& s = g_dev[d];
+  if (!s.checked) {
+    cudaDeviceProp prop;
+    const cudaError_t e = cudaGetDeviceProperties(&prop, d);
+    s.checked = true;
+    if (e != cudaSuccess) {
+      s.status = CC_ECUDA;
+    } else if (!(prop.major == 10 && prop.minor == 3)) {
+      s.status = CC_EDEVICE;
+    } else {
+      s.status = CC_OK;
+      s.sms = prop.multiProcessorCount;
+    }
+  }
+  if (s.status == CC_EDEVICE)
+    return fail(CC_EDEVICE, "the library is built for sm_103a (GB300) devices only");
+  if (s.status != CC_OK) return fail(s.status, "cudaGetDeviceProperties failed");
+  return CC_OK;
+}
+
+int num_sms() {
+  const int d = current_device();
+  if (d < 0 || d >= 64) return 1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return std::max(1, g_dev[d].sms);
+}
+
+void* scratch(size_t bytes) {
+  const int d = current_device();
+  if (d < 0 || d >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& s = g_dev[d];
+  if (s.scratch_bytes < bytes) {
+    if (s.scratch) cudaFree(s.scratch);
+    s.scratch = nullptr;
+    s.scratch_bytes = 0;
+    const size_t want = std::max(bytes, size_t(1) << 20);
+    if (cudaMalloc(&s.scratch, want) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    s.scratch_bytes = want;
+  }
+  return s.scratch;
+}
+
+void* device_alloc_copy(const void* host, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max(bytes, size_t(16))) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (bytes && cudaMemcpy(p, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return nullptr;
+  }
+  return p;
+}
+
+void device_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+int max_tile_bits(int precision) { return precision == CC_C128 ? 13 : 14; }
+int low_tile_bits(int precision) { return precision == CC_C128 ? 3 : 4; }
+
+int uncut_tile_bits(int precision) {
+  int k = max_tile_bits(precision);
+  if (const char* e = std::getenv("CUTSIM_UNCUT_TILE_BITS")) {
+    const int v = std::atoi(e);
+    if (v >= low_tile_bits(precision) + 1 && v <= max_tile_bits(precision)) k = v;
+  }
+  return k;
+}
+
+cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp) {
+  const size_t rb = precision == CC_C128 ? 8 : 4;
+  const size_t o_pass = 0;
+  const size_t o_ops = align16(o_pass + hp.passes.size() * sizeof(DPass));
+  const size_t o_terms = align16(o_ops + hp.ops.size() * sizeof(DOp));
+  const size_t o_mats = align16(o_terms + hp.terms.size() * sizeof(DTerm));
+  const size_t o_tabs = align16(o_mats + hp.mats.size() * 2 * rb);
+  const size_t total = align16(o_tabs + hp.tabs.size() * 2 * rb);
+  std::vector<unsigned char> img(total, 0);
+  std::memcpy(img.data() + o_pass, hp.passes.data(), hp.passes.size() * sizeof(DPass));
+  std::memcpy(img.data() + o_ops, hp.ops.data(), hp.ops.size() * sizeof(DOp));
+  std::memcpy(img.data() + o_terms, hp.terms.data(), hp.terms.size() * sizeof(DTerm));
+  auto put = [&](size_t off, const std::vector<cd>& v) {
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (rb == 8) {
+        double* p = reinterpret_cast<double*>(img.data() + off) + 2 * i;
+        p[0] = v[i].real();
+        p[1] = v[i].imag();
+      } else {
+        float* p = reinterpret_cast<float*>(img.data() + off) + 2 * i;
+        p[0] = (float)v[i].real();
+        p[1] = (float)v[i].imag();
+      }
+    }
+  };
+  put(o_mats, hp.mats);
+  put(o_tabs, hp.tabs);
+  void* base = device_alloc_copy(img.data(), total);
+  if (!base) return fail(CC_ENOMEM, "device allocation of a gate program failed");
+  unsigned char* b = static_cast<unsigned char*>(base);
+  dp.base = base;
+  dp.bytes = total;
+  dp.passes_dev = b + o_pass;
+  dp.ops = reinterpret_cast<const DOp*>(b + o_ops);
+  dp.terms = reinterpret_cast<const DTerm*>(b + o_terms);
+  dp.mats = b + o_mats;
+  dp.tabs = b + o_tabs;
+  dp.passes = hp.passes;
+  dp.n_ops = (int)hp.ops.size();
+  return CC_OK;
+}
+
+void free_program(DeviceProgram& dp) {
+  if (dp.base) cudaFree(dp.base);
+  dp = DeviceProgram();
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+namespace {
+int amp_bytes(int precision) { return precision == CC_C128 ? 16 : 8; }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+cc_status sync_status(cudaStream_t s, const char* what) {
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return CC_OK;
+}
+}  // namespace
+
+extern "C" cc_status cc_simulate_segments(const cc_plan* p, void* seg_buf, uint64_t bytes,
+                                          void* stream) {
+  if (!p) return fail(CC_EINVAL, "plan is NULL");
+  if (!seg_buf) return fail(CC_EINVAL, "seg_buf is NULL");
+  if (!aligned16(seg_buf)) return fail(CC_EINVAL, "seg_buf must be 16-byte aligned");
+  if (bytes < p->seg_buf_bytes)
+    return fail(CC_EBUFSIZE, "seg_buf holds " + std::to_string(bytes) + " bytes, plan needs " +
+                                 std::to_string(p->seg_buf_bytes));
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  const int ab = amp_bytes(p->precision);
+  for (int i = 0; i < p->n_seg; ++i) {
+    char* base = static_cast<char*>(seg_buf) + p->seg_off[i] * ab;
+    st = run_program(p->dprog[i], p->precision, base, int64_t(1) << p->seg_c[i],
+                     int64_t(1) << p->seg_q[i], stream);
+    if (st != CC_OK) return st;
+  }
+  return CC_OK;
+}
+
+extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t seg_bytes,
+                              void* psi, uint64_t psi_bytes, void* workspace, uint64_t ws_bytes,
+                              int32_t form, void* stream) {
+  if (!p) return fail(CC_EINVAL, "plan is NULL");
+  if (!seg_buf || !psi) return fail(CC_EINVAL, "NULL buffer");
+  if (!aligned16(seg_buf) || !aligned16(psi) || (workspace && !aligned16(workspace)))
+    return fail(CC_EINVAL, "buffers must be 16-byte aligned");
+  if (seg_bytes < p->seg_buf_bytes) return fail(CC_EBUFSIZE, "seg_buf too small");
+  if (psi_bytes < p->psi_bytes) return fail(CC_EBUFSIZE, "psi too small");
+  if (form < CC_MERGE_AUTO || form > CC_MERGE_BF16X3) return fail(CC_EINVAL, "unknown merge form");
+  if ((form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3) && p->precision != CC_C64)
+    return fail(CC_EINVAL, "tensor-core merge forms need a complex64 plan");
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ab = amp_bytes(p->precision);
+  const char* sb = static_cast<const char*>(seg_buf);
+  if (p->n_seg == 1) {
+    const cudaError_t e = cudaMemcpyAsync(psi, sb, p->psi_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+    return CC_OK;
+  }
+  const int32_t* tables = static_cast<const int32_t*>(p->tables_dev);
+  if (p->n_seg == 2) {
+    const auto& sg = p->stages[0];
+    MergeStage ms{sb + p->seg_off[0] * ab, sb + p->seg_off[1] * ab, psi, sg.qa, sg.qb,
+                  sg.K, sg.Z, int64_t(1) << (sg.qa + sg.qb), tables + sg.aidx_off,
+                  tables + sg.bidx_off};
+    int f = form;
+    if (f == CC_MERGE_AUTO) f = (p->precision == CC_C64 && sg.K >= 16) ? CC_MERGE_TF32X3 : CC_MERGE_FMA;
+    if (f != CC_MERGE_FMA) {
+      if (ws_bytes < merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f) || !workspace) {
+        if (form != CC_MERGE_AUTO) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
+        f = CC_MERGE_FMA;
+      } else {
+        st = launch_merge_tc(ms, f, workspace, ws_bytes, stream);
+        if (st == CC_OK) return CC_OK;
+        if (st != CC_EUNSUPPORTED || form != CC_MERGE_AUTO) return st;
+        f = CC_MERGE_FMA;
+      }
+    }
+    return launch_merge_fma(ms, p->precision, stream);
+  }
+  // n >= 3: chain through two workspace buffers.
+  const uint64_t half = p->chain_ws_amps * ab;
+  if (!workspace || ws_bytes < 2 * half) return fail(CC_EBUFSIZE, "workspace too small for the chained merge");
+  if (form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3)
+    return fail(CC_EINVAL, "tensor-core forms merge two segments; use FMA or AUTO for n >= 3");
+  char* w[2] = {static_cast<char*>(workspace), static_cast<char*>(workspace) + half};
+  const void* acc = sb + p->seg_off[0] * ab;
+  for (size_t s_i = 0; s_i < p->stages.size(); ++s_i) {
+    const auto& sg = p->stages[s_i];
+    const bool last = s_i + 1 == p->stages.size();
+    void* out = last ? psi : w[s_i & 1];
+    MergeStage ms{acc, sb + p->seg_off[sg.seg] * ab, out, sg.qa, sg.qb, sg.K, sg.Z,
+                  int64_t(1) << (sg.qa + sg.qb), tables + sg.aidx_off, tables + sg.bidx_off};
+    st = launch_merge_fma(ms, p->precision, stream);
+    if (st != CC_OK) return st;
+    acc = out;
+  }
+  return CC_OK;
+}
+
+extern "C" cc_status cc_simulate_uncut(const cc_uncut* u, void* psi, uint64_t psi_bytes,
+                                       void* stream) {
+  if (!u) return fail(CC_EINVAL, "uncut plan is NULL");
+  if (!psi) return fail(CC_EINVAL, "psi is NULL");
+  if (!aligned16(psi)) return fail(CC_EINVAL, "psi must be 16-byte aligned");
+  if (psi_bytes < (uint64_t(1) << u->q) * amp_bytes(u->precision))
+    return fail(CC_EBUFSIZE, "psi too small");
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  return run_program(u->dprog, u->precision, psi, 1, int64_t(1) << u->q, stream);
+}
+
+extern "C" cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precision,
+                                double* out, void* stream) {
+  if (!a || !b || !out) return fail(CC_EINVAL, "NULL argument");
+  if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+  if (n_amp < 0) return fail(CC_EINVAL, "n_amp < 0");
+  if (!aligned16(a) || !aligned16(b)) return fail(CC_EINVAL, "buffers must be 16-byte aligned");
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  const int n_blocks = num_sms() * 4;
+  double* scr = static_cast<double*>(scratch(sizeof(double) * 8 * (n_blocks + 1)));
+  if (!scr) return fail(CC_ENOMEM, "scratch allocation failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = launch_compare(a, b, n_amp, precision, scr + 8 * n_blocks, scr, n_blocks, stream);
+  if (st != CC_OK) return st;
+  double res[8];
+  const cudaError_t e = cudaMemcpyAsync(res, scr + 8 * n_blocks, sizeof(res), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+  st = sync_status(s, "cc_compare");
+  if (st != CC_OK) return st;
+  std::memcpy(out, res, 6 * sizeof(double));
+  return CC_OK;
+}
+
+extern "C" cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision,
+                               const int64_t* idx, int64_t n_idx, void* out, void* stream) {
+  if (!psi || !idx || !out) return fail(CC_EINVAL, "NULL argument");
+  if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+  if (n_idx < 0 || n_idx > (int64_t(1) << 20)) return fail(CC_ERANGE, "n_idx must be in 0..2^20");
+  for (int64_t i = 0; i < n_idx; ++i)
+    if (idx[i] < 0 || idx[i] >= n_amp)
+      return fail(CC_ERANGE, "index " + std::to_string(idx[i]) + " outside [0, n_amp)");
+  if (n_idx == 0) return CC_OK;
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  const int ab = amp_bytes(precision);
+  char* scr = static_cast<char*>(scratch(n_idx * (8 + ab) + 16));
+  if (!scr) return fail(CC_ENOMEM, "scratch allocation failed");
+  int64_t* idx_dev = reinterpret_cast<int64_t*>(scr);
+  void* out_dev = scr + ((n_idx * 8 + 15) & ~int64_t(15));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(idx_dev, idx, n_idx * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+  st = launch_gather(psi, precision, idx_dev, n_idx, out_dev, stream);
+  if (st != CC_OK) return st;
+  e = cudaMemcpyAsync(out, out_dev, n_idx * ab, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+  return sync_status(s, "cc_gather");
+}
+
+extern "C" const char* cc_last_error(void) { return g_error.c_str(); }
+
+extern "C" const char* cc_version(void) { return "cutsim 0.1 (sm_103a)"; }

@@ -1,0 +1,131 @@
+"""The C-ABI library: it builds, loads, exports every function include/cutsim.h
+declares, its struct layouts match the binding, and host-side validation
+rejects bad arguments before any device work (no GPU needed)."""
+
+import ctypes
+import os
+import subprocess
+import tempfile
+from ctypes import byref, c_double, c_int32, c_int64, c_void_p
+
+import pytest
+
+from paper_2603_01443_gb300 import capi
+
+import workload as w
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(capi.LIB_PATH):
+        from paper_2603_01443_gb300 import build
+
+        build.build()
+    return capi.lib()
+
+
+def test_header_declares_the_boundary():
+    names = capi.header_functions()
+    for fn in ("cc_plan_create", "cc_simulate_segments", "cc_merge", "cc_simulate_uncut",
+               "cc_uncut_create", "cc_compare", "cc_gather", "cc_last_error"):
+        assert fn in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = capi.header_functions()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding declares every one of them
+    assert sorted(capi._SIGNATURES) == names
+
+
+def test_struct_layout_matches_c(L):
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "cutsim.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cc_gate), offsetof(cc_gate, theta),
+             sizeof(cc_plan_info_t), offsetof(cc_plan_info_t, seg_offset),
+             offsetof(cc_plan_info_t, n_sub), offsetof(cc_plan_info_t, workspace_bytes),
+             offsetof(cc_plan_info_t, seg_passes));
+      return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(capi.HEADER), c, "-o", exe])
+        vals = [int(x) for x in subprocess.check_output([exe]).split()]
+    CI = capi.CPlanInfo
+    assert vals == [ctypes.sizeof(capi.CGate), capi.CGate.theta.offset, ctypes.sizeof(CI),
+                    CI.seg_offset.offset, CI.n_sub.offset, CI.workspace_bytes.offset,
+                    CI.seg_passes.offset]
+    assert vals[0] == 40
+
+
+def test_version_and_last_error(L):
+    assert b"sm_103a" in L.cc_version()
+    assert isinstance(L.cc_last_error(), bytes)
+
+
+def _create(L, gates, q, segs, decomp=0, prec=0):
+    arr = capi.gate_array(gates)
+    sizes = (c_int32 * len(segs))(*segs)
+    h = c_void_p()
+    st = L.cc_plan_create(arr, len(gates), q, sizes, len(segs), decomp, prec, byref(h))
+    return st, h
+
+
+def test_plan_rejects_bad_arguments(L):
+    g = w.brickwork(8, 2, 0)
+    assert _create(L, g, 8, [4, 3])[0] == 1          # sizes do not sum to q
+    assert _create(L, g, 8, [4, 4, 0])[0] == 1       # empty segment
+    assert _create(L, g, 35, [35])[0] == 2           # q too large
+    assert _create(L, g, 8, [1] * 8 + [0])[0] == 2   # more than 8 segments
+    assert _create(L, g, 8, [4, 4], decomp=7)[0] == 1
+    assert _create(L, g, 8, [4, 4], prec=5)[0] == 1
+    bad = g + [w.Gate("H", 8)]
+    assert _create(L, bad, 8, [4, 4])[0] == 1        # qubit out of range
+    assert b"out of range" in L.cc_last_error()
+    bad = g + [w.Gate("CZ", 3, 3)]
+    assert _create(L, bad, 8, [4, 4])[0] == 1        # two-qubit gate on one qubit
+    sizes = (c_int32 * 2)(4, 4)
+    assert L.cc_plan_create(capi.gate_array(g), len(g), 8, sizes, 2, 0, 0, None) == 1
+
+
+def test_plan_rejects_too_many_cuts(L):
+    g = w.brickwork_cut(16, 32, 0, [8, 8], 25)
+    assert _create(L, g, 16, [8, 8])[0] == 2
+    assert b"24" in L.cc_last_error()
+
+
+def test_plan_rejects_non_adjacent_cut_for_chained_merge(L):
+    g = [w.Gate("H", 0), w.Gate("CZ", 0, 8)]
+    assert _create(L, g, 9, [3, 3, 3])[0] == 3
+    assert b"non-adjacent" in L.cc_last_error()
+
+
+def test_valid_plan_needs_a_device(L):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    st, _ = _create(L, w.brickwork(8, 2, 0), 8, [4, 4])
+    assert st in (6, 8)  # no device / not sm_103
+
+
+def test_entry_points_reject_null(L):
+    assert L.cc_simulate_segments(None, None, 0, None) == 1
+    assert L.cc_merge(None, None, 0, None, 0, None, 0, 0, None) == 1
+    assert L.cc_simulate_uncut(None, None, 0, None) == 1
+    out = (c_double * 6)()
+    assert L.cc_compare(None, None, 4, 0, out, None) == 1
+    idx = (c_int64 * 1)(5)
+    assert L.cc_gather(c_void_p(16), 4, 0, idx, 1, c_void_p(16), None) == 2  # index >= n_amp
+    assert L.cc_gather(c_void_p(16), 4, 3, idx, 1, c_void_p(16), None) == 1  # bad precision
+    assert L.cc_plan_info(None, None) == 1
+    assert L.cc_uncut_info(None, None, None, None) == 1
+    L.cc_plan_destroy(None)
+    L.cc_uncut_destroy(None)

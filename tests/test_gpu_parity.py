@@ -1,0 +1,182 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle on the same
+seeded circuits, element by element (max |d psi| / max |psi| within 1e-12 in
+complex128 and 2e-6 in complex64, fidelity within 1e-6 of 1)."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workload as w
+from oracle import cutting as ct
+from oracle import statevector as sv
+from paper_2603_01443_gb300 import api, capi
+from gpu_util import TOL, assert_parity, gpu_cut, gpu_uncut, rel_err
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["c64", "c128"]
+DECOMPS = ["projector", "s_sdg"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("decomp", DECOMPS)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_small_brickwork_cut_and_uncut(cuda_lib, prec, decomp, seed):
+    # q = 12, depth 4, two 6-qubit segments, the natural c_total = 2
+    q, segs = 12, [6, 6]
+    gates = w.brickwork(q, 4, seed)
+    ref = sv.simulate(q, gates)
+    psi, _, plan = gpu_cut(gates, q, segs, decomp, prec)
+    assert plan.info["c_total"] == 2 and plan.info["n_sub"] == 8
+    assert_parity(psi.cpu().numpy(), ref, prec, "cut")
+    oracle_merge, _, _ = ct.cut_simulate(q, gates, segs, decomp)
+    assert rel_err(psi.cpu().numpy(), oracle_merge) <= TOL[prec]
+    u, _ = gpu_uncut(gates, q, prec)
+    assert_parity(u.cpu().numpy(), ref, prec, "uncut")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("decomp", DECOMPS)
+@pytest.mark.parametrize("q,segs,c", [(12, [6, 6], 3), (14, [5, 9], 4), (13, [4, 4, 5], 2)])
+def test_segment_variants_match_oracle_subcircuits(cuda_lib, prec, decomp, q, segs, c):
+    gates = w.brickwork_cut(q, 6, 7, segs, c)
+    pre = ct.preprocess(q, gates, segs, decomp)
+    states = ct.simulate_subcircuits(pre)
+    _, seg, plan = gpu_cut(gates, q, segs, decomp, prec)
+    for i in range(len(segs)):
+        got = plan.segment_view(seg, i).cpu().numpy()
+        assert got.shape == (len(states[i]), 1 << segs[i])
+        for r, ref in enumerate(states[i]):
+            # the library folds cut j's coefficient into the first-qubit side
+            fac = 1.0 + 0j
+            for t, j in enumerate(pre.seg_cuts[i]):
+                if pre.cuts[j].segments[0] == i:
+                    fac *= pre.coefs[j][(r >> t) & 1]
+            want = fac * ref
+            err = np.max(np.abs(got[r] - want))
+            assert err <= TOL[prec] * max(np.max(np.abs(want)), 1e-300) or err < 1e-14, (i, r, err)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("q,n_gates,seed", [(5, 80, 0), (11, 300, 1), (15, 400, 2), (17, 300, 3)])
+def test_uncut_random_gate_positions(cuda_lib, prec, q, n_gates, seed):
+    # every gate kind, two-qubit gates on far-apart pairs, high and low qubits;
+    # q > 14 (c64) / > 13 (c128) runs several HBM passes
+    gates = w.random_circuit(q, n_gates, seed)
+    u, up = gpu_uncut(gates, q, prec)
+    if q >= 15:
+        assert up.info["n_passes"] > 1
+    assert_parity(u.cpu().numpy(), sv.simulate(q, gates), prec, "uncut")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_uncut_brickwork_multipass(cuda_lib, prec):
+    q = 20
+    gates = w.brickwork(q, 8, 3)
+    u, up = gpu_uncut(gates, q, prec)
+    assert up.info["n_passes"] > 1
+    assert_parity(u.cpu().numpy(), sv.simulate(q, gates), prec, "uncut")
+
+
+@pytest.mark.parametrize("prec,segs", [("c64", [15, 5]), ("c64", [5, 15]), ("c128", [14, 6])])
+def test_segments_larger_than_one_tile(cuda_lib, prec, segs):
+    # segment vectors beyond shared memory run as multi-pass programs
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 6, 4, segs, 3)
+    psi, _, plan = gpu_cut(gates, q, segs, "projector", prec)
+    assert max(plan.info["seg_passes"]) > 1
+    assert_parity(psi.cpu().numpy(), sv.simulate(q, gates), prec, "cut")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("segs", [[8, 8], [7, 9], [3, 13], [12, 4]])
+@pytest.mark.parametrize("c", [0, 1, 5, 12])
+def test_merge_term_counts(cuda_lib, prec, segs, c):
+    # K = 2^c from 1 to 4096 merge terms, tiled and flat kernels, uneven factors
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 16, 5, segs, c)
+    psi, _, plan = gpu_cut(gates, q, segs, "s_sdg" if c % 2 else "projector", prec)
+    assert plan.info["c_total"] == c
+    assert_parity(psi.cpu().numpy(), sv.simulate(q, gates), prec, f"K={1 << c}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("decomp", DECOMPS)
+@pytest.mark.parametrize("segs,cpb", [([6, 6, 6], 2), ([7, 6, 5], [3, 1]), ([4, 4, 4, 4], 1)])
+def test_chained_merge_three_or_more_segments(cuda_lib, prec, decomp, segs, cpb):
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 8, 9, segs, cpb)
+    psi, _, plan = gpu_cut(gates, q, segs, decomp, prec)
+    assert_parity(psi.cpu().numpy(), sv.simulate(q, gates), prec, "chained")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("segs", [[4, 4, 4], [6, 6], [3, 9]])
+def test_staircase_cx_cuts(cuda_lib, prec, segs):
+    gates = w.staircase(12, 3)
+    psi, _, plan = gpu_cut(gates, 12, segs, "s_sdg", prec)
+    assert all(plan.cut(j)["kind"] == capi.GATE_KIND["CX"] for j in range(plan.info["c_total"]))
+    assert_parity(psi.cpu().numpy(), sv.simulate(12, gates), prec, "staircase")
+
+
+def test_ghz_closed_form(cuda_lib):
+    q = 16
+    psi, _, _ = gpu_cut(w.ghz(q), q, [8, 8], "projector", "c128")
+    ref = np.zeros(1 << q, complex)
+    ref[0] = ref[-1] = 1 / math.sqrt(2)
+    assert rel_err(psi.cpu().numpy(), ref) <= TOL["c128"]
+
+
+def test_single_segment_and_no_gates(cuda_lib):
+    gates = w.brickwork(9, 3, 1)
+    psi, _, plan = gpu_cut(gates, 9, [9], "projector", "c128")
+    assert plan.info["c_total"] == 0
+    assert_parity(psi.cpu().numpy(), sv.simulate(9, gates), "c128")
+    psi, _, _ = gpu_cut([], 6, [3, 3], "projector", "c64")
+    ref = np.zeros(64, complex)
+    ref[0] = 1
+    assert np.array_equal(psi.cpu().numpy(), ref.astype(np.complex64))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_compare_and_gather(cuda_lib, prec):
+    rng = np.random.default_rng(3)
+    n = (1 << 20) + 37
+    a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(api.NUMPY_DTYPE[prec])
+    b = a + (1e-3 * rng.standard_normal(n)).astype(api.NUMPY_DTYPE[prec])
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    got = api.compare(ta, tb, prec)
+    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
+    inner = np.vdot(a64, b64)
+    assert abs(got["max_abs_diff"] - np.max(np.abs(a64 - b64))) <= 1e-12 * np.max(np.abs(a64 - b64))
+    assert abs(got["max_abs_b"] - np.max(np.abs(b64))) <= 1e-12 * np.max(np.abs(b64))
+    assert abs(got["inner_re"] - inner.real) <= 1e-9 * abs(inner)
+    assert abs(got["inner_im"] - inner.imag) <= 1e-9 * abs(inner)
+    assert abs(got["norm2_a"] - np.vdot(a64, a64).real) <= 1e-9 * n
+    idx = w.sample_indices(20, 4096, 5) + [n - 1, 0]
+    assert np.array_equal(api.gather(ta, idx, prec), a[np.array(idx)])
+    with pytest.raises(capi.CutsimError):
+        api.gather(ta, [n], prec)
+
+
+def test_error_paths_on_device(cuda_lib):
+    gates = w.brickwork(10, 3, 0)
+    plan = api.CutPlan(gates, 10, [5, 5], "projector", "c128")
+    seg = plan.alloc_seg_buf()
+    psi = plan.alloc_psi()
+    with pytest.raises(capi.CutsimError) as e:
+        plan.simulate_segments(seg[:-1])
+    assert e.value.status == 5
+    plan.simulate_segments(seg)
+    with pytest.raises(capi.CutsimError) as e:
+        plan.merge(seg, psi[:-1])
+    assert e.value.status == 5
+    with pytest.raises(capi.CutsimError) as e:
+        plan.merge(seg, psi, None, "bf16x3")
+    assert e.value.status == 1
+    up = api.UncutPlan(gates, 10, "c64")
+    with pytest.raises(capi.CutsimError) as e:
+        up.simulate(up.alloc_psi()[:100])
+    assert e.value.status == 5
