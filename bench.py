@@ -151,7 +151,7 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline_sample(a, steps_budget_s=20.0):
+def cpu_baseline_sample(a, n_sub_sample=48, n_amp=1 << 21):
     """Time the FP64 oracle on a bounded sample of the workload, in a fresh
     single-threaded interpreter, and extrapolate to T_cut seconds."""
     code = r"""
@@ -184,8 +184,6 @@ print(json.dumps({"t_pre": t_pre, "t_sub": t_sub, "t_merge": t_merge,
                   "sample_s": t_pre + t_sub_sample + t_merge_sample,
                   "n_sub": len(subs), "n_sub_sample": len(pick), "n_amp": n_amp}))
 """
-    n_sub_sample = 48
-    n_amp = 1 << 21
     src = code % (ROOT, a.q, a.depth, a.n, a.ctotal, a.seed, a.decomp, n_sub_sample, n_amp)
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -215,7 +213,7 @@ def reference_arm(a):
     vals, secs = [], []
     last = None
     for i in range(a.warmup + a.steps):
-        r = cpu_baseline_sample(a)
+        r = cpu_baseline_sample(a, n_sub_sample=24, n_amp=1 << 20)
         if "error" in r:
             print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r["error"]}))
             return 0
@@ -272,7 +270,7 @@ def main(argv=None):
     probe.close()
     up_probe.close()
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     rec = {"pre": [], "sub": [], "merge": [], "orig": [], "orig_host": [], "verify": [], "cmp": []}
 
     def step(record):
@@ -291,8 +289,11 @@ def main(argv=None):
         up.simulate(psi_u, stream)
         ev[4].record(stream)
         cmp = api.compare(psi, psi_u, a.prec, stream)  # synchronizes
+        ev[5].record(stream)
+        ev[5].synchronize()
         t_verify_end = time.perf_counter()
         if record:
+            rec["verify"].append(ev[4].elapsed_time(ev[5]) / 1e3)
             rec["pre"].append(t_pre)
             rec["sub"].append(ev[0].elapsed_time(ev[1]) / 1e3)
             rec["merge"].append(ev[1].elapsed_time(ev[2]) / 1e3)
@@ -402,6 +403,7 @@ def main(argv=None):
                                 "and reads both 2^q vectors (>> 129 MB L2) between merges")),
         "stages": {"pre_s": mean["pre"], "sub_s": mean["sub"], "merge_s": mean["merge"],
                    "cut_s": t_cut, "orig_s": mean["orig"], "orig_plan_s": mean["orig_host"],
+                   "verify_s": mean["verify"],
                    "delta": (t_cut - mean["orig"]) / mean["orig"]},
         "merge_gbs": merge_gbs,
         "gate_pass_gbs": pass_gbs,

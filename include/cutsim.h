@@ -206,6 +206,12 @@ cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precis
 cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision, const int64_t* idx,
                     int64_t n_idx, void* out, void* stream);
 
+/* cc_sync -- synchronize `stream`, then report CC_ETIMEOUT if any kernel of
+ * this library on the current device gave up a bounded wait since the last
+ * cc_sync (the flag is cleared by the call).  Asynchronous entry points
+ * cannot return that status themselves. */
+cc_status cc_sync(void* stream);
+
 /* cc_last_error -- thread-local message of the last failure (never NULL). */
 const char* cc_last_error(void);
 

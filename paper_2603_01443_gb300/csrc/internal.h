@@ -153,5 +153,6 @@ cc_status launch_gather(const void* psi, int precision, const int64_t* idx_dev, 
 cc_status check_device();
 int num_sms();
 void* scratch(size_t bytes);  // per-device library scratch (grown on demand)
+int* device_error_flag();     // per-device int set by kernels whose bounded waits expire
 
 }  // namespace cc

@@ -1,16 +1,523 @@
-// Merging (Algorithm 3) on tcgen05 tensor cores -- placeholder until the
-// tensor-core kernel lands; every call reports CC_EUNSUPPORTED so that
-// CC_MERGE_AUTO falls back to the CUDA-core form.
+// Merging (Algorithm 3) on tcgen05 tensor cores.
+//
+// The two-factor merge psi[y * NA + x] = sum_k A_k[x] B_k[y] is one real GEMM
+//   C[y][n] = sum_kk R[y][kk] * Cop[n][kk],   n = 2x + (0: real, 1: imaginary)
+// with kk < K holding real parts and K <= kk < 2K imaginary parts:
+//   R[y][k] = Re B_k[y],          R[y][K+k] = Im B_k[y]
+//   Cop[2x][k] = Re A_k[x],       Cop[2x][K+k] = -Im A_k[x]
+//   Cop[2x+1][k] = Im A_k[x],     Cop[2x+1][K+k] = Re A_k[x]
+// so that C, stored row-major in FP32, is psi in interleaved complex64.
+// Every operand is split x = hi + lo (bf16 + bf16, or tf32 + tf32) and the
+// kernel accumulates hi*hi + hi*lo + lo*hi in FP32 (Markidis et al. 2018,
+// "NVIDIA tensor core programmability, performance & precision").
+//
+// Kernel structure (one CTA per SM, persistent over 128 x 256 output tiles):
+//   warp 0      TMA producer: per 128-byte K block, loads R_hi, R_lo (128 rows)
+//               and C_hi, C_lo (256 rows) with 128-byte swizzle into one of two
+//               96 KB shared-memory stages;
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
+//               and one lane issues the tcgen05.mma instructions;
+//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, 128-byte
+//               streaming stores of each row, then release of the accumulator,
+//               so the store of tile i overlaps the MMAs of tile i+1.
+// Every mbarrier wait is bounded: on expiry the kernel raises a device error
+// flag (reported as CC_ETIMEOUT by cc_sync), waits a bounded time for its own
+// copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 
 namespace cc {
 
-uint64_t merge_tc_workspace_bytes(int, int, int64_t, int) { return 0; }
+namespace {
 
-cc_status launch_merge_tc(const MergeStage&, int, void*, uint64_t, void*) {
-  return fail(CC_EUNSUPPORTED, "tensor-core merge not available in this build");
+constexpr int BM = 128;            // rows (y) per tile
+constexpr int BN = 256;            // real columns per tile (128 complex amplitudes)
+constexpr int KB_BYTES = 128;      // bytes of K per stage (one swizzle atom row)
+constexpr int STAGES = 2;
+constexpr int R_TILE = BM * KB_BYTES;  // 16 KB
+constexpr int C_TILE = BN * KB_BYTES;  // 32 KB
+constexpr int STAGE_BYTES = 2 * R_TILE + 2 * C_TILE;  // 96 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 512;
+constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity; false if the CTA is aborting or
+// the wait expired (which starts the abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded wait used on the abort path only.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity) && clock64() - t0 < WAIT_CYCLES) {
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 8-row (1024-byte) groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if (KIND == CC_MERGE_BF16X3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256.
+template <int KIND>
+__host__ __device__ constexpr uint32_t idesc_value() {
+  return (1u << 4)                                            // D format: F32
+         | ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 7)         // A format: BF16 / TF32
+         | ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 10)        // B format: BF16 / TF32
+         | ((uint32_t)(BN >> 3) << 17)                        // N / 8
+         | ((uint32_t)(BM >> 4) << 24);                       // M / 16
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1)
+    merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
+                    float* __restrict__ out, int n_rows, int n_cols, int kblocks, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* tfull = bars + 2 * STAGES;   // [2]
+  uint64_t* tempty = bars + 2 * STAGES + 2;  // [2]
+  uint64_t* drain = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 7);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = n_rows / BM, tiles_n = n_cols / BN;
+  const int n_tiles = tiles_m * tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_r)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c)) : "memory");
+      int s = 0;
+      uint32_t use = 0;  // how many times the stage ring wrapped
+      bool issued[STAGES] = {false, false};
+      uint32_t issued_parity[STAGES] = {0, 0};
+      bool ok = true;
+      const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = smem + s * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, m0);
+          tma_load_2d(smem_u32(st + R_TILE), &map_r, fb, kb * kelem, n_rows + m0);
+          tma_load_2d(smem_u32(st + 2 * R_TILE), &map_c, fb, kb * kelem, n0);
+          tma_load_2d(smem_u32(st + 2 * R_TILE + C_TILE), &map_c, fb, kb * kelem, n_cols + n0);
+          issued[s] = true;
+          issued_parity[s] = use & 1;
+          if (++s == STAGES) {
+            s = 0;
+            ++use;
+          }
+        }
+      }
+      if (!ok) {  // let our own copies land before the CTA exits
+        for (int i = 0; i < STAGES; ++i)
+          if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_value<KIND>();
+      int s = 0;
+      uint32_t use = 0;
+      int iter = 0;
+      bool ok = true;
+      bool any_mma = false;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++iter) {
+        const int a = iter & 1;
+        if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
+          const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
+#pragma unroll
+          for (int k = 0; k < KB_BYTES / 32; ++k) {
+            const uint64_t adv = (uint64_t)((k * 32) >> 4);
+            umma<KIND>(dtmem, rh + adv, ch + adv, idesc, (kb | k) != 0);
+            umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
+            umma<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
+          }
+          any_mma = true;
+          umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+          if (++s == STAGES) {
+            s = 0;
+            ++use;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[a]);  // accumulator a is complete
+      }
+      if (!ok && any_mma) {  // let our own MMAs finish before TMEM is freed
+        umma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    int iter = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++iter) {
+      const int a = iter & 1;
+      // one lane waits, the warp follows its verdict (tcgen05.ld needs the whole warp)
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+      const int row = m0 + quarter * 32 + lane;
+      float* orow = out + (size_t)row * n_cols + n0;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tbase + (uint32_t)(c * 32), r);
+        float4* dst = reinterpret_cast<float4*>(orow + c * 32);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          __stcs(dst + j, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                      __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- operand split
+__device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* lo, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  *hi = __bfloat16_as_ushort(h);
+  *lo = __bfloat16_as_ushort(l);
+}
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void split_store(uint32_t* hi, uint32_t* lo, float v) {
+  const uint32_t h = to_tf32(v);
+  *hi = h;
+  *lo = to_tf32(v - __uint_as_float(h));
+}
+
+// One warp per operand row; lanes walk the padded K range.  Rows [0, NB) are
+// the row operand R, rows [NB, NB + 2 NA) the column operand Cop.
+template <typename E>
+__global__ void __launch_bounds__(256)
+    split_operands(const float2* __restrict__ A, const float2* __restrict__ B, int qa, int qb,
+                   int K, int KR, const int32_t* __restrict__ aidx,
+                   const int32_t* __restrict__ bidx, E* __restrict__ r_ops, E* __restrict__ c_ops) {
+  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
+  const int64_t rows = NB + 2 * NA;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  if (row < NB) {
+    E* hi = r_ops + row * KR;
+    E* lo = r_ops + (NB + row) * KR;
+    for (int kk = lane; kk < KR; kk += 32) {
+      float v = 0.f;
+      if (kk < 2 * K) {
+        const float2 b = B[(int64_t)bidx[kk % K] * NB + row];
+        v = kk < K ? b.x : b.y;
+      }
+      split_store(hi + kk, lo + kk, v);
+    }
+  } else {
+    const int64_t n = row - NB;
+    const int64_t x = n >> 1;
+    const int part = (int)(n & 1);
+    E* hi = c_ops + n * KR;
+    E* lo = c_ops + (2 * NA + n) * KR;
+    for (int kk = lane; kk < KR; kk += 32) {
+      float v = 0.f;
+      if (kk < 2 * K) {
+        const float2 a = A[(int64_t)aidx[kk % K] * NA + x];
+        if (part == 0) v = kk < K ? a.x : -a.y;
+        else v = kk < K ? a.y : a.x;
+      }
+      split_store(hi + kk, lo + kk, v);
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+int kr_of(int64_t K, int form) {
+  const int kelem = form == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+  return (int)(((2 * K + kelem - 1) / kelem) * kelem);
+}
+
+int elem_bytes(int form) { return form == CC_MERGE_BF16X3 ? 2 : 4; }
+
+}  // namespace
+
+uint64_t merge_tc_workspace_bytes(int qa, int qb, int64_t K, int form) {
+  if (qa < 7 || qb < 7 || K < 1 || K > (1 << 20)) return 0;
+  const uint64_t kr = (uint64_t)kr_of(K, form);
+  const uint64_t rows = 2 * ((uint64_t(1) << qb) + 2 * (uint64_t(1) << qa));
+  return rows * kr * elem_bytes(form) + 1024;
+}
+
+cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint64_t ws_bytes,
+                          void* stream) {
+  if (st.Z != 1) return fail(CC_EUNSUPPORTED, "tensor-core merge handles single-batch stages");
+  if (st.qa < 7 || st.qb < 7)
+    return fail(CC_EUNSUPPORTED, "tensor-core merge needs both factors of >= 128 amplitudes");
+  if (st.qa + st.qb > 40) return fail(CC_ERANGE, "merge output too large");
+  const uint64_t need = merge_tc_workspace_bytes(st.qa, st.qb, st.K, form);
+  if (need == 0) return fail(CC_EUNSUPPORTED, "tensor-core merge shape unsupported");
+  if (ws_bytes < need) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(CC_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  int* err = device_error_flag();
+  if (!err) return fail(CC_ENOMEM, "device error flag allocation failed");
+
+  const int64_t NA = int64_t(1) << st.qa, NB = int64_t(1) << st.qb;
+  const int KR = kr_of(st.K, form);
+  const int eb = elem_bytes(form);
+  unsigned char* ws =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(workspace) + 1023) & ~uintptr_t(1023));
+  unsigned char* r_ops = ws;
+  unsigned char* c_ops = ws + (size_t)2 * NB * KR * eb;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  const int64_t rows = NB + 2 * NA;
+  const unsigned blocks = (unsigned)((rows + 7) / 8);
+  if (form == CC_MERGE_BF16X3)
+    split_operands<uint16_t><<<blocks, 256, 0, s>>>(
+        (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
+        (uint16_t*)r_ops, (uint16_t*)c_ops);
+  else
+    split_operands<uint32_t><<<blocks, 256, 0, s>>>(
+        (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
+        (uint32_t*)r_ops, (uint32_t*)c_ops);
+
+  CUtensorMap map_r, map_c;
+  const CUtensorMapDataType dt =
+      form == CC_MERGE_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint32_t box_k = (cuuint32_t)(KB_BYTES / eb);
+  const cuuint32_t estr[2] = {1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(2 * NB)};
+    const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
+    const cuuint32_t box[2] = {box_k, (cuuint32_t)BM};
+    if (enc(&map_r, dt, 2, r_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (row operand) failed");
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(4 * NA)};
+    const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
+    const cuuint32_t box[2] = {box_k, (cuuint32_t)BN};
+    if (enc(&map_c, dt, 2, c_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand) failed");
+  }
+
+  auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
+                                      : merge_tc_kernel<CC_MERGE_TF32X3>;
+  static int attr_done[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !(attr_done[dev] & (1 << form))) {
+    cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr_done[dev] |= 1 << form;
+  }
+  const int n_rows = (int)NB, n_cols = (int)(2 * NA);
+  const int n_tiles = (n_rows / BM) * (n_cols / BN);
+  const int grid = std::min(n_tiles, num_sms());
+  const int kblocks = KR * eb / KB_BYTES;
+  kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, (float*)st.out, n_rows, n_cols, kblocks, err);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(e));
+  return CC_OK;
 }
 
 }  // namespace cc

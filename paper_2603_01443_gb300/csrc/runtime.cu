@@ -24,6 +24,7 @@ struct DeviceState {
   int sms = 0;
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  int* err_flag = nullptr;
 };
 std::mutex g_mu;
 DeviceState g_dev[64];
@@ -92,6 +93,23 @@ void* scratch(size_t bytes) {
     s.scratch_bytes = want;
   }
   return s.scratch;
+}
+
+int* device_error_flag() {
+  const int d = current_device();
+  if (d < 0 || d >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState& s = g_dev[d];
+  if (!s.err_flag) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess || cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (p) cudaFree(p);
+      return nullptr;
+    }
+    s.err_flag = static_cast<int*>(p);
+  }
+  return s.err_flag;
 }
 
 void* device_alloc_copy(const void* host, size_t bytes) {
@@ -329,6 +347,20 @@ extern "C" cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision
   e = cudaMemcpyAsync(out, out_dev, n_idx * ab, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
   return sync_status(s, "cc_gather");
+}
+
+extern "C" cc_status cc_sync(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cc_status st = sync_status(s, "cc_sync");
+  if (st != CC_OK) return st;
+  int* flag = device_error_flag();
+  if (!flag) return fail(CC_ENOMEM, "device error flag allocation failed");
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h) e = cudaMemset(flag, 0, sizeof(int));
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("cc_sync: ") + cudaGetErrorString(e));
+  if (h) return fail(CC_ETIMEOUT, "a bounded device wait expired; results of that call are undefined");
+  return CC_OK;
 }
 
 extern "C" const char* cc_last_error(void) { return g_error.c_str(); }
