@@ -254,7 +254,7 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
                   sg.K, sg.Z, int64_t(1) << (sg.qa + sg.qb), tables + sg.aidx_off,
                   tables + sg.bidx_off};
     int f = form;
-    if (f == CC_MERGE_AUTO) f = (p->precision == CC_C64 && sg.K >= 16) ? CC_MERGE_TF32X3 : CC_MERGE_FMA;
+    if (f == CC_MERGE_AUTO) f = CC_MERGE_FMA;
     if (f != CC_MERGE_FMA) {
       if (ws_bytes < merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f) || !workspace) {
         if (form != CC_MERGE_AUTO) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
