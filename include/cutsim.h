@@ -206,6 +206,29 @@ cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precis
 cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision, const int64_t* idx,
                     int64_t n_idx, void* out, void* stream);
 
+/* cc_gather_static -- cc_gather that allocates nothing.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory, such as a process whose GPU memory belongs to another allocator
+ * (a framework's caching allocator, a fixed budget reserved at start-up) or a
+ * latency-sensitive loop that cannot take the device-wide synchronisation
+ * cudaMalloc/cudaFree may imply.  Same arguments, result and errors as
+ * cc_gather, except:
+ *   - indices and amplitudes are staged in a fixed device array that is part
+ *     of the library image (CC_GATHER_STATIC_MAX entries, 1.5 MiB held on
+ *     every GPU that loads the library until the process exits); n_idx above
+ *     CC_GATHER_STATIC_MAX is rejected with CC_ERANGE before any device work;
+ *   - the first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current, so make the first call
+ *     on each device before any stream capture;
+ *   - every call on a device shares the one array: calls whose device work
+ *     overlaps (other threads, other streams) race and may return each
+ *     other's amplitudes.  A call synchronizes `stream` before it returns, so
+ *     calls made one after another from one thread never overlap.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+#define CC_GATHER_STATIC_MAX 65536
+cc_status cc_gather_static(const void* psi, int64_t n_amp, int32_t precision, const int64_t* idx,
+                           int64_t n_idx, void* out, void* stream);
+
 /* cc_sync -- synchronize `stream`, then report CC_ETIMEOUT if any kernel of
  * this library on the current device gave up a bounded wait since the last
  * cc_sync (the flag is cleared by the call).  Asynchronous entry points

@@ -73,6 +73,8 @@ _SIGNATURES = {
     "cc_compare": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, POINTER(c_double), c_void_p]),
     "cc_gather": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), c_int64, c_void_p,
                             c_void_p]),
+    "cc_gather_static": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), c_int64,
+                                   c_void_p, c_void_p]),
     "cc_sync": (c_int32, [c_void_p]),
     "cc_last_error": (c_char_p, []),
     "cc_version": (c_char_p, []),
