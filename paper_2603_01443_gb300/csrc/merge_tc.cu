@@ -46,6 +46,7 @@ constexpr int STAGE_BYTES = 2 * R_TILE + 2 * C_TILE;  // 96 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
+constexpr int64_t kTf32MaxTerms = 256;        // 3xTF32 stays within 2e-6 relative up to here
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -450,6 +451,10 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   if (st.qa + st.qb > 40) return fail(CC_ERANGE, "merge output too large");
   const uint64_t need = merge_tc_workspace_bytes(st.qa, st.qb, st.K, form);
   if (need == 0) return fail(CC_EUNSUPPORTED, "tensor-core merge shape unsupported");
+  if (form == CC_MERGE_TF32X3 && st.K > kTf32MaxTerms)
+    return fail(CC_EUNSUPPORTED,
+                "3xTF32 merge is limited to 256 terms: beyond that the FP32 accumulation in the "
+                "tensor core exceeds the complex64 tolerance");
   if (ws_bytes < need) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CC_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");

@@ -1,0 +1,76 @@
+"""The tcgen05 tensor-core merge forms (3xTF32 and split-BF16) against the FP64
+oracle and against the CUDA-core form, on factors spanning one to many
+128 x 256 output tiles and K from 1 to 1024 merge terms."""
+
+import numpy as np
+import pytest
+import torch
+
+import workload as w
+from oracle import statevector as sv
+from paper_2603_01443_gb300 import api, capi
+from gpu_util import FID_TOL, TOL, fidelity, rel_err
+
+pytestmark = pytest.mark.gpu
+
+FORM_TOL = {"tf32x3": TOL["c64"], "bf16x3": TOL["bf16x3"]}
+
+
+def run(gates, q, segs, form, decomp="projector"):
+    plan = api.CutPlan(gates, q, segs, decomp, "c64")
+    seg = plan.alloc_seg_buf()
+    psi = plan.alloc_psi()
+    ws = plan.alloc_workspace()
+    plan.simulate_segments(seg)
+    plan.merge(seg, psi, ws, form)
+    capi.check(capi.lib().cc_sync(torch.cuda.current_stream().cuda_stream), "cc_sync")
+    return psi, plan
+
+
+CASES = [([7, 7], 0), ([7, 7], 3), ([8, 9], 5), ([9, 8], 6), ([10, 10], 4), ([8, 8], 8)]
+
+
+@pytest.mark.parametrize("form,segs,c", [("tf32x3",) + x for x in CASES] +
+                         [("bf16x3",) + x for x in CASES + [([8, 8], 10), ([8, 8], 12)]])
+def test_tc_merge_vs_oracle(cuda_lib, form, segs, c):
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 12, 21 + c, segs, c)
+    psi, plan = run(gates, q, segs, form, "s_sdg" if c % 2 else "projector")
+    ref = sv.simulate(q, gates)
+    got = psi.cpu().numpy()
+    err = rel_err(got, ref)
+    assert err <= FORM_TOL[form], f"{form} K={1 << c}: {err:.3e}"
+    assert 1 - fidelity(got, ref) <= FID_TOL
+
+
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+def test_tc_merge_matches_fma_at_scale(cuda_lib, form):
+    q, segs, c = 26, [13, 13], 6
+    gates = w.brickwork_cut(q, 16, 3, segs, c)
+    psi_tc, plan = run(gates, q, segs, form)
+    psi_fma, _ = run(gates, q, segs, "fma")
+    st = api.compare(psi_tc, psi_fma, "c64")
+    assert st["max_abs_diff"] <= FORM_TOL[form] * st["max_abs_b"], st
+    assert 1 - st["fidelity"] <= FID_TOL
+
+
+def test_tc_merge_rejects_small_workspace(cuda_lib):
+    gates = w.brickwork_cut(16, 8, 0, [8, 8], 4)
+    plan = api.CutPlan(gates, 16, [8, 8], "projector", "c64")
+    seg = plan.alloc_seg_buf()
+    psi = plan.alloc_psi()
+    plan.simulate_segments(seg)
+    ws = plan.alloc_workspace()
+    with pytest.raises(capi.CutsimError) as e:
+        plan.merge(seg, psi, ws[:16], "tf32x3")
+    assert e.value.status == 5
+
+
+def test_tf32x3_refuses_deep_merges(cuda_lib):
+    # beyond 256 terms the tensor-core FP32 accumulation exceeds 2e-6
+    gates = w.brickwork_cut(16, 12, 1, [8, 8], 9)
+    with pytest.raises(capi.CutsimError) as e:
+        run(gates, 16, [8, 8], "tf32x3")
+    assert e.value.status == 3
+    psi, _ = run(gates, 16, [8, 8], "auto")  # AUTO falls back to the FMA form
+    assert rel_err(psi.cpu().numpy(), sv.simulate(16, gates)) <= TOL["c64"]
