@@ -51,6 +51,10 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--sweep", choices=["boundary"], default=None,
+                   help="run a measurement sweep instead of the single-line benchmark")
+    p.add_argument("--sweep-both", action="store_true",
+                   help="sweep complex64 and complex128")
     return p.parse_args(argv)
 
 
@@ -76,6 +80,11 @@ def measured_peaks():
         return float(d["hbm_gbs"]), float(d.get("bf16_tflops", FALLBACK_BF16_TFLOPS)), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_source_hash(files):
@@ -205,6 +214,19 @@ print(json.dumps({"t_pre": t_pre, "t_sub": t_sub, "t_merge": t_merge,
     }
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings across the process group (the
+    slowest replica sets the job's time); identity for a single process."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def reference_arm(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -235,16 +257,87 @@ def reference_arm(a):
     return 0
 
 
+def sweep_boundary(a):
+    """Speedup-boundary sweep (the paper's Sec. V.B experiment on this GPU):
+    q in {16, 20, 24}, depth in {8, 16, 32}, n = 2 equal segments, c_total
+    from 0 to min(12, depth); per point the stage times and
+    Delta = (T_cut - T_orig) / T_orig.  One JSON line per point, then a
+    summary with the largest c_total that still gives Delta < 0 per (q, depth)
+    next to Eq. 13's c_total < q / 2."""
+    import torch
+
+    import workload as w
+    from paper_2603_01443_gb300 import api, capi
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    summary = {}
+    precs = ["c64", "c128"] if a.prec == "c64" and a.sweep_both else [a.prec]
+    for prec in precs:
+        for q in (16, 20, 24):
+            for depth in (8, 16, 32):
+                best = None
+                for c in range(0, min(12, depth) + 1):
+                    gates = w.brickwork_cut(q, depth, a.seed, [q // 2, q - q // 2], c)
+                    packed = capi.GateArray(gates)
+                    probe = api.CutPlan(packed, q, [q // 2, q - q // 2], a.decomp, prec)
+                    seg, psi, ws = probe.alloc_seg_buf(), probe.alloc_psi(), probe.alloc_workspace()
+                    probe.close()
+                    psi_u = torch.empty_like(psi)
+                    rec = []
+                    for rep in range(1 + 3):
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        plan = api.CutPlan(packed, q, [q // 2, q - q // 2], a.decomp, prec)
+                        t_pre = time.perf_counter() - t0
+                        ev[0].record(stream)
+                        plan.simulate_segments(seg, stream)
+                        ev[1].record(stream)
+                        plan.merge(seg, psi, ws, "auto", stream)
+                        ev[2].record(stream)
+                        t1 = time.perf_counter()
+                        up = api.UncutPlan(packed, q, prec)
+                        t_up = time.perf_counter() - t1
+                        ev[3].record(stream)
+                        up.simulate(psi_u, stream)
+                        end = torch.cuda.Event(enable_timing=True)
+                        end.record(stream)
+                        end.synchronize()
+                        if rep:
+                            rec.append((t_pre, ev[0].elapsed_time(ev[1]) / 1e3,
+                                        ev[1].elapsed_time(ev[2]) / 1e3,
+                                        t_up + ev[3].elapsed_time(end) / 1e3))
+                        plan.close()
+                        up.close()
+                    pre, sub, mer, orig = (statistics.mean(x) for x in zip(*rec))
+                    cut = pre + sub + mer
+                    delta = (cut - orig) / orig
+                    print(json.dumps({"sweep": "boundary", "precision": prec, "q": q,
+                                      "depth": depth, "c_total": c, "pre_s": pre, "sub_s": sub,
+                                      "merge_s": mer, "cut_s": cut, "orig_s": orig,
+                                      "delta": delta}), flush=True)
+                    if delta < 0:
+                        best = c
+                    del seg, psi, ws, psi_u
+                summary.setdefault(prec, {}).setdefault(str(q), {})[str(depth)] = best
+    print(json.dumps({"sweep": "boundary", "largest_c_total_with_speedup": summary,
+                      "eq13_threshold": {str(q): q / 2 for q in (16, 20, 24)}}))
+    return 0
+
+
 def main(argv=None):
     a = parse_args(argv)
     if a.impl == "reference":
         return reference_arm(a)
+    if a.sweep == "boundary":
+        return sweep_boundary(a)
 
     import torch
     import torch.distributed as dist
 
     import workload as w
-    from paper_2603_01443_gb300 import api
+    from paper_2603_01443_gb300 import api, capi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -257,6 +350,7 @@ def main(argv=None):
     seed = a.seed + rank
     gates = w.brickwork_cut(a.q, a.depth, seed, segs, cpb)
     stream = torch.cuda.current_stream()
+    packed = capi.GateArray(gates)  # the circuit as the C ABI takes it, packed once
 
     probe = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
     assert probe.info["c_total"] == a.ctotal
@@ -275,7 +369,7 @@ def main(argv=None):
 
     def step(record):
         t0 = time.perf_counter()
-        plan = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
+        plan = api.CutPlan(packed, a.q, segs, a.decomp, a.prec)
         t_pre = time.perf_counter() - t0
         ev[0].record(stream)
         plan.simulate_segments(seg, stream)
@@ -283,7 +377,7 @@ def main(argv=None):
         plan.merge(seg, psi, ws, a.merge_form, stream)
         ev[2].record(stream)
         t1 = time.perf_counter()
-        up = api.UncutPlan(gates, a.q, a.prec)
+        up = api.UncutPlan(packed, a.q, a.prec)
         t_uplan = time.perf_counter() - t1
         ev[3].record(stream)
         up.simulate(psi_u, stream)
@@ -323,10 +417,7 @@ def main(argv=None):
 
     mean = {k: statistics.mean(v) for k, v in rec.items() if k != "cmp"}
     t_cut = mean["pre"] + mean["sub"] + mean["merge"]
-    if world > 1:
-        t = torch.tensor([elapsed, t_cut], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed, t_cut = float(t[0]), float(t[1])
+    elapsed, t_cut = max_over_ranks([elapsed, t_cut], world, dev)
 
     # e2e: host circuit in, host state out (pinned), copies inside the timed region
     e2e = None
@@ -337,7 +428,7 @@ def main(argv=None):
         for i in range(a.warmup + a.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            plan = api.CutPlan(gates, a.q, segs, a.decomp, a.prec)
+            plan = api.CutPlan(packed, a.q, segs, a.decomp, a.prec)
             plan.simulate_segments(seg, stream)
             plan.merge(seg, psi, ws, a.merge_form, stream)
             host_psi.copy_(psi, non_blocking=True)
@@ -346,11 +437,7 @@ def main(argv=None):
                 times.append(time.perf_counter() - t0)
             h2d = plan.info["table_bytes"]
             plan.close()
-        e2e_v = statistics.mean(times)
-        if world > 1:
-            t = torch.tensor([e2e_v], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_v = float(t[0])
+        (e2e_v,) = max_over_ranks([statistics.mean(times)], world, dev)
         e2e = {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(info["psi_bytes"])}
         del host_psi
@@ -378,12 +465,32 @@ def main(argv=None):
                 "frac": merge_gbs / hbm, "traffic": recorded_traffic("merge"),
                 "kernel": "cut_merge", "bytes_per_launch": merge_bytes,
                 "launch_s": mean["merge"], "peak_source": peak_src}
-    pass_rf = {"bound": "hbm", "achieved": pass_gbs, "peak": hbm, "unit": "GB/s",
-               "frac": pass_gbs / hbm, "traffic": recorded_traffic("uncut_pass"),
-               "kernel": "sv_pass (uncut)", "bytes_per_launch": pass_bytes,
-               "launch_s": pass_s, "peak_source": peak_src}
+    # The uncut passes do 8 FMA (16 flops) per amplitude for every dense
+    # one-qubit gate (U3, H, X; a CX is H CZ H on its target) and nothing for
+    # the diagonal ones, which ride along as sign/phase factors: FP32-bound.
+    n_dense = sum(1 for g in gates if g.kind in ("U3", "H", "X")) + \
+        2 * sum(1 for g in gates if g.kind == "CX")
+    uncut_flops = 16.0 * n_dense * n_amp
+    fp32_peak = fp32_peak_tflops()
+    pass_tf = uncut_flops / n_pass / pass_s / 1e12
+    pass_rf = {"bound": "alu", "achieved": pass_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+               "frac": pass_tf / fp32_peak, "traffic": recorded_traffic("uncut_pass"),
+               "kernel": "stage_kernel (uncut passes)", "flops_per_launch": uncut_flops / n_pass,
+               "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+    tc_form = a.merge_form if a.merge_form != "auto" else (
+        "tf32x3" if (a.prec == "c64" and 16 <= K <= 256 and a.n == 2) else "fma")
+    if tc_form in ("tf32x3", "bf16x3"):
+        # three split products of the real GEMM: 3 x 8K flops per output amplitude
+        tc_flops = 3.0 * 8 * K * n_amp
+        tc_peak = bf16 * (0.5 if tc_form == "tf32x3" else 1.0)  # nominal TF32:BF16 = 1:2
+        merge_rf["tensor"] = {"achieved": tc_flops / mean["merge"] / 1e12, "peak": tc_peak,
+                              "unit": "TFLOP/s", "form": tc_form,
+                              "frac": tc_flops / mean["merge"] / 1e12 / tc_peak,
+                              "peak_source": peak_src + " bf16 burst" +
+                              (" x 0.5 (nominal TF32/BF16)" if tc_form == "tf32x3" else "")}
     dominant = pass_rf if orig_dev > mean["merge"] else merge_rf
-    launches = sum(info["seg_passes"]) + 1 + n_pass + 2
+    launches = sum(info["seg_passes"]) + (2 if tc_form != "fma" else 1) + n_pass + 2
     cmp = rec["cmp"][-1]
     cpu = None if a.no_cpu_baseline else cpu_baseline_sample(a)
     out = {

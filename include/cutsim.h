@@ -75,7 +75,8 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  *                    same three-product split, FP32 accumulation (CC_C64,
  *                    factors >= 2^7; max|dpsi|/max|psi| <= 5e-5).
  * CC_MERGE_AUTO    : TF32X3 where it applies and 16 <= K <= 256, else FMA.
- * The tensor-core forms apply to n_seg = 2 only (CC_EINVAL for n_seg >= 3). */
+ * For n_seg >= 3 the form applies to the last (2^q-sized) stage of the chain;
+ * the earlier, smaller stages always use FMA. */
 typedef enum {
   CC_MERGE_AUTO = 0,
   CC_MERGE_FMA = 1,

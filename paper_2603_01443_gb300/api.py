@@ -42,7 +42,10 @@ def _nbytes(t: Optional[torch.Tensor]) -> int:
 
 
 class CutPlan:
-    """Preprocessing (Algorithm 1) of one circuit and partition."""
+    """Preprocessing (Algorithm 1) of one circuit and partition.
+
+    ``gates`` is a sequence of gates (kind, q0, q1, theta, phi, lam) or a
+    ``capi.GateArray`` packed once beforehand."""
 
     def __init__(self, gates: Sequence, q: int, seg_sizes: Sequence[int],
                  decomp: str = "projector", precision: str = "c64"):
@@ -50,10 +53,10 @@ class CutPlan:
         self.q = q
         self.precision = precision
         self.decomp = decomp
-        arr = capi.gate_array(gates)
+        arr = gates if isinstance(gates, capi.GateArray) else capi.GateArray(gates)
         sizes = (c_int32 * len(seg_sizes))(*seg_sizes)
         h = c_void_p()
-        capi.check(L.cc_plan_create(arr, len(gates), q, sizes, len(seg_sizes),
+        capi.check(L.cc_plan_create(arr.data, arr.n, q, sizes, len(seg_sizes),
                                     capi.DECOMP[decomp], capi.PRECISION[precision], byref(h)),
                    "cc_plan_create")
         self._h = h
@@ -128,9 +131,9 @@ class UncutPlan:
         L = capi.lib()
         self.q = q
         self.precision = precision
-        arr = capi.gate_array(gates)
+        arr = gates if isinstance(gates, capi.GateArray) else capi.GateArray(gates)
         h = c_void_p()
-        capi.check(L.cc_uncut_create(arr, len(gates), q, capi.PRECISION[precision], byref(h)),
+        capi.check(L.cc_uncut_create(arr.data, arr.n, q, capi.PRECISION[precision], byref(h)),
                    "cc_uncut_create")
         self._h = h
         npass, nops, tb = c_int32(), c_int32(), c_int32()

@@ -107,6 +107,14 @@ def check(status: int, where: str) -> None:
         raise CutsimError(status, where, lib().cc_last_error().decode(errors="replace"))
 
 
+class GateArray:
+    """A circuit packed once into a cc_gate array (reusable across calls)."""
+
+    def __init__(self, gates):
+        self.n = len(gates)
+        self.data = gate_array(gates)
+
+
 def gate_array(gates):
     """Pack gates (objects with kind, q0, q1, theta, phi, lam) into a cc_gate array."""
     arr = (CGate * max(len(gates), 1))()

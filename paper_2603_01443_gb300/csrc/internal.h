@@ -17,16 +17,22 @@ void set_error(const std::string& msg);
 cc_status fail(cc_status s, const std::string& msg);
 
 // ------------------------------------------------------- device programs
-// A gate program on an nq-qubit vector is a list of passes.  A pass moves one
-// tile of 2^k amplitudes (k "tile bits" of the vector index) into shared
-// memory, applies a list of fused operations there and writes it back.
+// A gate program acts on one vector of 2^nq amplitudes.  For a segment the
+// vector is the whole block of its 2^{c_i} variants: the variant number
+// occupies the index bits above the segment's q_i qubits, so a variant bit is
+// a "qubit" that carries no dense gate, only the diagonal cut terms, and many
+// small variants share one tile.
 //
-// Inside a pass every amplitude carries a "virtual index"
-//   v = l | (T << k) | (r << nq)
-// where l is its tile-local index, T the tile number (the non-tile index bits
-// in increasing order) and r the variant number of the vector.  Diagonal
-// factors are functions of two bits of v, so a phase may depend on tile bits,
-// on fixed (non-tile) bits and on the variant's cut bits alike.
+// The program is a list of passes.  A pass moves tiles of 2^k amplitudes (k
+// "tile bits" of the vector index) through shared memory.  Inside a pass every
+// amplitude carries a virtual index v = l | (T << k), where l is its tile-local
+// index and T the tile number (the non-tile bits in increasing order); every
+// diagonal factor is a function of bits of v.
+//
+// A pass is a list of stages.  In a stage each thread holds 2^rbits amplitudes
+// in registers whose tile bits are the stage's register bits; dense one-qubit
+// matrices act on register bits only, so a stage runs without touching shared
+// memory, and shared memory is used only to re-map bits between stages.
 
 enum : uint8_t { TERM_SIGN = 0, TERM_TABLE = 1 };
 
@@ -40,34 +46,48 @@ struct DTerm {
 
 enum : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
 
-// OP_DENSE: for every pair (l0, l1 = l0 | 1<<t) apply the terms
-//           [term_begin, term_end) to both amplitudes, then the 2x2 matrix
-//           mats[8*mat ...] (row-major, interleaved re/im).
-// OP_DIAG : apply the terms to every amplitude.
+// Before its matrix, an op multiplies each amplitude by (-1)^s with
+//   s = popcount(v & (v >> 1) & sign_adj) + sum of the sign terms (bit pairs
+//       not adjacent in v)   (mod 2)
+// and by every table term.  OP_DENSE then applies the 2x2 matrix
+// mats[8*mat ...] (row-major, interleaved re/im) to register bit t;
+// OP_DIAG stops after the diagonal factors.
 struct DOp {
   int32_t type, t;
   int32_t term_begin, term_sign_end, term_end;  // sign terms first
   int32_t mat;
+  uint64_t sign_adj;  // bit p set: a sign term on (p, p+1)
+};
+
+struct DStage {
+  int32_t op_begin, op_end;
+  int8_t rb[8];  // tile bit of register bit i
 };
 
 constexpr int MAX_TILE_BITS = 16;
-constexpr int MAX_REST_BITS = 40;
+constexpr int MAX_REST_BITS = 48;
+constexpr int MAX_REG_BITS = 5;
 
 struct DPass {
-  int32_t nq;         // qubits of the vector
-  int32_t k;          // tile bits
-  int32_t low;        // tile bits [0, low) are vector bits [0, low)
-  int32_t init_zero;  // tile starts as |0...0> instead of being loaded
-  int32_t op_begin, op_end;
-  int32_t n_rest;     // nq - k
+  int32_t nq;          // bits of the vector index
+  int32_t k;           // tile bits
+  int32_t low;         // tile bits [0, low) are vector bits [0, low)
+  int32_t init_zero;   // tiles start from |0...0> per variant instead of being loaded
+  int32_t stage_begin, stage_end;
+  int32_t rbits;       // register bits per thread: 2^rbits amplitudes, 2^(k - rbits) threads
+  int32_t n_rest;      // nq - k
+  uint32_t zero_tile;  // init: tile bits that are state qubits (must be 0 for amplitude 1)
+  uint32_t pad;
+  uint64_t zero_rest;  // init: bits of T that are state qubits
   int8_t tile_bit[MAX_TILE_BITS];  // vector bit of tile bit t
   int8_t rest_bit[MAX_REST_BITS];  // vector bit of the r-th non-tile bit
 };
 
 struct HostProgram {
-  int nq = 0;
-  int var_bits = 0;
+  int nq = 0;       // vector bits (state qubits + variant bits)
+  int n_state = 0;  // state qubits (the low bits)
   std::vector<DPass> passes;
+  std::vector<DStage> stages;
   std::vector<DOp> ops;
   std::vector<DTerm> terms;
   std::vector<cd> mats;  // 4 per matrix, row-major
@@ -78,17 +98,19 @@ struct HostProgram {
 enum ItemKind : int { IT_DENSE = 0, IT_DIAG1 = 1, IT_CZ = 2, IT_VAR = 3 };
 struct Item {
   int kind = IT_DENSE;
-  int a = -1, b = -1;  // qubits (b for IT_CZ)
+  int a = -1, b = -1;  // qubits (IT_CZ: the second qubit; IT_VAR: the variant bit)
   cd u[4];             // IT_DENSE: matrix; IT_DIAG1: u[0], u[3] diagonal
-  int slot = -1;       // IT_VAR: variant bit
+  int slot = -1;       // IT_VAR: variant bit number (b = n_state + slot)
   bool var_sign = false;  // IT_VAR: factor is Z^b (a sign term)
   cd d[2][2];             // IT_VAR: factor d[b][x] for variant bit b, index bit x
 };
 
-// Build the program of a list of items on nq qubits with var_bits variant
-// bits.  Tiles have at most kmax bits, the lowest `low` of them contiguous.
-HostProgram compile_program(const std::vector<Item>& items, int nq, int var_bits, int kmax,
-                            int low);
+// Build the program of a list of items on an nq-bit vector whose low n_state
+// bits are state qubits.  Tiles have at most kmax bits, the lowest `low` of
+// them contiguous; stages hold at most rb_max register bits.
+HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state, int kmax,
+                            int low, int rb_max);
+int reg_bits_max(int precision);
 
 // Gate -> items (CX as H CZ H on the target; diagonal one-qubit gates as IT_DIAG1).
 cc_status gate_items(const cc_gate& g, int qoff, std::vector<Item>& out);
@@ -104,17 +126,26 @@ struct DeviceProgram {
   const void* mats = nullptr;
   const void* tabs = nullptr;
   const void* passes_dev = nullptr;
+  const DStage* stages = nullptr;
   std::vector<DPass> passes;
   int n_ops = 0;
 };
 
+// Device image layout of one program inside a larger table buffer.
+struct ImageLayout {
+  size_t base, o_pass, o_stages, o_ops, o_terms, o_mats, o_tabs, end;
+};
+// Append hp's image (reals in the plan's precision) to img, 256-byte aligned.
+ImageLayout append_program_image(const HostProgram& hp, int precision,
+                                 std::vector<unsigned char>& img);
+// Point dp at an uploaded image (dev_base = device copy of img); dp does not own it.
+void bind_program(DeviceProgram& dp, const HostProgram& hp, unsigned char* dev_base,
+                  const ImageLayout& L);
 cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp);
 void free_program(DeviceProgram& dp);
 
-// Launch every pass of a program over n_vec vectors of 2^nq amplitudes
-// spaced vec_stride amplitudes apart, starting at `state`.
-cc_status run_program(const DeviceProgram& dp, int precision, void* state, int64_t n_vec,
-                      int64_t vec_stride, void* stream);
+// Launch every pass of a program over the 2^nq-amplitude vector at `state`.
+cc_status run_program(const DeviceProgram& dp, int precision, void* state, void* stream);
 
 // Largest tile (bits) a pass may use: 2^k amplitudes in shared memory.
 int max_tile_bits(int precision);

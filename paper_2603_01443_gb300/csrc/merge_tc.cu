@@ -17,9 +17,10 @@
 //               96 KB shared-memory stages;
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //               and one lane issues the tcgen05.mma instructions;
-//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, 128-byte
-//               streaming stores of each row, then release of the accumulator,
-//               so the store of tile i overlaps the MMAs of tile i+1.
+//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator in 32 x 32
+//               blocks, staged through shared memory and written by bulk
+//               tensor stores (TMA), then release of the accumulator, so the
+//               store of tile i overlaps the MMAs of tile i+1.
 // Every mbarrier wait is bounded: on expiry the kernel raises a device error
 // flag (reported as CC_ETIMEOUT by cc_sync), waits a bounded time for its own
 // copies and MMAs in flight, frees its TMEM and returns.
@@ -43,7 +44,9 @@ constexpr int STAGES = 2;
 constexpr int R_TILE = BM * KB_BYTES;  // 16 KB
 constexpr int C_TILE = BN * KB_BYTES;  // 32 KB
 constexpr int STAGE_BYTES = 2 * R_TILE + 2 * C_TILE;  // 96 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int STG_BYTES = 32 * 128;  // one epilogue store box: 32 rows x 32 FP32
+constexpr int STG_TOTAL = 4 * 2 * STG_BYTES;  // 4 epilogue warps x 2 buffers
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STG_TOTAL + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
 constexpr int64_t kTf32MaxTerms = 256;        // 3xTF32 stays within 2e-6 relative up to here
@@ -178,11 +181,13 @@ __host__ __device__ constexpr uint32_t idesc_value() {
 template <int KIND>
 __global__ void __launch_bounds__(192, 1)
     merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
-                    float* __restrict__ out, int n_rows, int n_cols, int kblocks, int* err) {
+                    const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
+                    int kblocks, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  unsigned char* stg_base = smem + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
   uint64_t* full = bars;                 // [STAGES]
   uint64_t* empty = bars + STAGES;       // [STAGES]
   uint64_t* tfull = bars + 2 * STAGES;   // [2]
@@ -306,8 +311,13 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4.  Each 32 x 32 block
+    // of the accumulator goes TMEM -> registers -> a 128-byte-swizzled staging
+    // buffer (conflict-free: a lane's row keeps its 16-byte chunks at j ^ (row & 7))
+    // -> one bulk tensor store; two buffers keep one store in flight.
     const int quarter = warp & 3;
+    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
+    int buf = 0;
     int iter = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++iter) {
       const int a = iter & 1;
@@ -318,23 +328,38 @@ __global__ void __launch_bounds__(192, 1)
       if (!ok) break;
       tc_fence_after();
       const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-      const int row = m0 + quarter * 32 + lane;
-      float* orow = out + (size_t)row * n_cols + n0;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
         tmem_ld32(tbase + (uint32_t)(c * 32), r);
-        float4* dst = reinterpret_cast<float4*>(orow + c * 32);
+        unsigned char* sb = stg + buf * STG_BYTES;
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          __stcs(dst + j, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                      __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+        for (int j = 0; j < 8; ++j) {
+          float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
+          *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile(
+              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                  reinterpret_cast<uint64_t>(&map_out)),
+              "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        buf ^= 1;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[a]);
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
   }
 
   tc_fence_before();
@@ -481,7 +506,7 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
         (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
         (uint32_t*)r_ops, (uint32_t*)c_ops);
 
-  CUtensorMap map_r, map_c;
+  CUtensorMap map_r, map_c, map_out;
   const CUtensorMapDataType dt =
       form == CC_MERGE_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint32_t box_k = (cuuint32_t)(KB_BYTES / eb);
@@ -505,6 +530,16 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand) failed");
   }
 
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * NA), (cuuint64_t)NB};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * NA) * 4};
+    const cuuint32_t box[2] = {32, 32};
+    if (enc(&map_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, st.out, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (output) failed");
+  }
+
   auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
                                       : merge_tc_kernel<CC_MERGE_TF32X3>;
   static int attr_done[64] = {0};
@@ -519,7 +554,7 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   const int n_tiles = (n_rows / BM) * (n_cols / BN);
   const int grid = std::min(n_tiles, num_sms());
   const int kblocks = KR * eb / KB_BYTES;
-  kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, (float*)st.out, n_rows, n_cols, kblocks, err);
+  kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(e));
   return CC_OK;

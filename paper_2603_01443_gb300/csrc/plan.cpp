@@ -37,11 +37,12 @@ int seg_of_qubit(const cc_plan* p, int qb) {
 }
 
 // Local term of cut j on one side, as a variant-selected diagonal factor.
-Item cut_item(int decomp, bool first_side, int local_qubit, int slot) {
+Item cut_item(int decomp, bool first_side, int local_qubit, int slot, int seg_qubits) {
   Item it;
   it.kind = IT_VAR;
   it.a = local_qubit;
   it.slot = slot;
+  it.b = seg_qubits + slot;  // the variant bit sits above the segment's qubits
   const cd I(0.0, 1.0);
   if (decomp == CC_DECOMP_PROJECTOR) {
     if (first_side) {  // |b><b|, coefficient 1
@@ -74,8 +75,7 @@ Item hadamard(int a) {
 }  // namespace
 
 cc_plan::~cc_plan() {
-  for (auto& d : dprog) free_program(d);
-  if (tables_dev) device_free(tables_dev);
+  if (arena) device_free(arena);
 }
 
 extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32_t q,
@@ -137,9 +137,9 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
       p->seg_cut_ids[s0].push_back(j);
       p->seg_cut_ids[s1].push_back(j);
       const int l0 = gt.q0 - p->seg_start[s0], l1 = gt.q1 - p->seg_start[s1];
-      items[s0].push_back(cut_item(decomp, true, l0, slot0));
+      items[s0].push_back(cut_item(decomp, true, l0, slot0, p->seg_q[s0]));
       if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
-      items[s1].push_back(cut_item(decomp, false, l1, slot1));
+      items[s1].push_back(cut_item(decomp, false, l1, slot1, p->seg_q[s1]));
       if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
     }
     p->c_total = (int)p->cuts.size();
@@ -162,19 +162,11 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
 
     // One shared program per segment.
     for (int i = 0; i < n_seg; ++i) {
-      HostProgram hp = compile_program(items[i], p->seg_q[i], p->seg_c[i],
-                                       max_tile_bits(precision), low_tile_bits(precision));
+      HostProgram hp = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
+                                       seg_tile_bits(precision), low_tile_bits(precision),
+                                       reg_bits_max(precision));
       if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
       p->hprog.push_back(std::move(hp));
-    }
-    // Everything above is host work; the device is needed from here on.
-    st = check_device();
-    if (st != CC_OK) return st;
-    for (int i = 0; i < n_seg; ++i) {
-      DeviceProgram dp;
-      st = upload_program(p->hprog[i], precision, dp);
-      if (st != CC_OK) return st;
-      p->dprog.push_back(dp);
     }
 
     // Merge stages: stage s absorbs segment s into the product of segments < s.
@@ -225,21 +217,35 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
         qa += sg.qb;
         p->stages.push_back(sg);
       }
+      // Workspace: the two chained-merge intermediates (n >= 3), then the split
+      // operands of a tensor-core form for the last (2^q-sized) stage.
       p->chain_ws_amps = u_max;
-      p->workspace_bytes = 2 * u_max * ab;
-      if (n_seg == 2) {
-        const auto& sg = p->stages[0];
-        uint64_t w = std::max(merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_TF32X3),
-                              merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_BF16X3));
-        p->workspace_bytes = std::max(p->workspace_bytes, w);
-      }
+      const auto& last = p->stages.back();
+      const uint64_t tc = std::max(merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_TF32X3),
+                                   merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_BF16X3));
+      p->workspace_bytes = 2 * u_max * ab + (precision == CC_C64 ? tc : 0);
     }
-    if (!tab.empty()) {
-      p->tables_dev = device_alloc_copy(tab.data(), tab.size() * sizeof(int32_t));
-      if (!p->tables_dev) return fail(CC_ENOMEM, "device allocation of merge tables failed");
-      p->table_bytes += tab.size() * sizeof(int32_t);
+    // All device tables of the plan (gate programs, merge index tables) go up
+    // in one allocation and one copy.  Everything above is host work; the
+    // device is needed from here on.
+    st = check_device();
+    if (st != CC_OK) return st;
+    std::vector<unsigned char> img;
+    std::vector<ImageLayout> lay;
+    for (int i = 0; i < n_seg; ++i) lay.push_back(append_program_image(p->hprog[i], precision, img));
+    const size_t tab_off = (img.size() + 255) & ~size_t(255);
+    img.resize(tab_off + tab.size() * sizeof(int32_t));
+    if (!tab.empty()) std::memcpy(img.data() + tab_off, tab.data(), tab.size() * sizeof(int32_t));
+    p->arena = device_alloc_copy(img.data(), img.size());
+    if (!p->arena) return fail(CC_ENOMEM, "device allocation of the plan tables failed");
+    unsigned char* dev = static_cast<unsigned char*>(p->arena);
+    for (int i = 0; i < n_seg; ++i) {
+      DeviceProgram dp;
+      bind_program(dp, p->hprog[i], dev, lay[i]);
+      p->dprog.push_back(dp);
     }
-    for (auto& d : p->dprog) p->table_bytes += d.bytes;
+    p->tables_dev = tab.empty() ? nullptr : dev + tab_off;
+    p->table_bytes = img.size();
     *out = p.release();
     return CC_OK;
   } catch (const std::bad_alloc&) {
@@ -308,7 +314,8 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
       st = gate_items(gates[g], 0, items);
       if (st != CC_OK) return st;
     }
-    u->hprog = compile_program(items, q, 0, uncut_tile_bits(precision), low_tile_bits(precision));
+    u->hprog = compile_program(items, q, q, uncut_tile_bits(precision), low_tile_bits(precision),
+                               reg_bits_max(precision));
     if (u->hprog.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
     st = check_device();
     if (st != CC_OK) return st;

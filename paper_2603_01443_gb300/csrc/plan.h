@@ -11,6 +11,7 @@ namespace cc {
 void* device_alloc_copy(const void* host, size_t bytes);  // NULL on failure
 void device_free(void* p);
 int uncut_tile_bits(int precision);
+int seg_tile_bits(int precision);
 }  // namespace cc
 
 struct cc_plan {
@@ -33,7 +34,8 @@ struct cc_plan {
   std::vector<cc::HostProgram> hprog;
   std::vector<cc::DeviceProgram> dprog;
   std::vector<Stage> stages;
-  void* tables_dev = nullptr;
+  void* arena = nullptr;       // the one device allocation holding every table below
+  void* tables_dev = nullptr;  // merge index tables (inside arena)
   int64_t n_sub = 0;
   uint64_t seg_buf_bytes = 0, psi_bytes = 0, workspace_bytes = 0, table_bytes = 0;
   uint64_t chain_ws_amps = 0;  // amplitudes of one chained-merge intermediate buffer

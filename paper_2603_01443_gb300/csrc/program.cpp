@@ -119,41 +119,98 @@ namespace {
 
 inline uint64_t item_mask(const Item& it) {
   uint64_t m = 1ull << it.a;
-  if (it.kind == IT_CZ) m |= 1ull << it.b;
+  if (it.kind == IT_CZ || it.kind == IT_VAR) m |= 1ull << it.b;
   return m;
 }
 
-// Forward scan: an item is applied when none of its qubits is blocked and it
-// is diagonal or its qubit is in the tile; otherwise its qubits become blocked
-// (so no later item on them can overtake it).
-int scan_pass(const std::vector<Item>& items, const std::vector<char>& applied, uint64_t tile,
-              std::vector<int>* take) {
+// Forward scan over the items listed in `order` that are not yet applied: an
+// item is taken when none of its qubits is blocked and it is diagonal or its
+// qubit is in `dense_ok`; otherwise its qubits become blocked, so no later item
+// on them can overtake it.  Returns the number of dense items taken.
+int scan(const std::vector<Item>& items, const std::vector<int>& order,
+         const std::vector<char>& applied, uint64_t dense_ok, std::vector<int>* take) {
   uint64_t blocked = 0;
   int dense = 0;
-  for (size_t i = 0; i < items.size(); ++i) {
+  for (int i : order) {
     if (applied[i]) continue;
     const Item& it = items[i];
     const uint64_t m = item_mask(it);
-    if ((m & blocked) || (it.kind == IT_DENSE && !(tile & (1ull << it.a)))) {
+    if ((m & blocked) || (it.kind == IT_DENSE && !(dense_ok & (1ull << it.a)))) {
       blocked |= m;
       continue;
     }
     if (it.kind == IT_DENSE) ++dense;
-    if (take) take->push_back((int)i);
+    if (take) take->push_back(i);
   }
   return dense;
 }
 
+// Choose `width` qubits out of `pool` (ascending) for the dense items to act
+// on, plus the always-included `fixed` mask: the candidates are the qubits of
+// the earliest pending dense items and every window of `width` consecutive
+// pool entries; the one that admits the most dense items wins.
+uint64_t choose_set(const std::vector<Item>& items, const std::vector<int>& order,
+                    const std::vector<char>& applied, const std::vector<int>& pool, int width,
+                    uint64_t fixed) {
+  if (width >= (int)pool.size()) {
+    uint64_t m = fixed;
+    for (int j : pool) m |= 1ull << j;
+    return m;
+  }
+  std::vector<uint64_t> cands;
+  {
+    std::vector<int> picked;
+    uint64_t seen = 0, in_pool = 0;
+    for (int j : pool) in_pool |= 1ull << j;
+    for (int i : order) {
+      if (applied[i] || items[i].kind != IT_DENSE) continue;
+      const uint64_t b = 1ull << items[i].a;
+      if ((b & in_pool) && !(b & seen)) {
+        seen |= b;
+        picked.push_back(items[i].a);
+        if ((int)picked.size() == width) break;
+      }
+    }
+    for (int j : pool) {
+      if ((int)picked.size() == width) break;
+      if (!(seen & (1ull << j))) {
+        seen |= 1ull << j;
+        picked.push_back(j);
+      }
+    }
+    uint64_t m = fixed;
+    for (int j : picked) m |= 1ull << j;
+    cands.push_back(m);
+  }
+  for (size_t s = 0; s + width <= pool.size(); ++s) {
+    uint64_t m = fixed;
+    for (int w = 0; w < width; ++w) m |= 1ull << pool[s + w];
+    cands.push_back(m);
+  }
+  uint64_t best = cands[0];
+  int best_d = -1;
+  for (uint64_t m : cands) {
+    const int d = scan(items, order, applied, m, nullptr);
+    if (d > best_d) {
+      best_d = d;
+      best = m;
+    }
+  }
+  return best;
+}
+
 struct PassBuilder {
   HostProgram& hp;
-  int nq, k;
+  int nq;
   int vpos[64];
+  int reg_of[64];
   std::vector<DTerm> pend_sign, pend_tab;
+  uint64_t pend_adj = 0;
   cd pend_u[64][4];
   bool pend_has[64];
 
   PassBuilder(HostProgram& h, int nq_, const std::vector<int>& tile_bits) : hp(h), nq(nq_) {
-    k = (int)tile_bits.size();
+    const int k = (int)tile_bits.size();
     uint64_t tmask = 0;
     for (int t = 0; t < k; ++t) {
       vpos[tile_bits[t]] = t;
@@ -162,7 +219,10 @@ struct PassBuilder {
     int r = 0;
     for (int j = 0; j < nq; ++j)
       if (!(tmask & (1ull << j))) vpos[j] = k + r++;
-    for (int j = 0; j < 64; ++j) pend_has[j] = false;
+    for (int j = 0; j < 64; ++j) {
+      pend_has[j] = false;
+      reg_of[j] = -1;
+    }
   }
 
   int add_table(const cd* t4) {
@@ -171,26 +231,39 @@ struct PassBuilder {
     return id;
   }
 
+  void add_sign(int p0, int p1) {
+    if (p0 > p1) std::swap(p0, p1);
+    if (p1 == p0 + 1) {
+      pend_adj ^= 1ull << p0;  // a repeated CZ cancels
+      return;
+    }
+    DTerm t{};
+    t.kind = TERM_SIGN;
+    t.p0 = (uint8_t)p0;
+    t.p1 = (uint8_t)p1;
+    pend_sign.push_back(t);
+  }
+
   void add_diag1(int j, cd d0, cd d1) {
     if (d0 == cd(1.0) && d1 == cd(1.0)) return;
+    if (d0 == cd(1.0) && d1 == cd(-1.0)) {
+      add_sign(vpos[j], vpos[j]);
+      return;
+    }
     DTerm t{};
     t.p0 = (uint8_t)vpos[j];
     t.p1 = (uint8_t)vpos[j];
-    if (d0 == cd(1.0) && d1 == cd(-1.0)) {
-      t.kind = TERM_SIGN;
-      pend_sign.push_back(t);
-      return;
-    }
     cd tab[4] = {d0, 0.0, 0.0, d1};  // index bit + 2 * index bit is 0 or 3
     t.kind = TERM_TABLE;
     t.tab = add_table(tab);
     pend_tab.push_back(t);
   }
 
-  void emit(int type, int t_bit, const cd* u) {
+  void emit(int type, int t_reg, const cd* u) {
     DOp op{};
     op.type = type;
-    op.t = t_bit;
+    op.t = t_reg;
+    op.sign_adj = pend_adj;
     op.term_begin = (int32_t)hp.terms.size();
     for (auto& d : pend_sign) hp.terms.push_back(d);
     op.term_sign_end = (int32_t)hp.terms.size();
@@ -198,6 +271,7 @@ struct PassBuilder {
     op.term_end = (int32_t)hp.terms.size();
     pend_sign.clear();
     pend_tab.clear();
+    pend_adj = 0;
     op.mat = -1;
     if (u) {
       op.mat = (int32_t)(hp.mats.size() / 4);
@@ -206,6 +280,8 @@ struct PassBuilder {
     hp.ops.push_back(op);
   }
 
+  bool pending_terms() const { return pend_adj || !pend_sign.empty() || !pend_tab.empty(); }
+
   void flush(int j) {
     if (!pend_has[j]) return;
     pend_has[j] = false;
@@ -213,7 +289,7 @@ struct PassBuilder {
     if (is_zero(u[1]) && is_zero(u[2])) {
       add_diag1(j, u[0], u[3]);
     } else {
-      emit(OP_DENSE, vpos[j], u);
+      emit(OP_DENSE, reg_of[j], u);
     }
   }
 
@@ -228,25 +304,19 @@ struct PassBuilder {
           mat_lmul(it.u, pend_u[it.a]);
         }
         return;
-      case IT_CZ: {
+      case IT_CZ:
         flush(it.a);
         flush(it.b);
-        DTerm t{};
-        t.kind = TERM_SIGN;
-        t.p0 = (uint8_t)vpos[it.a];
-        t.p1 = (uint8_t)vpos[it.b];
-        pend_sign.push_back(t);
+        add_sign(vpos[it.a], vpos[it.b]);
         return;
-      }
       case IT_VAR: {
         flush(it.a);
-        DTerm t{};
-        t.p0 = (uint8_t)vpos[it.a];
-        t.p1 = (uint8_t)(nq + it.slot);
         if (it.var_sign) {
-          t.kind = TERM_SIGN;
-          pend_sign.push_back(t);
+          add_sign(vpos[it.a], vpos[it.b]);
         } else {
+          DTerm t{};
+          t.p0 = (uint8_t)vpos[it.a];
+          t.p1 = (uint8_t)vpos[it.b];
           cd tab[4] = {it.d[0][0], it.d[0][1], it.d[1][0], it.d[1][1]};  // x + 2b
           t.kind = TERM_TABLE;
           t.tab = add_table(tab);
@@ -257,14 +327,30 @@ struct PassBuilder {
     }
   }
 
-  void finish() {
+  // Start a stage whose register bits are the tile bits of `qubits`.
+  void begin_stage(const std::vector<int>& qubits, DStage& st) {
+    for (int j = 0; j < 64; ++j) reg_of[j] = -1;
+    std::vector<int> pos;
+    for (int j : qubits) pos.push_back(vpos[j]);
+    std::sort(pos.begin(), pos.end());
+    for (int i = 0; i < 8; ++i) st.rb[i] = (int8_t)(i < (int)pos.size() ? pos[i] : 0);
+    for (int j : qubits)
+      for (size_t i = 0; i < pos.size(); ++i)
+        if (pos[i] == vpos[j]) reg_of[j] = (int)i;
+    st.op_begin = (int32_t)hp.ops.size();
+  }
+
+  // End a stage: every open matrix is emitted; diagonal factors may stay
+  // pending into the next stage of the same pass.
+  void end_stage(DStage& st, bool last) {
     for (int j = 0; j < nq; ++j) flush(j);
-    if (!pend_sign.empty() || !pend_tab.empty()) emit(OP_DIAG, 0, nullptr);
+    if (last && pending_terms()) emit(OP_DIAG, 0, nullptr);
+    st.op_end = (int32_t)hp.ops.size();
   }
 };
 
 void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector<int>& take,
-              const std::vector<int>& tile_bits, bool first) {
+              const std::vector<int>& tile_bits, bool first, int rb_max) {
   DPass P{};
   P.nq = hp.nq;
   P.k = (int)tile_bits.size();
@@ -273,94 +359,89 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
   int low = 0;
   while (low < P.k && tile_bits[low] == low) ++low;
   P.low = low;
-  for (int t = 0; t < P.k; ++t) P.tile_bit[t] = (int8_t)tile_bits[t];
+  P.rbits = std::max(1, std::min(rb_max, P.k - 5));
+  P.rbits = std::min(P.rbits, P.k);
   uint64_t tmask = 0;
-  for (int b : tile_bits) tmask |= 1ull << b;
+  for (int t = 0; t < P.k; ++t) {
+    P.tile_bit[t] = (int8_t)tile_bits[t];
+    tmask |= 1ull << tile_bits[t];
+    if (tile_bits[t] < hp.n_state) P.zero_tile |= 1u << t;
+  }
   int r = 0;
   for (int j = 0; j < P.nq; ++j)
-    if (!(tmask & (1ull << j))) P.rest_bit[r++] = (int8_t)j;
-  P.op_begin = (int32_t)hp.ops.size();
+    if (!(tmask & (1ull << j))) {
+      if (j < hp.n_state) P.zero_rest |= 1ull << r;
+      P.rest_bit[r++] = (int8_t)j;
+    }
+
+  // Stages: register-bit sets chosen like tiles, one level down.
+  P.stage_begin = (int32_t)hp.stages.size();
   PassBuilder pb(hp, hp.nq, tile_bits);
-  for (int i : take) pb.add(items[i]);
-  pb.finish();
-  P.op_end = (int32_t)hp.ops.size();
+  std::vector<char> done(items.size(), 1);
+  for (int i : take) done[i] = 0;
+  size_t left = take.size();
+  do {
+    const uint64_t regs = choose_set(items, take, done, tile_bits, P.rbits, 0);
+    std::vector<int> qubits;
+    for (int j : tile_bits)
+      if (regs & (1ull << j)) qubits.push_back(j);
+    std::vector<int> st_items;
+    scan(items, take, done, regs, &st_items);
+    DStage st{};
+    pb.begin_stage(qubits, st);
+    for (int i : st_items) {
+      pb.add(items[i]);
+      done[i] = 1;
+    }
+    left -= st_items.size();
+    if (st_items.empty() && left > 0) {  // cannot happen: the first pending item always fits
+      hp.nq = -1;
+      return;
+    }
+    pb.end_stage(st, left == 0);
+    hp.stages.push_back(st);
+  } while (left > 0);
+  P.stage_end = (int32_t)hp.stages.size();
   hp.passes.push_back(P);
 }
 
 }  // namespace
 
-HostProgram compile_program(const std::vector<Item>& items, int nq, int var_bits, int kmax,
-                            int low) {
+HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state, int kmax,
+                            int low, int rb_max) {
   HostProgram hp;
   hp.nq = nq;
-  hp.var_bits = var_bits;
+  hp.n_state = n_state;
   std::vector<char> applied(items.size(), 0);
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < items.size(); ++i) order[i] = (int)i;
+  std::vector<int> all_bits(nq);
+  for (int j = 0; j < nq; ++j) all_bits[j] = j;
   if (nq <= kmax) {
-    std::vector<int> take(items.size());
-    for (size_t i = 0; i < items.size(); ++i) take[i] = (int)i;
-    std::vector<int> tile(nq);
-    for (int j = 0; j < nq; ++j) tile[j] = j;
-    add_pass(hp, items, take, tile, true);
+    add_pass(hp, items, order, all_bits, true, rb_max);
     return hp;
   }
   low = std::min(low, kmax);
-  const int n_high = kmax - low;
+  std::vector<int> pool;
+  for (int j = low; j < nq; ++j) pool.push_back(j);
+  const uint64_t fixed = (low >= 64) ? ~0ull : ((1ull << low) - 1);
   size_t left = items.size();
   bool first = true;
   while (left > 0 || first) {
-    // Urgency of each high qubit: program position of its first pending dense item.
-    std::vector<long> urg(nq, (long)items.size() + 1);
-    {
-      uint64_t seen = 0;
-      for (size_t i = 0; i < items.size(); ++i) {
-        if (applied[i] || items[i].kind != IT_DENSE) continue;
-        const int a = items[i].a;
-        if (!(seen & (1ull << a))) {
-          seen |= 1ull << a;
-          urg[a] = (long)i;
-        }
-      }
-    }
-    std::vector<std::vector<int>> cands;
-    {
-      std::vector<int> hi;
-      for (int j = low; j < nq; ++j) hi.push_back(j);
-      std::stable_sort(hi.begin(), hi.end(), [&](int x, int y) { return urg[x] < urg[y]; });
-      hi.resize(n_high);
-      std::sort(hi.begin(), hi.end());
-      cands.push_back(hi);
-    }
-    for (int s = low; s + n_high <= nq; ++s) {
-      std::vector<int> hi;
-      for (int j = s; j < s + n_high; ++j) hi.push_back(j);
-      cands.push_back(hi);
-    }
-    int best = 0, best_dense = -1;
-    for (size_t c = 0; c < cands.size(); ++c) {
-      uint64_t tile = (low >= 64) ? ~0ull : ((1ull << low) - 1);
-      for (int j : cands[c]) tile |= 1ull << j;
-      const int d = scan_pass(items, applied, tile, nullptr);
-      if (d > best_dense) {
-        best_dense = d;
-        best = (int)c;
-      }
-    }
-    uint64_t tile = (1ull << low) - 1;
+    const uint64_t tile = choose_set(items, order, applied, pool, kmax - low, fixed);
     std::vector<int> tile_bits;
-    for (int j = 0; j < low; ++j) tile_bits.push_back(j);
-    for (int j : cands[best]) {
-      tile |= 1ull << j;
-      tile_bits.push_back(j);
-    }
+    for (int j = 0; j < nq; ++j)
+      if (tile & (1ull << j)) tile_bits.push_back(j);
     std::vector<int> take;
-    scan_pass(items, applied, tile, &take);
-    if (take.empty() && left > 0) {  // cannot happen: the first pending item is always applicable
+    scan(items, order, applied, tile, &take);
+    if (take.empty() && left > 0) {  // cannot happen: the first pending item always fits
       hp.nq = -1;
       return hp;
     }
     for (int i : take) applied[i] = 1;
     left -= take.size();
-    add_pass(hp, items, take, tile_bits, first);
+    add_pass(hp, items, take, tile_bits, first, rb_max);
+    if (hp.nq < 0) return hp;
     first = false;
   }
   return hp;

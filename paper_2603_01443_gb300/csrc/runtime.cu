@@ -133,6 +133,17 @@ void device_free(void* p) {
 int max_tile_bits(int precision) { return precision == CC_C128 ? 13 : 14; }
 int low_tile_bits(int precision) { return precision == CC_C128 ? 3 : 4; }
 
+int seg_tile_bits(int precision) {
+  // 2^13-amplitude tiles leave room for two CTAs per SM (measured ~11% faster
+  // than 2^14 on the 15-qubit, 64-variant segments)
+  int k = std::min(13, max_tile_bits(precision));
+  if (const char* e = std::getenv("CUTSIM_SEG_TILE_BITS")) {
+    const int v = std::atoi(e);
+    if (v >= low_tile_bits(precision) + 1 && v <= max_tile_bits(precision)) k = v;
+  }
+  return k;
+}
+
 int uncut_tile_bits(int precision) {
   int k = max_tile_bits(precision);
   if (const char* e = std::getenv("CUTSIM_UNCUT_TILE_BITS")) {
@@ -142,45 +153,64 @@ int uncut_tile_bits(int precision) {
   return k;
 }
 
-cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp) {
+ImageLayout append_program_image(const HostProgram& hp, int precision,
+                                 std::vector<unsigned char>& img) {
   const size_t rb = precision == CC_C128 ? 8 : 4;
-  const size_t o_pass = 0;
-  const size_t o_ops = align16(o_pass + hp.passes.size() * sizeof(DPass));
-  const size_t o_terms = align16(o_ops + hp.ops.size() * sizeof(DOp));
-  const size_t o_mats = align16(o_terms + hp.terms.size() * sizeof(DTerm));
-  const size_t o_tabs = align16(o_mats + hp.mats.size() * 2 * rb);
-  const size_t total = align16(o_tabs + hp.tabs.size() * 2 * rb);
-  std::vector<unsigned char> img(total, 0);
-  std::memcpy(img.data() + o_pass, hp.passes.data(), hp.passes.size() * sizeof(DPass));
-  std::memcpy(img.data() + o_ops, hp.ops.data(), hp.ops.size() * sizeof(DOp));
-  std::memcpy(img.data() + o_terms, hp.terms.data(), hp.terms.size() * sizeof(DTerm));
+  ImageLayout L;
+  L.base = (img.size() + 255) & ~size_t(255);
+  L.o_pass = 0;
+  L.o_stages = align16(L.o_pass + hp.passes.size() * sizeof(DPass));
+  L.o_ops = align16(L.o_stages + hp.stages.size() * sizeof(DStage));
+  L.o_terms = align16(L.o_ops + hp.ops.size() * sizeof(DOp));
+  L.o_mats = align16(L.o_terms + hp.terms.size() * sizeof(DTerm));
+  L.o_tabs = align16(L.o_mats + hp.mats.size() * 2 * rb);
+  L.end = align16(L.o_tabs + hp.tabs.size() * 2 * rb);
+  img.resize(L.base + L.end, 0);
+  unsigned char* p0 = img.data() + L.base;
+  std::memcpy(p0 + L.o_pass, hp.passes.data(), hp.passes.size() * sizeof(DPass));
+  std::memcpy(p0 + L.o_stages, hp.stages.data(), hp.stages.size() * sizeof(DStage));
+  std::memcpy(p0 + L.o_ops, hp.ops.data(), hp.ops.size() * sizeof(DOp));
+  std::memcpy(p0 + L.o_terms, hp.terms.data(), hp.terms.size() * sizeof(DTerm));
   auto put = [&](size_t off, const std::vector<cd>& v) {
     for (size_t i = 0; i < v.size(); ++i) {
       if (rb == 8) {
-        double* p = reinterpret_cast<double*>(img.data() + off) + 2 * i;
+        double* p = reinterpret_cast<double*>(p0 + off) + 2 * i;
         p[0] = v[i].real();
         p[1] = v[i].imag();
       } else {
-        float* p = reinterpret_cast<float*>(img.data() + off) + 2 * i;
+        float* p = reinterpret_cast<float*>(p0 + off) + 2 * i;
         p[0] = (float)v[i].real();
         p[1] = (float)v[i].imag();
       }
     }
   };
-  put(o_mats, hp.mats);
-  put(o_tabs, hp.tabs);
-  void* base = device_alloc_copy(img.data(), total);
-  if (!base) return fail(CC_ENOMEM, "device allocation of a gate program failed");
-  unsigned char* b = static_cast<unsigned char*>(base);
-  dp.base = base;
-  dp.bytes = total;
-  dp.passes_dev = b + o_pass;
-  dp.ops = reinterpret_cast<const DOp*>(b + o_ops);
-  dp.terms = reinterpret_cast<const DTerm*>(b + o_terms);
-  dp.mats = b + o_mats;
-  dp.tabs = b + o_tabs;
+  put(L.o_mats, hp.mats);
+  put(L.o_tabs, hp.tabs);
+  return L;
+}
+
+void bind_program(DeviceProgram& dp, const HostProgram& hp, unsigned char* dev_base,
+                  const ImageLayout& L) {
+  unsigned char* b = dev_base + L.base;
+  dp.base = nullptr;  // not owned
+  dp.bytes = L.end;
+  dp.passes_dev = b + L.o_pass;
+  dp.stages = reinterpret_cast<const DStage*>(b + L.o_stages);
+  dp.ops = reinterpret_cast<const DOp*>(b + L.o_ops);
+  dp.terms = reinterpret_cast<const DTerm*>(b + L.o_terms);
+  dp.mats = b + L.o_mats;
+  dp.tabs = b + L.o_tabs;
   dp.passes = hp.passes;
   dp.n_ops = (int)hp.ops.size();
+}
+
+cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp) {
+  std::vector<unsigned char> img;
+  const ImageLayout L = append_program_image(hp, precision, img);
+  void* base = device_alloc_copy(img.data(), img.size());
+  if (!base) return fail(CC_ENOMEM, "device allocation of a gate program failed");
+  bind_program(dp, hp, static_cast<unsigned char*>(base), L);
+  dp.base = base;  // owned
   return CC_OK;
 }
 
@@ -218,8 +248,7 @@ extern "C" cc_status cc_simulate_segments(const cc_plan* p, void* seg_buf, uint6
   const int ab = amp_bytes(p->precision);
   for (int i = 0; i < p->n_seg; ++i) {
     char* base = static_cast<char*>(seg_buf) + p->seg_off[i] * ab;
-    st = run_program(p->dprog[i], p->precision, base, int64_t(1) << p->seg_c[i],
-                     int64_t(1) << p->seg_q[i], stream);
+    st = run_program(p->dprog[i], p->precision, base, stream);
     if (st != CC_OK) return st;
   }
   return CC_OK;
@@ -248,31 +277,11 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
     return CC_OK;
   }
   const int32_t* tables = static_cast<const int32_t*>(p->tables_dev);
-  if (p->n_seg == 2) {
-    const auto& sg = p->stages[0];
-    MergeStage ms{sb + p->seg_off[0] * ab, sb + p->seg_off[1] * ab, psi, sg.qa, sg.qb,
-                  sg.K, sg.Z, int64_t(1) << (sg.qa + sg.qb), tables + sg.aidx_off,
-                  tables + sg.bidx_off};
-    int f = form;
-    if (f == CC_MERGE_AUTO) f = CC_MERGE_FMA;
-    if (f != CC_MERGE_FMA) {
-      if (ws_bytes < merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f) || !workspace) {
-        if (form != CC_MERGE_AUTO) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
-        f = CC_MERGE_FMA;
-      } else {
-        st = launch_merge_tc(ms, f, workspace, ws_bytes, stream);
-        if (st == CC_OK) return CC_OK;
-        if (st != CC_EUNSUPPORTED || form != CC_MERGE_AUTO) return st;
-        f = CC_MERGE_FMA;
-      }
-    }
-    return launch_merge_fma(ms, p->precision, stream);
-  }
-  // n >= 3: chain through two workspace buffers.
-  const uint64_t half = p->chain_ws_amps * ab;
-  if (!workspace || ws_bytes < 2 * half) return fail(CC_EBUFSIZE, "workspace too small for the chained merge");
-  if (form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3)
-    return fail(CC_EINVAL, "tensor-core forms merge two segments; use FMA or AUTO for n >= 3");
+  // n >= 3: the stages before the last chain through two workspace buffers;
+  // the last stage (Z = 1, the 2^q output) may use a tensor-core form.
+  const uint64_t half = p->n_seg >= 3 ? p->chain_ws_amps * ab : 0;
+  if (p->n_seg >= 3 && (!workspace || ws_bytes < 2 * half))
+    return fail(CC_EBUFSIZE, "workspace too small for the chained merge");
   char* w[2] = {static_cast<char*>(workspace), static_cast<char*>(workspace) + half};
   const void* acc = sb + p->seg_off[0] * ab;
   for (size_t s_i = 0; s_i < p->stages.size(); ++s_i) {
@@ -281,9 +290,34 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
     void* out = last ? psi : w[s_i & 1];
     MergeStage ms{acc, sb + p->seg_off[sg.seg] * ab, out, sg.qa, sg.qb, sg.K, sg.Z,
                   int64_t(1) << (sg.qa + sg.qb), tables + sg.aidx_off, tables + sg.bidx_off};
-    st = launch_merge_fma(ms, p->precision, stream);
-    if (st != CC_OK) return st;
-    acc = out;
+    if (!last) {
+      st = launch_merge_fma(ms, p->precision, stream);
+      if (st != CC_OK) return st;
+      acc = out;
+      continue;
+    }
+    // AUTO: the CUDA-core form while the merge is store-bound (K < 16) or too
+    // deep for 3xTF32 to hold the complex64 tolerance (K > 256), else 3xTF32.
+    int f = form;
+    if (f == CC_MERGE_AUTO)
+      f = (p->precision == CC_C64 && sg.K >= 16 && sg.K <= 256 && sg.qa >= 7 && sg.qb >= 7)
+              ? CC_MERGE_TF32X3
+              : CC_MERGE_FMA;
+    if (f != CC_MERGE_FMA) {
+      void* tc_ws = workspace ? static_cast<char*>(workspace) + 2 * half : nullptr;
+      const uint64_t tc_bytes = ws_bytes > 2 * half ? ws_bytes - 2 * half : 0;
+      if (!tc_ws || tc_bytes < merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f)) {
+        if (form != CC_MERGE_AUTO)
+          return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
+        f = CC_MERGE_FMA;
+      } else {
+        st = launch_merge_tc(ms, f, tc_ws, tc_bytes, stream);
+        if (st == CC_OK) return CC_OK;
+        if (st != CC_EUNSUPPORTED || form != CC_MERGE_AUTO) return st;
+        f = CC_MERGE_FMA;
+      }
+    }
+    return launch_merge_fma(ms, p->precision, stream);
   }
   return CC_OK;
 }
@@ -297,7 +331,7 @@ extern "C" cc_status cc_simulate_uncut(const cc_uncut* u, void* psi, uint64_t ps
     return fail(CC_EBUFSIZE, "psi too small");
   cc_status st = check_device();
   if (st != CC_OK) return st;
-  return run_program(u->dprog, u->precision, psi, 1, int64_t(1) << u->q, stream);
+  return run_program(u->dprog, u->precision, psi, stream);
 }
 
 extern "C" cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precision,

@@ -1,14 +1,19 @@
-// Gate passes over batched state vectors (subcircuit simulation, Algorithm 2,
-// and the uncut simulation T_orig).
+// Gate passes over state vectors (subcircuit simulation, Algorithm 2, and the
+// uncut simulation T_orig).
 //
-// One CTA owns one tile of 2^k amplitudes of one vector at a time: it loads
-// the tile into shared memory with 16-byte vector loads (the lowest tile bits
-// are contiguous vector bits, so every load is part of a >= 128-byte run),
-// applies the pass's fused operations in shared memory, and stores the tile
-// back in place.  The first pass of a program starts from |0...0> and reads
-// nothing.  When the whole vector fits one tile (segments of up to 14 qubits
-// in complex64, 13 in complex128) the program is a single pass and every
-// variant of a segment is one CTA.
+// One CTA owns one tile of 2^k amplitudes at a time.  It loads the tile into
+// shared memory with 16-byte vector loads (the lowest tile bits are
+// contiguous vector bits, so every load is part of a >= 128-byte run) -- or,
+// in a program's first pass, starts from |0...0> and reads nothing -- then
+// runs the pass's stages and stores the tile back in place.
+//
+// Stage: thread tau holds the 2^RB amplitudes whose tile index has its RB
+// register bits free and its other bits equal to tau's bits (deposited in
+// increasing order), so the 32 lanes of a warp cover low tile bits.  Each
+// fused op multiplies every held amplitude by its diagonal factors and then
+// applies a 2x2 matrix to one register bit, entirely in registers.  Between
+// stages the tile goes through shared memory, whose layout XORs the low four
+// index bits with higher ones to spread a warp's accesses over the banks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,37 +38,10 @@ struct CT<double> {
   static constexpr int PV = 1;
 };
 
-template <typename R>
-__device__ __forceinline__ void cmul(R& xr, R& xi, R yr, R yi) {
-  const R t = xr * yr - xi * yi;
-  xi = xr * yi + xi * yr;
-  xr = t;
-}
+namespace {
 
-// Multiply amplitude a (virtual index v) by the diagonal factors of an op.
-template <typename R>
-__device__ __forceinline__ void apply_terms(typename CT<R>::C& a, uint64_t v,
-                                            const DTerm* __restrict__ terms, int tb, int tse,
-                                            int te, const R* __restrict__ tabs) {
-  uint32_t sign = 0;
-  for (int i = tb; i < tse; ++i) {
-    const DTerm d = terms[i];
-    sign ^= (uint32_t)((v >> d.p0) & (v >> d.p1)) & 1u;
-  }
-  if (te > tse) {
-    R fr = R(1), fi = R(0);
-    for (int i = tse; i < te; ++i) {
-      const DTerm d = terms[i];
-      const int idx = (int)((v >> d.p0) & 1u) | ((int)((v >> d.p1) & 1u) << 1);
-      const R* t = tabs + 8 * d.tab + 2 * idx;
-      cmul(fr, fi, t[0], t[1]);
-    }
-    cmul(a.x, a.y, fr, fi);
-  }
-  if (sign) {
-    a.x = -a.x;
-    a.y = -a.y;
-  }
+__device__ __forceinline__ uint32_t swz(uint32_t l) {
+  return l ^ (((l >> 4) ^ (l >> 8) ^ (l >> 12)) & 15u);
 }
 
 // Vector offset of tile row h (the tile bits above the contiguous low run).
@@ -75,109 +53,283 @@ __device__ __forceinline__ int64_t tile_row_offset(uint32_t h, const int8_t* __r
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1024)
-    pass_kernel(typename CT<R>::C* __restrict__ state, int64_t vec_stride,
-                const DPass* __restrict__ pass, const DOp* __restrict__ ops,
-                const DTerm* __restrict__ terms, const R* __restrict__ mats,
-                const R* __restrict__ tabs, int64_t n_work, int64_t tiles_per_vec) {
+__device__ __forceinline__ void cmul(R& xr, R& xi, R yr, R yi) {
+  const R t = xr * yr - xi * yi;
+  xi = xr * yi + xi * yr;
+  xr = t;
+}
+
+// Slots j < 2^RB whose register bit i is set (i < 5).
+__host__ __device__ constexpr uint32_t slot_pattern(int i) {
+  return i == 0 ? 0xAAAAAAAAu : i == 1 ? 0xCCCCCCCCu : i == 2 ? 0xF0F0F0F0u
+       : i == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+
+// Per-stage view of where the register bits sit in the tile index.
+template <int RB>
+struct StageRegs {
+  int rb[RB];          // tile bit of register bit i (ascending)
+  uint32_t rmask;      // tile bits held in registers
+  uint32_t cons;       // bit i: register bits i and i+1 are adjacent tile bits
+  __device__ __forceinline__ int index_of(int p) const {  // -1 if tile bit p is not a register bit
+    return (p < 32 && ((rmask >> p) & 1u)) ? __popc(rmask & ((1u << p) - 1u)) : -1;
+  }
+};
+
+// Multiply the thread's 2^RB amplitudes by an op's diagonal factors.  With
+// v = c | r (c: the thread's fixed index bits, r: register bits, disjoint),
+// the CZ-type sign (-1)^{popcount(v & (v>>1) & adj)} splits into a constant,
+// a part linear in r and a part quadratic in adjacent register bits, which
+// gives the sign of every slot at once as a 32-bit mask over slots.
+template <typename R, int RB>
+__device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], const DOp& op,
+                                           uint64_t c, const StageRegs<RB>& sr,
+                                           const DTerm* __restrict__ terms,
+                                           const R* __restrict__ tabs) {
+  constexpr int N = 1 << RB;
+  constexpr uint32_t ALL = N >= 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
+  uint32_t smask = 0;
+  if (op.sign_adj) {
+    const uint64_t adj = op.sign_adj;
+    const uint64_t lin = ((c & adj) << 1) ^ ((c >> 1) & adj);
+    if (__popcll(c & (c >> 1) & adj) & 1) smask = ALL;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      if ((lin >> sr.rb[i]) & 1u) smask ^= slot_pattern(i);
+      if (i + 1 < RB && ((sr.cons >> i) & 1u) && ((adj >> sr.rb[i]) & 1u))
+        smask ^= slot_pattern(i) & slot_pattern(i + 1 < RB ? i + 1 : i);
+    }
+  }
+  for (int t = op.term_begin; t < op.term_sign_end; ++t) {
+    const DTerm d = terms[t];
+    const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
+    const uint32_t c0 = (uint32_t)(c >> d.p0) & 1u, c1 = (uint32_t)(c >> d.p1) & 1u;
+    uint32_t pa = 0, pb = 0;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      if (i == i0) pa = slot_pattern(i);
+      if (i == i1) pb = slot_pattern(i);
+    }
+    if (i0 < 0) pa = c0 ? ALL : 0u;
+    if (i1 < 0) pb = c1 ? ALL : 0u;
+    smask ^= pa & pb;
+  }
+  smask &= ALL;
+  if (smask) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const uint32_t sb = (smask << (31 - j)) & 0x80000000u;
+      if (sizeof(R) == 4) {
+        a[j].x = __int_as_float(__float_as_int((float)a[j].x) ^ (int)sb);
+        a[j].y = __int_as_float(__float_as_int((float)a[j].y) ^ (int)sb);
+      } else {
+        a[j].x = __longlong_as_double(__double_as_longlong((double)a[j].x) ^ ((long long)sb << 32));
+        a[j].y = __longlong_as_double(__double_as_longlong((double)a[j].y) ^ ((long long)sb << 32));
+      }
+    }
+  }
+  for (int t = op.term_sign_end; t < op.term_end; ++t) {
+    const DTerm d = terms[t];
+    const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
+    const int c0 = (int)((c >> d.p0) & 1u), c1 = (int)((c >> d.p1) & 1u);
+    const R* tb = tabs + 8 * d.tab;
+    const R f0r = tb[0], f0i = tb[1], f1r = tb[2], f1i = tb[3];
+    const R f2r = tb[4], f2i = tb[5], f3r = tb[6], f3i = tb[7];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const int x0 = i0 >= 0 ? (j >> i0) & 1 : c0;
+      const int x1 = i1 >= 0 ? (j >> i1) & 1 : c1;
+      const int idx = x0 | (x1 << 1);
+      const R fr = idx == 0 ? f0r : idx == 1 ? f1r : idx == 2 ? f2r : f3r;
+      const R fi = idx == 0 ? f0i : idx == 1 ? f1i : idx == 2 ? f2i : f3i;
+      cmul(a[j].x, a[j].y, fr, fi);
+    }
+  }
+}
+
+// Tile index of register slot j: lo[j & (2^L - 1)] | hi[j >> L], where the
+// low L = min(RB, 2) register bits index `lo` (which also carries the
+// thread's own bits) and the others index `hi`.
+template <int RB>
+struct SlotIndex {
+  static constexpr int L = RB < 2 ? RB : 2;
+  static constexpr int H = RB - L;
+  uint32_t lo[1 << L];
+  uint32_t hi[1 << H];
+  __device__ __forceinline__ uint32_t operator()(int j) const {
+    return lo[j & ((1 << L) - 1)] | hi[j >> L];
+  }
+};
+
+// 2x2 matrix on register bit RHO of every held pair.
+template <typename R, int RB, int RHO>
+__device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const R* __restrict__ m) {
+  using C = typename CT<R>::C;
+  constexpr int N = 1 << RB;
+  const R u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
+  const R u2r = m[4], u2i = m[5], u3r = m[6], u3i = m[7];
+#pragma unroll
+  for (int p = 0; p < N / 2; ++p) {
+    constexpr int lo = (1 << RHO) - 1;
+    const int j0 = ((p & ~lo) << 1) | (p & lo);
+    const int j1 = j0 | (1 << RHO);
+    const C a0 = a[j0], a1 = a[j1];
+    C b0, b1;
+    b0.x = u0r * a0.x - u0i * a0.y + u1r * a1.x - u1i * a1.y;
+    b0.y = u0r * a0.y + u0i * a0.x + u1r * a1.y + u1i * a1.x;
+    b1.x = u2r * a0.x - u2i * a0.y + u3r * a1.x - u3i * a1.y;
+    b1.y = u2r * a0.y + u2i * a0.x + u3r * a1.y + u3i * a1.x;
+    a[j0] = b0;
+    a[j1] = b1;
+  }
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(512)
+    stage_kernel(typename CT<R>::C* __restrict__ vec, const DPass* __restrict__ pass,
+                 const DStage* __restrict__ stages, const DOp* __restrict__ ops,
+                 const DTerm* __restrict__ terms, const R* __restrict__ mats,
+                 const R* __restrict__ tabs, int64_t n_tiles) {
   using C = typename CT<R>::C;
   using V = typename CT<R>::V;
   constexpr int PV = CT<R>::PV;
+  constexpr int N = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const DPass P = *pass;
   const uint32_t n = 1u << P.k;
-  const uint32_t half = n >> 1;
   const uint32_t nt = blockDim.x, tid = threadIdx.x;
   const uint32_t low_mask = (P.low >= 32) ? 0xffffffffu : ((1u << P.low) - 1u);
+  const uint32_t kmask = n - 1u;
   const int8_t* __restrict__ hi_bits = pass->tile_bit + P.low;
 
-  for (int64_t w = blockIdx.x; w < n_work; w += gridDim.x) {
-    const int64_t r = w / tiles_per_vec;
-    const int64_t T = w - r * tiles_per_vec;
-    C* vec = state + r * vec_stride;
-    const uint64_t vbase = ((uint64_t)T << P.k) | ((uint64_t)r << P.nq);
+  for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x) {
+    const uint64_t vbase = (uint64_t)T << P.k;
     int64_t gbase = 0;
     for (int b = 0; b < P.n_rest; ++b) gbase |= ((T >> b) & 1) << pass->rest_bit[b];
+    const bool rest_zero = (((uint64_t)T) & P.zero_rest) == 0;
 
-    if (P.init_zero) {
-      for (uint32_t l = tid; l < n; l += nt) {
-        C z;
-        z.x = (T == 0 && l == 0) ? R(1) : R(0);
-        z.y = R(0);
-        s[l] = z;
-      }
-    } else {
+    if (!P.init_zero) {
+#pragma unroll 4
       for (uint32_t u = tid; u < n / PV; u += nt) {
         const uint32_t l = u * PV;
         const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-        *reinterpret_cast<V*>(s + l) = *reinterpret_cast<const V*>(vec + g);
-      }
-    }
-    __syncthreads();
-
-    for (int o = P.op_begin; o < P.op_end; ++o) {
-      const DOp op = ops[o];
-      if (op.type == OP_DENSE) {
-        const R* m = mats + 8 * op.mat;
-        const R u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
-        const R u2r = m[4], u2i = m[5], u3r = m[6], u3i = m[7];
-        const int t = op.t;
-        const uint32_t lo = (1u << t) - 1u;
-        const bool has_terms = op.term_end > op.term_begin;
-        for (uint32_t p = tid; p < half; p += nt) {
-          const uint32_t l0 = ((p & ~lo) << 1) | (p & lo);
-          const uint32_t l1 = l0 | (1u << t);
-          C a0 = s[l0], a1 = s[l1];
-          if (has_terms) {
-            apply_terms<R>(a0, vbase | l0, terms, op.term_begin, op.term_sign_end, op.term_end, tabs);
-            apply_terms<R>(a1, vbase | l1, terms, op.term_begin, op.term_sign_end, op.term_end, tabs);
-          }
-          C b0, b1;
-          b0.x = u0r * a0.x - u0i * a0.y + u1r * a1.x - u1i * a1.y;
-          b0.y = u0r * a0.y + u0i * a0.x + u1r * a1.y + u1i * a1.x;
-          b1.x = u2r * a0.x - u2i * a0.y + u3r * a1.x - u3i * a1.y;
-          b1.y = u2r * a0.y + u2i * a0.x + u3r * a1.y + u3i * a1.x;
-          s[l0] = b0;
-          s[l1] = b1;
+        V val = *reinterpret_cast<const V*>(vec + g);
+        const uint32_t pl = swz(l);
+        if (PV == 2 && (pl & 1u)) {  // the swizzle swapped the pair
+          V sw = val;
+          reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
+                                                      reinterpret_cast<float4&>(val).w,
+                                                      reinterpret_cast<float4&>(val).x,
+                                                      reinterpret_cast<float4&>(val).y);
+          val = sw;
         }
-      } else {
-        for (uint32_t l = tid; l < n; l += nt) {
-          C a = s[l];
-          apply_terms<R>(a, vbase | l, terms, op.term_begin, op.term_sign_end, op.term_end, tabs);
-          s[l] = a;
-        }
+        *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = val;
       }
       __syncthreads();
     }
 
+    for (int si = P.stage_begin; si < P.stage_end; ++si) {
+      const DStage st = stages[si];
+      StageRegs<RB> sr;
+      sr.rmask = 0;
+      sr.cons = 0;
+      SlotIndex<RB> dep;
+#pragma unroll
+      for (int j = 0; j < (1 << SlotIndex<RB>::L); ++j) dep.lo[j] = 0;
+#pragma unroll
+      for (int j = 0; j < (1 << SlotIndex<RB>::H); ++j) dep.hi[j] = 0;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        sr.rb[i] = st.rb[i];
+        const uint32_t b = 1u << st.rb[i];
+        sr.rmask |= b;
+        if (i + 1 < RB && st.rb[i + 1 < RB ? i + 1 : i] == st.rb[i] + 1) sr.cons |= 1u << i;
+        if (i < SlotIndex<RB>::L) {
+#pragma unroll
+          for (int j = 0; j < (1 << SlotIndex<RB>::L); ++j)
+            if (j & (1 << i)) dep.lo[j] |= b;
+        } else {
+#pragma unroll
+          for (int j = 0; j < (1 << SlotIndex<RB>::H); ++j)
+            if (j & (1 << (i - SlotIndex<RB>::L))) dep.hi[j] |= b;
+        }
+      }
+      uint32_t base = 0;
+      {
+        uint32_t free_bits = kmask & ~sr.rmask, t = tid;
+        while (free_bits) {
+          const uint32_t p = __ffs(free_bits) - 1;
+          free_bits &= free_bits - 1;
+          base |= (t & 1u) << p;
+          t >>= 1;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < (1 << SlotIndex<RB>::L); ++j) dep.lo[j] |= base;
+      const uint64_t cfix = vbase | base;  // the thread's fixed index bits in this stage
+
+      C a[N];
+      if (P.init_zero && si == P.stage_begin) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          a[j].x = (rest_zero && (dep(j) & P.zero_tile) == 0) ? R(1) : R(0);
+          a[j].y = R(0);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[j] = s[swz(dep(j))];
+      }
+
+      for (int o = st.op_begin; o < st.op_end; ++o) {
+        const DOp op = ops[o];
+        if (op.sign_adj != 0 || op.term_end > op.term_begin)
+          apply_diag<R, RB>(a, op, cfix, sr, terms, tabs);
+        if (op.type == OP_DENSE) {
+          const R* m = mats + 8 * op.mat;
+          switch (op.t) {
+            case 0: dense_mat<R, RB, 0>(a, m); break;
+            case 1: if (RB > 1) dense_mat<R, RB, (RB > 1 ? 1 : 0)>(a, m); break;
+            case 2: if (RB > 2) dense_mat<R, RB, (RB > 2 ? 2 : 0)>(a, m); break;
+            case 3: if (RB > 3) dense_mat<R, RB, (RB > 3 ? 3 : 0)>(a, m); break;
+            default: if (RB > 4) dense_mat<R, RB, (RB > 4 ? 4 : 0)>(a, m); break;
+          }
+        }
+      }
+
+#pragma unroll
+      for (int j = 0; j < N; ++j) s[swz(dep(j))] = a[j];
+      __syncthreads();
+    }
+
+#pragma unroll 4
     for (uint32_t u = tid; u < n / PV; u += nt) {
       const uint32_t l = u * PV;
       const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-      *reinterpret_cast<V*>(vec + g) = *reinterpret_cast<const V*>(s + l);
+      const uint32_t pl = swz(l);
+      V val = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
+      if (PV == 2 && (pl & 1u)) {
+        V sw = val;
+        reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
+                                                    reinterpret_cast<float4&>(val).w,
+                                                    reinterpret_cast<float4&>(val).x,
+                                                    reinterpret_cast<float4&>(val).y);
+        val = sw;
+      }
+      *reinterpret_cast<V*>(vec + g) = val;
     }
     __syncthreads();
   }
 }
 
-namespace {
-
-int threads_for(int k) {
-  const int pairs = 1 << std::max(k - 1, 0);
-  return std::min(1024, std::max(32, pairs / 4));
-}
-
-template <typename R>
-cc_status launch_pass_t(const DeviceProgram& dp, int pi, void* state, int64_t n_vec,
-                        int64_t vec_stride, cudaStream_t stream) {
+template <typename R, int RB>
+cc_status launch_rb(const DeviceProgram& dp, int pi, void* state, cudaStream_t stream) {
   using C = typename CT<R>::C;
   const DPass& P = dp.passes[pi];
-  const int64_t tiles_per_vec = int64_t(1) << (P.nq - P.k);
-  const int64_t n_work = n_vec * tiles_per_vec;
-  if (n_work <= 0) return CC_OK;
+  const int64_t n_tiles = int64_t(1) << (P.nq - P.k);
   const size_t smem = sizeof(C) << P.k;
-  const int nt = threads_for(P.k);
-  auto kern = pass_kernel<R>;
+  const int nt = 1 << (P.k - P.rbits);
+  auto kern = stage_kernel<R, RB>;
   static int attr_done[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -188,29 +340,42 @@ cc_status launch_pass_t(const DeviceProgram& dp, int pi, void* state, int64_t n_
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem);
   occ = std::max(occ, 1);
-  const int64_t cap = (int64_t)num_sms() * occ;
-  const int64_t grid = std::min(n_work, cap);
+  const int64_t grid = std::min(n_tiles, (int64_t)num_sms() * occ);
   const DPass* dpass = reinterpret_cast<const DPass*>(
       reinterpret_cast<const char*>(dp.passes_dev) + sizeof(DPass) * pi);
   kern<<<(unsigned)grid, nt, smem, stream>>>(
-      reinterpret_cast<C*>(state), vec_stride, dpass, dp.ops, dp.terms,
-      reinterpret_cast<const R*>(dp.mats), reinterpret_cast<const R*>(dp.tabs), n_work,
-      tiles_per_vec);
+      reinterpret_cast<C*>(state), dpass, dp.stages, dp.ops, dp.terms,
+      reinterpret_cast<const R*>(dp.mats), reinterpret_cast<const R*>(dp.tabs), n_tiles);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
-    return fail(CC_ECUDA, std::string("pass kernel launch: ") + cudaGetErrorString(e));
+    return fail(CC_ECUDA, std::string("gate pass launch: ") + cudaGetErrorString(e));
   return CC_OK;
+}
+
+template <typename R>
+cc_status launch_pass(const DeviceProgram& dp, int pi, void* state, cudaStream_t stream) {
+  switch (dp.passes[pi].rbits) {
+    case 1: return launch_rb<R, 1>(dp, pi, state, stream);
+    case 2: return launch_rb<R, 2>(dp, pi, state, stream);
+    case 3: return launch_rb<R, 3>(dp, pi, state, stream);
+    case 4: return launch_rb<R, 4>(dp, pi, state, stream);
+    case 5:
+      return launch_rb<R, (sizeof(R) == 4 ? 5 : 4)>(dp, pi, state, stream);
+    default:
+      break;
+  }
+  return fail(CC_EINVAL, "pass has an unsupported register width");
 }
 
 }  // namespace
 
-cc_status run_program(const DeviceProgram& dp, int precision, void* state, int64_t n_vec,
-                      int64_t vec_stride, void* stream) {
+int reg_bits_max(int precision) { return precision == CC_C128 ? 4 : 5; }
+
+cc_status run_program(const DeviceProgram& dp, int precision, void* state, void* stream) {
   for (int pi = 0; pi < (int)dp.passes.size(); ++pi) {
     const cc_status st =
-        precision == CC_C128
-            ? launch_pass_t<double>(dp, pi, state, n_vec, vec_stride, (cudaStream_t)stream)
-            : launch_pass_t<float>(dp, pi, state, n_vec, vec_stride, (cudaStream_t)stream);
+        precision == CC_C128 ? launch_pass<double>(dp, pi, state, (cudaStream_t)stream)
+                             : launch_pass<float>(dp, pi, state, (cudaStream_t)stream);
     if (st != CC_OK) return st;
   }
   return CC_OK;

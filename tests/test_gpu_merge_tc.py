@@ -74,3 +74,15 @@ def test_tf32x3_refuses_deep_merges(cuda_lib):
     assert e.value.status == 3
     psi, _ = run(gates, 16, [8, 8], "auto")  # AUTO falls back to the FMA form
     assert rel_err(psi.cpu().numpy(), sv.simulate(16, gates)) <= TOL["c64"]
+
+
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "auto"])
+def test_tc_last_stage_of_chained_merge(cuda_lib, form):
+    # n = 3: the last stage (2^q output, K = 2^4 terms) runs on tensor cores
+    segs = [6, 7, 7]
+    gates = w.brickwork_cut(20, 10, 13, segs, [2, 4])
+    psi, plan = run(gates, 20, segs, form, "s_sdg")
+    ref = sv.simulate(20, gates)
+    tol = FORM_TOL.get(form, TOL["c64"])
+    assert rel_err(psi.cpu().numpy(), ref) <= tol
+    assert 1 - fidelity(psi.cpu().numpy(), ref) <= FID_TOL
