@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -48,6 +49,7 @@ constexpr int STG_BYTES = 32 * 128;  // one epilogue store box: 32 rows x 32 FP3
 constexpr int STG_TOTAL = 4 * 2 * STG_BYTES;  // 4 epilogue warps x 2 buffers
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STG_TOTAL + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int TMEM_COLS = 512;
+constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA on sm_103
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
 constexpr int64_t kTf32MaxTerms = 256;        // 3xTF32 stays within 2e-6 relative up to here
 
@@ -372,6 +374,251 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// ------------------------------------------------- row-operand-stationary form
+// For small K the whole row-operand tile (R_hi and R_lo of 128 rows, every K
+// block) fits in shared memory.  Each CTA then takes a contiguous run of
+// tiles -- runs of tiles_n tiles share one m -- keeps R resident while m is
+// unchanged and streams only the column operand, one 32 KB block (C_hi or
+// C_lo of one K block) per stage: two thirds of the operand bytes of the
+// streaming form per output tile for 3xTF32.
+constexpr int RS_C_STAGE = BN * KB_BYTES;  // 32 KB: one K block of C_hi or C_lo
+constexpr int RS_MAX_STAGES = 4;
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1)
+    merge_tc_rs_kernel(const __grid_constant__ CUtensorMap map_r,
+                       const __grid_constant__ CUtensorMap map_c,
+                       const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
+                       int kblocks, int n_stages, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* r_buf = smem;                               // [2][kblocks][R_TILE]: hi, lo
+  unsigned char* c_buf = smem + 2 * kblocks * R_TILE;        // [n_stages][RS_C_STAGE]
+  unsigned char* stg_base = c_buf + n_stages * RS_C_STAGE;   // epilogue staging
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
+  uint64_t* full = bars;                        // [RS_MAX_STAGES]
+  uint64_t* empty = bars + RS_MAX_STAGES;       // [RS_MAX_STAGES]
+  uint64_t* tfull = bars + 2 * RS_MAX_STAGES;   // [2]
+  uint64_t* tempty = tfull + 2;                 // [2]
+  uint64_t* r_full = tempty + 2;
+  uint64_t* r_empty = r_full + 1;
+  uint64_t* drain = r_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_n = n_cols / BN;
+  const int n_tiles = (n_rows / BM) * tiles_n;
+  const int t_begin = (int)(((int64_t)n_tiles * blockIdx.x) / gridDim.x);
+  const int t_end = (int)(((int64_t)n_tiles * (blockIdx.x + 1)) / gridDim.x);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < n_stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(r_full, 1);
+    mbar_init(r_empty, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_r)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c)) : "memory");
+      int s = 0;
+      uint32_t use = 0;
+      uint32_t r_use = 0;
+      int cur_m = -1;
+      bool issued[RS_MAX_STAGES] = {false, false, false, false};
+      uint32_t issued_parity[RS_MAX_STAGES] = {0, 0, 0, 0};
+      bool r_issued = false;
+      uint32_t r_parity = 0;
+      bool ok = true;
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+        if (m0 != cur_m) {
+          if (!mbar_wait(r_empty, (r_use & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t rb = smem_u32(r_full);
+          mbar_expect_tx(r_full, 2 * kblocks * R_TILE);
+          for (int kb = 0; kb < kblocks; ++kb) {
+            tma_load_2d(smem_u32(r_buf + kb * R_TILE), &map_r, rb, kb * kelem, m0);
+            tma_load_2d(smem_u32(r_buf + (kblocks + kb) * R_TILE), &map_r, rb, kb * kelem,
+                        n_rows + m0);
+          }
+          r_issued = true;
+          r_parity = r_use & 1;
+          ++r_use;
+          cur_m = m0;
+        }
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+          for (int part = 0; part < 2; ++part) {
+            if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full[s], RS_C_STAGE);
+            tma_load_2d(smem_u32(c_buf + s * RS_C_STAGE), &map_c, smem_u32(&full[s]), kb * kelem,
+                        part ? n_cols + n0 : n0);
+            issued[s] = true;
+            issued_parity[s] = use & 1;
+            if (++s == n_stages) {
+              s = 0;
+              ++use;
+            }
+          }
+        }
+      }
+      if (!ok) {  // let our own copies land before the CTA exits
+        for (int i = 0; i < n_stages; ++i)
+          if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
+        if (r_issued) mbar_drain(r_full, r_parity);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_value<KIND>();
+      int s = 0;
+      uint32_t use = 0, r_use = 0;
+      int cur_m = -1;
+      int iter = 0;
+      bool ok = true;
+      bool any_mma = false;
+      const uint32_t rh0 = smem_u32(r_buf), rl0 = smem_u32(r_buf + kblocks * R_TILE);
+      for (int t = t_begin; t < t_end && ok; ++t, ++iter) {
+        const int a = iter & 1;
+        const int m0 = (t / tiles_n) * BM;
+        if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (m0 != cur_m) {
+          if (cur_m >= 0) umma_commit(r_empty);  // the old R is free once its MMAs complete
+          if (!mbar_wait(r_full, r_use & 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          ++r_use;
+          cur_m = m0;
+          tc_fence_after();
+        }
+        const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+          const uint64_t rh = sdesc(rh0 + kb * R_TILE), rl = sdesc(rl0 + kb * R_TILE);
+          for (int part = 0; part < 2; ++part) {
+            if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t cd = sdesc(smem_u32(c_buf + s * RS_C_STAGE));
+#pragma unroll
+            for (int k = 0; k < KB_BYTES / 32; ++k) {
+              const uint64_t adv = (uint64_t)((k * 32) >> 4);
+              if (part == 0) {  // C_hi: R_hi * C_hi and R_lo * C_hi
+                umma<KIND>(dtmem, rh + adv, cd + adv, idesc, (kb | k) != 0);
+                umma<KIND>(dtmem, rl + adv, cd + adv, idesc, 1);
+              } else {          // C_lo: R_hi * C_lo
+                umma<KIND>(dtmem, rh + adv, cd + adv, idesc, 1);
+              }
+            }
+            any_mma = true;
+            umma_commit(&empty[s]);
+            if (++s == n_stages) {
+              s = 0;
+              ++use;
+            }
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[a]);
+      }
+      if (!ok && any_mma) {
+        umma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
+    int buf = 0;
+    int iter = 0;
+    for (int t = t_begin; t < t_end; ++t, ++iter) {
+      const int a = iter & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tbase + (uint32_t)(c * 32), r);
+        unsigned char* sb = stg + buf * STG_BYTES;
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
+          *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile(
+              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                  reinterpret_cast<uint64_t>(&map_out)),
+              "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        buf ^= 1;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- operand split
 __device__ __forceinline__ void split_store(uint16_t* hi, uint16_t* lo, float v) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -450,6 +697,16 @@ EncodeTiledFn encode_fn() {
     cudaGetLastError();
   }
   return fn;
+}
+
+// CUTSIM_TC_STATIONARY=1 selects the row-operand-stationary form where it
+// applies.  It reads a third fewer operand bytes but keeps only 2-4 x 32 KB of
+// loads in flight per SM against the streaming form's 2 x 96 KB, and on GB300
+// the streaming form is faster (3xTF32, K = 64, q = 30: 2.86 vs 3.10 ms), so
+// it is the default.
+bool tc_stationary_requested() {
+  const char* e = std::getenv("CUTSIM_TC_STATIONARY");
+  return e && e[0] == '1';
 }
 
 int kr_of(int64_t K, int form) {
@@ -540,21 +797,34 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (output) failed");
   }
 
-  auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
-                                      : merge_tc_kernel<CC_MERGE_TF32X3>;
   static int attr_done[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !(attr_done[dev] & (1 << form))) {
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
     cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr_done[dev] |= 1 << form;
+    cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    attr_done[dev] = 1;
   }
   const int n_rows = (int)NB, n_cols = (int)(2 * NA);
   const int n_tiles = (n_rows / BM) * (n_cols / BN);
   const int grid = std::min(n_tiles, num_sms());
   const int kblocks = KR * eb / KB_BYTES;
-  kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, err);
+  // Row-operand-stationary form when the 128-row R tile (hi and lo, all K
+  // blocks) leaves room for at least two 32 KB column stages.
+  const int r_bytes = 2 * kblocks * R_TILE;
+  const int rs_stages = std::min(RS_MAX_STAGES, (SMEM_LIMIT - 1024 - 256 - STG_TOTAL - r_bytes) / RS_C_STAGE);
+  if (rs_stages >= 2 && tc_stationary_requested()) {
+    const int smem_rs = r_bytes + rs_stages * RS_C_STAGE + STG_TOTAL + 1024 + 256;
+    auto kern = form == CC_MERGE_BF16X3 ? merge_tc_rs_kernel<CC_MERGE_BF16X3>
+                                        : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
+    kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
+  } else {
+    auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
+                                        : merge_tc_kernel<CC_MERGE_TF32X3>;
+    kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, err);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(e));
   return CC_OK;

@@ -86,3 +86,17 @@ def test_tc_last_stage_of_chained_merge(cuda_lib, form):
     tol = FORM_TOL.get(form, TOL["c64"])
     assert rel_err(psi.cpu().numpy(), ref) <= tol
     assert 1 - fidelity(psi.cpu().numpy(), ref) <= FID_TOL
+
+
+@pytest.mark.parametrize("stationary", ["0", "1"])
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("segs,c", [([8, 9], 5), ([10, 10], 6), ([9, 9], 7)])
+def test_tc_forms_stationary_and_streaming(cuda_lib, monkeypatch, stationary, form, segs, c):
+    # the streaming kernel (default) and the row-operand-stationary kernel
+    # (opt-in where R fits) must agree with the oracle alike
+    monkeypatch.setenv("CUTSIM_TC_STATIONARY", stationary)
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 12, 31 + c, segs, c)
+    psi, _ = run(gates, q, segs, form)
+    ref = sv.simulate(q, gates)
+    assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
