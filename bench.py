@@ -479,7 +479,7 @@ def main(argv=None):
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        "tf32x3" if (a.prec == "c64" and 16 <= K <= 256 and a.n == 2) else "fma")
+        "tf32x3" if (a.prec == "c64" and 16 <= K <= 64) else "fma")
     if tc_form in ("tf32x3", "bf16x3"):
         # three split products of the real GEMM: 3 x 8K flops per output amplitude
         tc_flops = 3.0 * 8 * K * n_amp

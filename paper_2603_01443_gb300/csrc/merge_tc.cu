@@ -51,7 +51,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STG_TOTAL + 1024 /*align*/ + 2
 constexpr int TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA on sm_103
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
-constexpr int64_t kTf32MaxTerms = 256;        // 3xTF32 stays within 2e-6 relative up to here
+constexpr int64_t kTf32MaxTerms = 64;        // 3xTF32 stays within 2e-6 relative up to here
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -735,7 +735,7 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   if (need == 0) return fail(CC_EUNSUPPORTED, "tensor-core merge shape unsupported");
   if (form == CC_MERGE_TF32X3 && st.K > kTf32MaxTerms)
     return fail(CC_EUNSUPPORTED,
-                "3xTF32 merge is limited to 256 terms: beyond that the FP32 accumulation in the "
+                "3xTF32 merge is limited to 64 terms: beyond that the FP32 accumulation in the "
                 "tensor core exceeds the complex64 tolerance");
   if (ws_bytes < need) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
   EncodeTiledFn enc = encode_fn();

@@ -61,6 +61,7 @@ def test_q30_n2_c6_bench_workload_sampled_and_vs_uncut(cuda_lib):
     (30, 2, 6, "projector", "c64", "bf16x3"),
     (30, 2, 2, "s_sdg", "c64", "auto"),
     (28, 2, 8, "s_sdg", "c64", "auto"),
+    (28, 2, 7, "projector", "c64", "auto"),
     (28, 3, 6, "s_sdg", "c64", "auto"),
     (30, 3, 8, "projector", "c64", "auto"),
     (26, 2, 4, "projector", "c64", "fma"),
