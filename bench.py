@@ -51,8 +51,10 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["boundary"], default=None,
+    p.add_argument("--sweep", choices=["boundary", "batch"], default=None,
                    help="run a measurement sweep instead of the single-line benchmark")
+    p.add_argument("--sweep-cmax", type=int, default=20,
+                   help="largest c_total of the boundary sweep (capped by the depth)")
     p.add_argument("--sweep-both", action="store_true",
                    help="sweep complex64 and complex128")
     return p.parse_args(argv)
@@ -95,13 +97,20 @@ def kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no measured figure; nominal)
+
+
+def traffic_key(kernel, a):
+    return f"{kernel}@q{a.q}_d{a.depth}_n{a.n}_c{a.ctotal}_{a.prec}"
+
+
+def recorded_traffic(kernel, a):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source and this workload (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            d = json.load(f)[kernel]
+            d = json.load(f)[traffic_key(kernel, a)]
     except Exception:
         return None
     try:
@@ -160,7 +169,7 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline_sample(a, n_sub_sample=48, n_amp=1 << 21):
+def cpu_baseline_sample(a, n_sub_sample=96, n_amp=1 << 22):
     """Time the FP64 oracle on a bounded sample of the workload, in a fresh
     single-threaded interpreter, and extrapolate to T_cut seconds."""
     code = r"""
@@ -260,7 +269,8 @@ def reference_arm(a):
 def sweep_boundary(a):
     """Speedup-boundary sweep (the paper's Sec. V.B experiment on this GPU):
     q in {16, 20, 24}, depth in {8, 16, 32}, n = 2 equal segments, c_total
-    from 0 to min(12, depth); per point the stage times and
+    from 0 to min(--sweep-cmax, depth), stopping two points after the cut form
+    stops winning; per point the stage times and
     Delta = (T_cut - T_orig) / T_orig.  One JSON line per point, then a
     summary with the largest c_total that still gives Delta < 0 per (q, depth)
     next to Eq. 13's c_total < q / 2."""
@@ -278,7 +288,12 @@ def sweep_boundary(a):
         for q in (16, 20, 24):
             for depth in (8, 16, 32):
                 best = None
-                for c in range(0, min(12, depth) + 1):
+                above = 0
+                for c in range(0, min(a.sweep_cmax, depth) + 1):
+                    if above >= 2:  # past the crossover: the merge only grows from here
+                        break
+                    if q - q // 2 + c > 28:  # keep each segment block within 2^28 amplitudes
+                        break
                     gates = w.brickwork_cut(q, depth, a.seed, [q // 2, q - q // 2], c)
                     packed = capi.GateArray(gates)
                     probe = api.CutPlan(packed, q, [q // 2, q - q // 2], a.decomp, prec)
@@ -319,10 +334,118 @@ def sweep_boundary(a):
                                       "delta": delta}), flush=True)
                     if delta < 0:
                         best = c
+                        above = 0
+                    else:
+                        above += 1
                     del seg, psi, ws, psi_u
                 summary.setdefault(prec, {}).setdefault(str(q), {})[str(depth)] = best
     print(json.dumps({"sweep": "boundary", "largest_c_total_with_speedup": summary,
                       "eq13_threshold": {str(q): q / 2 for q in (16, 20, 24)}}))
+    return 0
+
+
+def sweep_batch(a, n_circ=64):
+    """Batched uneven workload: n_circ independent random brickwork circuits
+    (q uniform in 16..26, depth in {8, 16, 32}, n in {2, 3} unequal segments,
+    c_total 2..6).  All segment passes of all circuits run in one persistent
+    launch and the merges in one launch per chain level, replayed from a CUDA
+    graph after the autotuner picked the segment tile width and merge tile
+    height.  Reported next to the plain form: the same circuits one after
+    another through the one-circuit API (plans made beforehand, AUTO merge).
+    Latency of circuit i in the batch = completion of its merge minus the
+    start of the persistent launch (device %globaltimer)."""
+    import numpy as np
+    import torch
+
+    import workload as w
+    from paper_2603_01443_gb300 import api, capi
+
+    torch.cuda.set_device(0)
+    items = w.uneven_batch(n_circ, a.seed)
+    circ = [(capi.GateArray(it.gates), it.q, it.seg_sizes) for it in items]
+    t0 = time.perf_counter()
+    b = api.Batch(circ, a.decomp, a.prec)
+    t_plan = time.perf_counter() - t0
+    seg, psi, ws = b.alloc_buffers()
+    stamps = b.alloc_stamps()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, stream, reps):
+        for _ in range(max(1, a.warmup)):
+            fn()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    cur = torch.cuda.current_stream()
+    default_info = dict(b.info)
+    t_default = timed(lambda: b.run(seg, psi, ws, None, cur), cur, a.steps)
+    table = b.autotune(seg, psi, ws, cur)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    b.capture(seg, psi, ws, stamps, stream=s)
+    t_batch = timed(lambda: b.launch(s), s, a.steps)
+    b.launch(s)
+    s.synchronize()
+    capi.check(capi.lib().cc_sync(s.cuda_stream), "cc_sync")
+    st = stamps.cpu().numpy().view(np.uint64).astype(np.float64)
+    lat = (st[1:] - st[0]) / 1e9
+
+    # the plain form: one circuit at a time through the one-circuit API
+    plans = [api.CutPlan(g, q, segs, a.decomp, a.prec) for g, q, segs in circ]
+    bufs = [(p.alloc_seg_buf(), p.alloc_psi(), p.alloc_workspace()) for p in plans]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_circ + 1)]
+
+    def sequential():
+        evs[0].record(cur)
+        for i, (p, (sg, ps, wk)) in enumerate(zip(plans, bufs)):
+            p.simulate_segments(sg, cur)
+            p.merge(sg, ps, wk, "auto", cur)
+            evs[i + 1].record(cur)
+
+    for _ in range(max(1, a.warmup)):
+        sequential()
+    torch.cuda.synchronize()
+    seq_tot, seq_dur, seq_done = [], [], []
+    for _ in range(a.steps):
+        sequential()
+        evs[-1].synchronize()
+        seq_tot.append(evs[0].elapsed_time(evs[-1]) / 1e3)
+        seq_dur.append([evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(n_circ)])
+        seq_done.append([evs[0].elapsed_time(evs[i + 1]) / 1e3 for i in range(n_circ)])
+    dur = np.mean(np.array(seq_dur), axis=0)
+    done = np.mean(np.array(seq_done), axis=0)
+    worst = 0.0
+    for i, (_, (_, ps, _)) in enumerate(zip(plans, bufs)):
+        r = api.compare(b.psi_view(psi, i), ps, a.prec)
+        worst = max(worst, r["max_abs_diff"] / r["max_abs_b"])
+    n_amp = sum(1 << it.q for it in items)
+    t_seq = statistics.mean(seq_tot)
+    print(json.dumps({
+        "sweep": "batch", "n_circ": n_circ, "precision": a.prec, "decomp": a.decomp,
+        "workload": "uneven_batch(64): q 16..26, depth {8,16,32}, n {2,3} unequal, c_total 2..6",
+        "n_sub": b.info["n_sub"], "amplitudes": n_amp, "plan_s": t_plan,
+        "default": {"tile_bits": default_info["tile_bits"], "merge_rows": default_info["merge_rows"],
+                    "batch_s": t_default},
+        "autotune": table, "chosen": {"tile_bits": b.info["tile_bits"],
+                                      "merge_rows": b.info["merge_rows"]},
+        "persistent_launch": {"grid": b.info["grid"], "block": b.info["block"],
+                              "jobs": b.info["n_jobs"], "tiles": b.info["n_items"]},
+        "batch_s": t_batch, "circuits_per_s": n_circ / t_batch,
+        "output_gbs": n_amp * api.AMP_BYTES[a.prec] / t_batch / 1e9,
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "sequential": {"total_s": t_seq, "circuits_per_s": n_circ / t_seq,
+                       "duration_p50_s": float(np.percentile(dur, 50)),
+                       "duration_p99_s": float(np.percentile(dur, 99)),
+                       "completion_p50_s": float(np.percentile(done, 50)),
+                       "completion_p99_s": float(np.percentile(done, 99))},
+        "speedup_vs_sequential": t_seq / t_batch,
+        "max_rel_diff_vs_sequential": worst,
+    }), flush=True)
     return 0
 
 
@@ -332,6 +455,8 @@ def main(argv=None):
         return reference_arm(a)
     if a.sweep == "boundary":
         return sweep_boundary(a)
+    if a.sweep == "batch":
+        return sweep_batch(a)
 
     import torch
     import torch.distributed as dist
@@ -462,7 +587,7 @@ def main(argv=None):
     pass_s = orig_dev / n_pass
     pass_gbs = pass_bytes / pass_s / 1e9
     merge_rf = {"bound": "hbm", "achieved": merge_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": merge_gbs / hbm, "traffic": recorded_traffic("merge"),
+                "frac": merge_gbs / hbm, "traffic": None,
                 "kernel": "cut_merge", "bytes_per_launch": merge_bytes,
                 "launch_s": mean["merge"], "peak_source": peak_src}
     # The uncut passes do 8 FMA (16 flops) per amplitude for every dense
@@ -471,15 +596,26 @@ def main(argv=None):
     n_dense = sum(1 for g in gates if g.kind in ("U3", "H", "X")) + \
         2 * sum(1 for g in gates if g.kind == "CX")
     uncut_flops = 16.0 * n_dense * n_amp
-    fp32_peak = fp32_peak_tflops()
+    if a.prec == "c64":
+        alu_peak, alu_src = fp32_peak_tflops(), "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+    else:  # complex128 runs on the FP64 pipes
+        alu_peak, alu_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 (no measured FP64 peak)"
     pass_tf = uncut_flops / n_pass / pass_s / 1e12
-    pass_rf = {"bound": "alu", "achieved": pass_tf, "peak": fp32_peak, "unit": "TFLOP/s",
-               "frac": pass_tf / fp32_peak, "traffic": recorded_traffic("uncut_pass"),
+    pass_rf = {"bound": "alu", "achieved": pass_tf, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": pass_tf / alu_peak, "traffic": recorded_traffic("uncut_pass", a),
                "kernel": "stage_kernel (uncut passes)", "flops_per_launch": uncut_flops / n_pass,
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
-               "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+               "peak_source": alu_src}
     tc_form = a.merge_form if a.merge_form != "auto" else (
         "tf32x3" if (a.prec == "c64" and 16 <= K <= 64) else "fma")
+    merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
+    if tc_form == "fma":
+        # complex FMA merge: 8 flops per term per output amplitude on the ALU pipes
+        fma_flops = 8.0 * K * n_amp
+        merge_rf["alu"] = {"achieved": fma_flops / mean["merge"] / 1e12, "peak": alu_peak,
+                           "unit": "TFLOP/s",
+                           "frac": fma_flops / mean["merge"] / 1e12 / alu_peak,
+                           "peak_source": alu_src}
     if tc_form in ("tf32x3", "bf16x3"):
         # three split products of the real GEMM: 3 x 8K flops per output amplitude
         tc_flops = 3.0 * 8 * K * n_amp

@@ -232,6 +232,105 @@ cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision, const int
 cc_status cc_gather_static(const void* psi, int64_t n_amp, int32_t precision, const int64_t* idx,
                            int64_t n_idx, void* out, void* stream);
 
+/* ------------------------------------------------------------- batching
+ * Batched cut simulation of many independent circuits.  The paper runs the
+ * subcircuits of one circuit one after another and names running them in
+ * parallel as a way to lower the effective threshold further (Sec. VI); it
+ * also studies unequal partitions (supplementary Fig. 7).  A batch takes
+ * n_circ circuits, each with its own q, gates and contiguous partition
+ * (segments may differ in size), and runs
+ *   - every pass of every segment program of every circuit in ONE persistent
+ *     launch: a device queue of (job, tile) items, jobs ordered by pass
+ *     number, each job waiting (bounded) until the pass before it on the same
+ *     segment has stored all its tiles;
+ *   - then one merge launch per chain level (one for n_seg = 2, two for
+ *     n_seg = 3, ...), each over the output tiles of every circuit's stage at
+ *     that level, on CUDA cores (CC_MERGE_FMA arithmetic).
+ * The whole sequence can be captured once into a CUDA graph and replayed.
+ *
+ * Buffers (caller-owned device memory, 16-byte aligned): seg_buf holds every
+ * circuit's segment vectors, psi every circuit's 2^q output (circuit i at
+ * amplitude psi_offset(i), see cc_batch_circuit), workspace the chained-merge
+ * intermediates of circuits with n_seg >= 3.  Sizes come from cc_batch_info.
+ */
+typedef struct cc_batch cc_batch;  /* opaque, library-owned */
+
+typedef struct {
+  int32_t n_circ;
+  int32_t precision;
+  int32_t tile_bits;       /* largest segment tile (bits) the programs were planned with */
+  int32_t merge_rows;      /* output rows per merge tile (16 or 32; complex128 always 32) */
+  int32_t n_jobs;          /* segment passes in the persistent launch */
+  int32_t merge_levels;    /* merge launches per run */
+  int64_t n_items;         /* tiles in the persistent launch's queue */
+  int64_t n_sub;           /* subcircuits (variants) over all circuits */
+  uint64_t seg_buf_bytes;
+  uint64_t psi_bytes;
+  uint64_t workspace_bytes;
+  int32_t block;           /* threads per CTA of the persistent launch */
+  int32_t grid;            /* CTAs of the persistent launch */
+} cc_batch_info_t;
+
+/* cc_batch_create -- plan every circuit (Algorithm 1 per circuit) and build
+ * the batched launch.
+ *   gates             all circuits' gates, circuit i at gates[gate_offset[i] ..
+ *                     gate_offset[i+1]); host memory, read during the call.
+ *   gate_offset[n_circ+1], q[n_circ], seg_sizes[seg_offset[n_circ]],
+ *   seg_offset[n_circ+1]: host arrays; circuit i's segments are
+ *                     seg_sizes[seg_offset[i] .. seg_offset[i+1]), at least 2,
+ *                     summing to q[i].
+ *   tile_bits         0 = the default segment tile, else 5..14 (complex64) or
+ *                     4..13 (complex128): the largest tile of a segment pass.
+ *   merge_rows        0 = 32, else 16 or 32.
+ * Each circuit obeys the rules of cc_plan_create.  n_circ in 1..65536.
+ * Errors: those of cc_plan_create (naming the circuit), CC_EINVAL for
+ * malformed offsets or a circuit with fewer than 2 segments. */
+cc_status cc_batch_create(const cc_gate* gates, const int64_t* gate_offset, int32_t n_circ,
+                          const int32_t* q, const int32_t* seg_sizes, const int32_t* seg_offset,
+                          int32_t decomp, int32_t precision, int32_t tile_bits,
+                          int32_t merge_rows, cc_batch** out);
+
+cc_status cc_batch_info(const cc_batch* b, cc_batch_info_t* info);
+
+/* cc_batch_circuit -- circuit i's output offset in psi (amplitudes), q,
+ * c_total and its number of subcircuits. */
+cc_status cc_batch_circuit(const cc_batch* b, int32_t i, int64_t* psi_offset, int32_t* q,
+                           int32_t* c_total, int64_t* n_sub);
+
+/* cc_batch_run -- simulate and merge every circuit of the batch (asynchronous
+ * on `stream`).  stamps: optional device array of n_circ + 1 uint64 that
+ * receives %globaltimer (ns) when the persistent launch takes its first tile
+ * (stamps[0]) and when circuit i's output is complete (stamps[1 + i]).
+ * Errors: CC_EBUFSIZE, CC_EINVAL; a dependency wait that gives up is
+ * reported by cc_sync as CC_ETIMEOUT. */
+cc_status cc_batch_run(const cc_batch* b, void* seg_buf, uint64_t seg_buf_bytes, void* psi,
+                       uint64_t psi_bytes, void* workspace, uint64_t workspace_bytes,
+                       uint64_t* stamps, void* stream);
+
+/* cc_batch_capture -- record cc_batch_run with these buffers into a CUDA
+ * graph owned by the batch (replacing any earlier one).  `stream` must be a
+ * stream other than the legacy NULL stream; nothing runs during the call.
+ * The buffers are baked into the graph and must outlive it. */
+cc_status cc_batch_capture(cc_batch* b, void* seg_buf, uint64_t seg_buf_bytes, void* psi,
+                           uint64_t psi_bytes, void* workspace, uint64_t workspace_bytes,
+                           uint64_t* stamps, void* stream);
+
+/* cc_batch_launch -- replay the captured graph on `stream` (CC_EINVAL if none). */
+cc_status cc_batch_launch(const cc_batch* b, void* stream);
+
+/* cc_batch_autotune -- time cc_batch_run on these buffers for every segment
+ * tile width in 10..max (complex64 14, complex128 13) and every merge tile
+ * height (16, 32; complex128 32 only), re-planning the batch for each, and
+ * keep the fastest.  Writes up to max_out candidates (tile bits, merge rows,
+ * mean ms over 3 timed runs after one warm-up) and their count to *n_out.
+ * Synchronizes `stream`; any captured graph is discarded. */
+cc_status cc_batch_autotune(cc_batch* b, void* seg_buf, uint64_t seg_buf_bytes, void* psi,
+                            uint64_t psi_bytes, void* workspace, uint64_t workspace_bytes,
+                            void* stream, int32_t max_out, int32_t* n_out, int32_t* tile_bits,
+                            int32_t* merge_rows, float* ms);
+
+void cc_batch_destroy(cc_batch* b);
+
 /* cc_sync -- synchronize `stream`, then report CC_ETIMEOUT if any kernel of
  * this library on the current device gave up a bounded wait since the last
  * cc_sync (the flag is cleared by the call).  Asynchronous entry points

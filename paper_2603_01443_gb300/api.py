@@ -195,3 +195,112 @@ def cut_simulate(gates, q, seg_sizes, decomp="projector", precision="c64", form=
     plan.simulate_segments(seg, stream)
     plan.merge(seg, psi, ws, form, stream)
     return psi, plan
+
+
+class Batch:
+    """Many independent circuits cut, simulated and merged together.
+
+    ``circuits`` is a sequence of ``(gates, q, seg_sizes)``; gates may be a
+    sequence of gates or a ``capi.GateArray``.  All segment passes of all
+    circuits run in one persistent launch, then one merge launch per chain
+    level; ``capture`` records that sequence into a CUDA graph."""
+
+    def __init__(self, circuits, decomp: str = "projector", precision: str = "c64",
+                 tile_bits: int = 0, merge_rows: int = 0):
+        L = capi.lib()
+        self.precision = precision
+        arrays = [g if isinstance(g, capi.GateArray) else capi.GateArray(g) for g, _, _ in circuits]
+        n_g = sum(a.n for a in arrays)
+        gates = (capi.CGate * max(n_g, 1))()
+        goff = (c_int64 * (len(circuits) + 1))()
+        at = 0
+        for i, a in enumerate(arrays):
+            goff[i] = at
+            ctypes.memmove(ctypes.byref(gates, at * ctypes.sizeof(capi.CGate)), a.data,
+                           a.n * ctypes.sizeof(capi.CGate))
+            at += a.n
+        goff[len(circuits)] = at
+        qs = (c_int32 * len(circuits))(*[q for _, q, _ in circuits])
+        sizes = [s for _, _, segs in circuits for s in segs]
+        seg_sizes = (c_int32 * max(len(sizes), 1))(*sizes)
+        soff = (c_int32 * (len(circuits) + 1))()
+        at = 0
+        for i, (_, _, segs) in enumerate(circuits):
+            soff[i] = at
+            at += len(segs)
+        soff[len(circuits)] = at
+        h = c_void_p()
+        capi.check(L.cc_batch_create(gates, goff, len(circuits), qs, seg_sizes, soff,
+                                     capi.DECOMP[decomp], capi.PRECISION[precision], tile_bits,
+                                     merge_rows, byref(h)), "cc_batch_create")
+        self._h = h
+        self.n_circ = len(circuits)
+        self._refresh_info()
+        self.circuits = []
+        for i in range(self.n_circ):
+            off, q, c, ns = c_int64(), c_int32(), c_int32(), c_int64()
+            capi.check(L.cc_batch_circuit(self._h, i, byref(off), byref(q), byref(c), byref(ns)),
+                       "cc_batch_circuit")
+            self.circuits.append({"psi_offset": off.value, "q": q.value, "c_total": c.value,
+                                  "n_sub": ns.value})
+
+    def _refresh_info(self):
+        info = capi.CBatchInfo()
+        capi.check(capi.lib().cc_batch_info(self._h, byref(info)), "cc_batch_info")
+        self.info = {f: getattr(info, f) for f, _ in capi.CBatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.lib().cc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _alloc(self, nbytes: int, device) -> torch.Tensor:
+        n = max(1, nbytes // AMP_BYTES[self.precision])
+        return torch.empty(n, dtype=TORCH_DTYPE[self.precision], device=device)
+
+    def alloc_buffers(self, device="cuda"):
+        """(seg_buf, psi, workspace) sized for the batch; workspace may be None."""
+        ws = self.info["workspace_bytes"]
+        return (self._alloc(self.info["seg_buf_bytes"], device),
+                self._alloc(self.info["psi_bytes"], device),
+                self._alloc(ws, device) if ws else None)
+
+    def alloc_stamps(self, device="cuda") -> torch.Tensor:
+        return torch.zeros(self.n_circ + 1, dtype=torch.int64, device=device)
+
+    def psi_view(self, psi: torch.Tensor, i: int) -> torch.Tensor:
+        c = self.circuits[i]
+        return psi[c["psi_offset"]:c["psi_offset"] + (1 << c["q"])]
+
+    def _args(self, seg, psi, ws, stamps):
+        return (_ptr(seg), _nbytes(seg), _ptr(psi), _nbytes(psi), _ptr(ws), _nbytes(ws),
+                _ptr(stamps))
+
+    def run(self, seg, psi, ws=None, stamps=None, stream=None) -> None:
+        capi.check(capi.lib().cc_batch_run(self._h, *self._args(seg, psi, ws, stamps),
+                                           _stream(stream)), "cc_batch_run")
+
+    def capture(self, seg, psi, ws=None, stamps=None, stream=None) -> None:
+        capi.check(capi.lib().cc_batch_capture(self._h, *self._args(seg, psi, ws, stamps),
+                                               _stream(stream)), "cc_batch_capture")
+
+    def launch(self, stream=None) -> None:
+        capi.check(capi.lib().cc_batch_launch(self._h, _stream(stream)), "cc_batch_launch")
+
+    def autotune(self, seg, psi, ws=None, stream=None):
+        """Time every (tile bits, merge rows) candidate, keep the fastest; returns the table."""
+        n_max = 16
+        tb, rows = (c_int32 * n_max)(), (c_int32 * n_max)()
+        ms = (ctypes.c_float * n_max)()
+        n = c_int32()
+        capi.check(capi.lib().cc_batch_autotune(
+            self._h, _ptr(seg), _nbytes(seg), _ptr(psi), _nbytes(psi), _ptr(ws), _nbytes(ws),
+            _stream(stream), n_max, byref(n), tb, rows, ms), "cc_batch_autotune")
+        self._refresh_info()
+        return [{"tile_bits": tb[i], "merge_rows": rows[i], "ms": ms[i]} for i in range(n.value)]

@@ -50,6 +50,16 @@ class CPlanInfo(ctypes.Structure):
     ]
 
 
+class CBatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_circ", c_int32), ("precision", c_int32), ("tile_bits", c_int32),
+        ("merge_rows", c_int32), ("n_jobs", c_int32), ("merge_levels", c_int32),
+        ("n_items", c_int64), ("n_sub", c_int64),
+        ("seg_buf_bytes", c_uint64), ("psi_bytes", c_uint64), ("workspace_bytes", c_uint64),
+        ("block", c_int32), ("grid", c_int32),
+    ]
+
+
 class CutsimError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -75,6 +85,21 @@ _SIGNATURES = {
                             c_void_p]),
     "cc_gather_static": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), c_int64,
                                    c_void_p, c_void_p]),
+    "cc_batch_create": (c_int32, [POINTER(CGate), POINTER(c_int64), c_int32, POINTER(c_int32),
+                                  POINTER(c_int32), POINTER(c_int32), c_int32, c_int32, c_int32,
+                                  c_int32, POINTER(c_void_p)]),
+    "cc_batch_info": (c_int32, [c_void_p, POINTER(CBatchInfo)]),
+    "cc_batch_circuit": (c_int32, [c_void_p, c_int32, POINTER(c_int64), POINTER(c_int32),
+                                   POINTER(c_int32), POINTER(c_int64)]),
+    "cc_batch_run": (c_int32, [c_void_p, c_void_p, c_uint64, c_void_p, c_uint64, c_void_p,
+                               c_uint64, c_void_p, c_void_p]),
+    "cc_batch_capture": (c_int32, [c_void_p, c_void_p, c_uint64, c_void_p, c_uint64, c_void_p,
+                                   c_uint64, c_void_p, c_void_p]),
+    "cc_batch_launch": (c_int32, [c_void_p, c_void_p]),
+    "cc_batch_autotune": (c_int32, [c_void_p, c_void_p, c_uint64, c_void_p, c_uint64, c_void_p,
+                                    c_uint64, c_void_p, c_int32, POINTER(c_int32),
+                                    POINTER(c_int32), POINTER(c_int32), POINTER(ctypes.c_float)]),
+    "cc_batch_destroy": (None, [c_void_p]),
     "cc_sync": (c_int32, [c_void_p]),
     "cc_last_error": (c_char_p, []),
     "cc_version": (c_char_p, []),

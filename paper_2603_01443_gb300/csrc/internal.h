@@ -151,6 +151,59 @@ cc_status run_program(const DeviceProgram& dp, int precision, void* state, void*
 int max_tile_bits(int precision);
 int low_tile_bits(int precision);
 
+// ------------------------------------------------------------- batching
+// One pass of one segment program inside a batched launch.  The queue of the
+// launch is the concatenation of every job's tiles, jobs ordered by pass
+// number, so every tile a job waits for sits earlier in the queue.
+struct BJob {
+  int64_t vec_off;       // amplitude offset of the program's vector in seg_buf
+  const DPass* pass;     // device pointers into the program's image
+  const DStage* stages;
+  const DOp* ops;
+  const DTerm* terms;
+  const void* mats;
+  const void* tabs;
+  int64_t tile_begin;    // first queue item of this job
+  int64_t n_tiles;
+  int32_t dep;           // job whose tiles must all be stored first (-1: none)
+  int32_t pad;
+};
+
+// Persistent launch over all jobs: CTAs take queue items from *head; done[j]
+// counts the stored tiles of job j (both zeroed by the caller).  A wait that
+// exceeds its iteration limit sets the device error flag, skips the tile and
+// still counts it, so the launch always ends.  stamps (optional) receives the
+// %globaltimer value when the first item is taken.
+cc_status launch_batch_segments(void* seg_buf, const BJob* jobs, int n_jobs, int64_t n_items,
+                                int* done, unsigned long long* head,
+                                unsigned long long* stamps, int precision, int block,
+                                size_t smem, int grid, void* stream);
+// CTAs per SM the batched segment kernel reaches with this block and shared memory.
+int batch_segments_occupancy(int precision, int block, size_t smem);
+
+// One merge stage of one circuit inside a batched merge launch; operands are
+// offsets (in amplitudes) into one of three caller buffers.
+enum : int32_t { BUF_SEG = 0, BUF_WORK = 1, BUF_PSI = 2 };
+struct BMergeJob {
+  int32_t a_buf, b_buf, out_buf, kind;  // kind: 0 tiled, 1 flat
+  int64_t a_off, b_off, out_off;
+  int32_t qa, qb;
+  int64_t K, Z, out_stride;
+  const int32_t* aidx;
+  const int32_t* bidx;
+  int64_t unit_begin, n_units;
+  int32_t circ;  // circuit whose output this stage completes (-1: intermediate)
+  int32_t pad;
+};
+// Work units of a batched merge job for the given tile rows (16 or 32).
+int64_t merge_batch_units(int precision, int qa, int qb, int64_t Z, int rows, int32_t* kind);
+// One launch over every job of one merge level.  circ_done counts finished
+// units per circuit (zeroed by the caller); when a circuit's final stage
+// completes, stamps[1 + circ] receives %globaltimer.
+cc_status launch_merge_batch(const BMergeJob* jobs, int n_jobs, int64_t n_units, void* seg_buf,
+                             void* work, void* psi, int* circ_done, unsigned long long* stamps,
+                             int precision, int rows, void* stream);
+
 // -------------------------------------------------------------- merging
 // Batched two-factor merge:
 //   out[z*out_stride + y*NA + x] = sum_k A[aidx[z*K+k]*NA + x] * B[bidx[z*K+k]*NB + y]

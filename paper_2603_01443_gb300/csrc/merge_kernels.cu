@@ -56,7 +56,70 @@ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
   acc.y = fma(a.y, b.x, acc.y);
 }
 
-// complex64 tile: 32 rows (y) x 128 columns (x); 256 threads = 64 column pairs x 4 row groups.
+// complex64 tile: 4*RPT rows (y) x 128 columns (x) of out_z (the output of
+// one batch entry z); 256 threads = 64 column pairs x 4 row groups of RPT rows.
+template <bool COMP, int RPT>
+__device__ __forceinline__ void tile_c64(const float2* __restrict__ A, const float2* __restrict__ B,
+                                         float2* __restrict__ out_z, int64_t NA, int64_t NB,
+                                         int64_t K, const int32_t* __restrict__ ai,
+                                         const int32_t* __restrict__ bi, int64_t y0, int64_t x0,
+                                         float2 (*As)[128], float2 (*Bs)[4 * RPT]) {
+  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+  float2 acc[RPT][2], hi[COMP ? RPT : 1][2], lo[COMP ? RPT : 1][2];
+#pragma unroll
+  for (int i = 0; i < (COMP ? RPT : 1); ++i)
+    hi[i][0] = hi[i][1] = lo[i][0] = lo[i][1] = make_float2(0.f, 0.f);
+  for (int64_t k0 = 0; k0 < K; k0 += KC) {
+    const int kc = (int)((K - k0) < KC ? (K - k0) : KC);
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+    for (int e = tid; e < kc * 64; e += 256) {
+      const int kk = e >> 6, c = e & 63;
+      const float4 v = *reinterpret_cast<const float4*>(A + (int64_t)ai[k0 + kk] * NA + x0 + 2 * c);
+      *reinterpret_cast<float4*>(&As[kk][2 * c]) = v;
+    }
+    for (int e = tid; e < kc * 2 * RPT; e += 256) {
+      const int kk = e / (2 * RPT), c = e % (2 * RPT);
+      const float4 v = *reinterpret_cast<const float4*>(B + (int64_t)bi[k0 + kk] * NB + y0 + 2 * c);
+      *reinterpret_cast<float4*>(&Bs[kk][2 * c]) = v;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][2 * tx]);
+      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+#pragma unroll
+      for (int i = 0; i < RPT; i += 2) {
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][ty * RPT + i]);
+        const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+        cfma(acc[i][0], a0, b0);
+        cfma(acc[i][1], a1, b0);
+        cfma(acc[i + 1][0], a0, b1);
+        cfma(acc[i + 1][1], a1, b1);
+      }
+    }
+    __syncthreads();
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        two_sum_add(hi[i][0], lo[i][0], acc[i][0]);
+        two_sum_add(hi[i][1], lo[i][1], acc[i][1]);
+      }
+    }
+  }
+  if (COMP) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      acc[i][0] = make_float2(hi[i][0].x + lo[i][0].x, hi[i][0].y + lo[i][0].y);
+      acc[i][1] = make_float2(hi[i][1].x + lo[i][1].x, hi[i][1].y + lo[i][1].y);
+    }
+  }
+  float2* o = out_z + (y0 + ty * RPT) * NA + x0 + 2 * tx;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+    __stcs(reinterpret_cast<float4*>(o + i * NA),
+           make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y));
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(256)
     merge_tile_c64(const float2* __restrict__ A, const float2* __restrict__ B,
@@ -68,70 +131,49 @@ __global__ void __launch_bounds__(256)
   const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
   const int64_t tiles_x = NA >> 7, tiles_y = NB >> 5;
   const int64_t n_tiles = tiles_x * tiles_y * Z;
-  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
   for (int64_t w = blockIdx.x; w < n_tiles; w += gridDim.x) {
     const int64_t z = w / (tiles_x * tiles_y);
     const int64_t rem = w - z * tiles_x * tiles_y;
     const int64_t y0 = (rem / tiles_x) << 5, x0 = (rem % tiles_x) << 7;
-    const int32_t* ai = aidx + z * K;
-    const int32_t* bi = bidx + z * K;
-    float2 acc[8][2], hi[COMP ? 8 : 1][2], lo[COMP ? 8 : 1][2];
-#pragma unroll
-    for (int i = 0; i < (COMP ? 8 : 1); ++i)
-      hi[i][0] = hi[i][1] = lo[i][0] = lo[i][1] = make_float2(0.f, 0.f);
-    for (int64_t k0 = 0; k0 < K; k0 += KC) {
-      const int kc = (int)((K - k0) < KC ? (K - k0) : KC);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-      for (int e = tid; e < kc * 64; e += 256) {
-        const int kk = e >> 6, c = e & 63;
-        const float4 v = *reinterpret_cast<const float4*>(A + (int64_t)ai[k0 + kk] * NA + x0 + 2 * c);
-        *reinterpret_cast<float4*>(&As[kk][2 * c]) = v;
-      }
-      for (int e = tid; e < kc * 16; e += 256) {
-        const int kk = e >> 4, c = e & 15;
-        const float4 v = *reinterpret_cast<const float4*>(B + (int64_t)bi[k0 + kk] * NB + y0 + 2 * c);
-        *reinterpret_cast<float4*>(&Bs[kk][2 * c]) = v;
-      }
-      __syncthreads();
-      for (int kk = 0; kk < kc; ++kk) {
-        const float4 a = *reinterpret_cast<const float4*>(&As[kk][2 * tx]);
-        const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-          const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][ty * 8 + i]);
-          const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
-          cfma(acc[i][0], a0, b0);
-          cfma(acc[i][1], a1, b0);
-          cfma(acc[i + 1][0], a0, b1);
-          cfma(acc[i + 1][1], a1, b1);
-        }
-      }
-      __syncthreads();
-      if (COMP) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          two_sum_add(hi[i][0], lo[i][0], acc[i][0]);
-          two_sum_add(hi[i][1], lo[i][1], acc[i][1]);
-        }
-      }
-    }
-    if (COMP) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        acc[i][0] = make_float2(hi[i][0].x + lo[i][0].x, hi[i][0].y + lo[i][0].y);
-        acc[i][1] = make_float2(hi[i][1].x + lo[i][1].x, hi[i][1].y + lo[i][1].y);
-      }
-    }
-    float2* o = out + z * out_stride + (y0 + ty * 8) * NA + x0 + 2 * tx;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      __stcs(reinterpret_cast<float4*>(o + i * NA),
-             make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y));
+    tile_c64<COMP, 8>(A, B, out + z * out_stride, NA, NB, K, aidx + z * K, bidx + z * K, y0, x0,
+                      As, Bs);
   }
 }
 
 // complex128 tile: 32 rows x 64 columns; 256 threads = 64 columns x 4 row groups.
+__device__ __forceinline__ void tile_c128(const double2* __restrict__ A,
+                                          const double2* __restrict__ B,
+                                          double2* __restrict__ out_z, int64_t NA, int64_t NB,
+                                          int64_t K, const int32_t* __restrict__ ai,
+                                          const int32_t* __restrict__ bi, int64_t y0, int64_t x0,
+                                          double2 (*As)[64], double2 (*Bs)[32]) {
+  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+  double2 acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = make_double2(0.0, 0.0);
+  for (int64_t k0 = 0; k0 < K; k0 += KC) {
+    const int kc = (int)((K - k0) < KC ? (K - k0) : KC);
+    for (int e = tid; e < kc * 64; e += 256) {
+      const int kk = e >> 6, c = e & 63;
+      As[kk][c] = A[(int64_t)ai[k0 + kk] * NA + x0 + c];
+    }
+    for (int e = tid; e < kc * 32; e += 256) {
+      const int kk = e >> 5, c = e & 31;
+      Bs[kk][c] = B[(int64_t)bi[k0 + kk] * NB + y0 + c];
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kc; ++kk) {
+      const double2 a = As[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cfma(acc[i], a, Bs[kk][ty * 8 + i]);
+    }
+    __syncthreads();
+  }
+  double2* o = out_z + (y0 + ty * 8) * NA + x0 + tx;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) __stcs(o + i * NA, acc[i]);
+}
+
 __global__ void __launch_bounds__(256)
     merge_tile_c128(const double2* __restrict__ A, const double2* __restrict__ B,
                     double2* __restrict__ out, int qa, int qb, int64_t K, int64_t Z,
@@ -142,37 +184,11 @@ __global__ void __launch_bounds__(256)
   const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
   const int64_t tiles_x = NA >> 6, tiles_y = NB >> 5;
   const int64_t n_tiles = tiles_x * tiles_y * Z;
-  const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
   for (int64_t w = blockIdx.x; w < n_tiles; w += gridDim.x) {
     const int64_t z = w / (tiles_x * tiles_y);
     const int64_t rem = w - z * tiles_x * tiles_y;
     const int64_t y0 = (rem / tiles_x) << 5, x0 = (rem % tiles_x) << 6;
-    const int32_t* ai = aidx + z * K;
-    const int32_t* bi = bidx + z * K;
-    double2 acc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = make_double2(0.0, 0.0);
-    for (int64_t k0 = 0; k0 < K; k0 += KC) {
-      const int kc = (int)((K - k0) < KC ? (K - k0) : KC);
-      for (int e = tid; e < kc * 64; e += 256) {
-        const int kk = e >> 6, c = e & 63;
-        As[kk][c] = A[(int64_t)ai[k0 + kk] * NA + x0 + c];
-      }
-      for (int e = tid; e < kc * 32; e += 256) {
-        const int kk = e >> 5, c = e & 31;
-        Bs[kk][c] = B[(int64_t)bi[k0 + kk] * NB + y0 + c];
-      }
-      __syncthreads();
-      for (int kk = 0; kk < kc; ++kk) {
-        const double2 a = As[kk][tx];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) cfma(acc[i], a, Bs[kk][ty * 8 + i]);
-      }
-      __syncthreads();
-    }
-    double2* o = out + z * out_stride + (y0 + ty * 8) * NA + x0 + tx;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) __stcs(o + i * NA, acc[i]);
+    tile_c128(A, B, out + z * out_stride, NA, NB, K, aidx + z * K, bidx + z * K, y0, x0, As, Bs);
   }
 }
 
@@ -210,6 +226,92 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// One output amplitude of a merge stage, any factor sizes.
+template <typename C>
+__device__ __forceinline__ C flat_one(const C* __restrict__ A, const C* __restrict__ B, int qa,
+                                      int64_t NA, int64_t NB, int64_t K,
+                                      const int32_t* __restrict__ ai,
+                                      const int32_t* __restrict__ bi, int64_t e) {
+  const int64_t x = e & (NA - 1), y = e >> qa;
+  C hi, lo;
+  hi.x = hi.y = lo.x = lo.y = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += KC) {
+    const int64_t k1 = (K - k0) < KC ? K : k0 + KC;
+    C acc;
+    acc.x = acc.y = 0;
+    for (int64_t k = k0; k < k1; ++k) cfma(acc, A[(int64_t)ai[k] * NA + x], B[(int64_t)bi[k] * NB + y]);
+    add_chunk(hi, lo, acc);
+  }
+  hi.x += lo.x;
+  hi.y += lo.y;
+  return hi;
+}
+
+__device__ __forceinline__ unsigned long long merge_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Batched merge: the units (output tiles, or runs of 256 amplitudes for
+// factors too short for a tile) of many stage jobs in one grid-stride loop.
+template <typename C, int RPT>
+__global__ void __launch_bounds__(256)
+    merge_batch_kernel(const BMergeJob* __restrict__ jobs, int n_jobs, long long n_units,
+                       C* seg, C* work, C* psi, int* __restrict__ circ_done,
+                       unsigned long long* __restrict__ stamps) {
+  constexpr bool F32 = sizeof(C) == 8;
+  constexpr int TX = F32 ? 128 : 64, TY = F32 ? 4 * RPT : 32;
+  __shared__ __align__(16) C As[KC][TX];
+  __shared__ __align__(16) C Bs[KC][TY];
+  for (long long w = blockIdx.x; w < n_units; w += gridDim.x) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].unit_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    const BMergeJob& J = jobs[lo];
+    C* const bufs[3] = {seg, work, psi};
+    const C* A = bufs[J.a_buf] + J.a_off;
+    const C* B = bufs[J.b_buf] + J.b_off;
+    C* out = bufs[J.out_buf] + J.out_off;
+    const int64_t NA = int64_t(1) << J.qa, NB = int64_t(1) << J.qb;
+    const int64_t u = w - J.unit_begin;
+    if (J.kind == 0) {
+      const int64_t tiles_x = NA / TX, tiles_y = NB / TY;
+      const int64_t z = u / (tiles_x * tiles_y);
+      const int64_t rem = u - z * tiles_x * tiles_y;
+      const int64_t y0 = (rem / tiles_x) * TY, x0 = (rem % tiles_x) * TX;
+      if constexpr (F32) {
+        if (J.K > KC)
+          tile_c64<true, RPT>(A, B, out + z * J.out_stride, NA, NB, J.K, J.aidx + z * J.K,
+                              J.bidx + z * J.K, y0, x0, As, Bs);
+        else
+          tile_c64<false, RPT>(A, B, out + z * J.out_stride, NA, NB, J.K, J.aidx + z * J.K,
+                               J.bidx + z * J.K, y0, x0, As, Bs);
+      } else {
+        tile_c128(A, B, out + z * J.out_stride, NA, NB, J.K, J.aidx + z * J.K, J.bidx + z * J.K,
+                  y0, x0, As, Bs);
+      }
+    } else {
+      const int64_t per = NA * NB, f = u * 256 + threadIdx.x;
+      if (f < per * J.Z) {
+        const int64_t z = f / per, e = f - z * per;
+        out[z * J.out_stride + e] =
+            flat_one<C>(A, B, J.qa, NA, NB, J.K, J.aidx + z * J.K, J.bidx + z * J.K, e);
+      }
+    }
+    if (J.circ >= 0 && stamps) {
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int v = atomicAdd(circ_done + J.circ, 1);
+        if (v + 1 == J.n_units) stamps[1 + J.circ] = merge_timer();
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cc_status launch_merge_fma(const MergeStage& st, int precision, void* stream) {
@@ -244,6 +346,44 @@ cc_status launch_merge_fma(const MergeStage& st, int precision, void* stream) {
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("merge launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
+
+}  // namespace cc
+
+namespace cc {
+
+int64_t merge_batch_units(int precision, int qa, int qb, int64_t Z, int rows, int32_t* kind) {
+  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
+  const int tx = precision == CC_C64 ? 128 : 64;
+  const int ty = precision == CC_C64 ? rows : 32;
+  if (NA >= tx && NB >= ty) {
+    if (kind) *kind = 0;
+    return (NA / tx) * (NB / ty) * Z;
+  }
+  if (kind) *kind = 1;
+  return (NA * NB * Z + 255) / 256;
+}
+
+cc_status launch_merge_batch(const BMergeJob* jobs, int n_jobs, int64_t n_units, void* seg_buf,
+                             void* work, void* psi, int* circ_done, unsigned long long* stamps,
+                             int precision, int rows, void* stream) {
+  if (n_units <= 0 || n_jobs <= 0) return CC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t grid = std::min<int64_t>(n_units, (int64_t)num_sms() * 8);
+  if (precision == CC_C128) {
+    merge_batch_kernel<double2, 8><<<(unsigned)grid, 256, 0, s>>>(
+        jobs, n_jobs, n_units, (double2*)seg_buf, (double2*)work, (double2*)psi, circ_done, stamps);
+  } else if (rows == 16) {
+    merge_batch_kernel<float2, 4><<<(unsigned)grid, 256, 0, s>>>(
+        jobs, n_jobs, n_units, (float2*)seg_buf, (float2*)work, (float2*)psi, circ_done, stamps);
+  } else {
+    merge_batch_kernel<float2, 8><<<(unsigned)grid, 256, 0, s>>>(
+        jobs, n_jobs, n_units, (float2*)seg_buf, (float2*)work, (float2*)psi, circ_done, stamps);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(CC_ECUDA, std::string("batched merge launch: ") + cudaGetErrorString(e));
   return CC_OK;
 }
 

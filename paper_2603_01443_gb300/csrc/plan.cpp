@@ -81,6 +81,12 @@ cc_plan::~cc_plan() {
 extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32_t q,
                                     const int32_t* seg_sizes, int32_t n_seg, int32_t decomp,
                                     int32_t precision, cc_plan** out) {
+  return cc::create_plan(gates, n_gates, q, seg_sizes, n_seg, decomp, precision,
+                         seg_tile_bits(precision), out);
+}
+
+cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* seg_sizes,
+                          int n_seg, int decomp, int precision, int seg_kmax, cc_plan** out) {
   try {
     if (!out) return fail(CC_EINVAL, "out is NULL");
     *out = nullptr;
@@ -163,7 +169,7 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
     // One shared program per segment.
     for (int i = 0; i < n_seg; ++i) {
       HostProgram hp = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
-                                       seg_tile_bits(precision), low_tile_bits(precision),
+                                       seg_kmax, low_tile_bits(precision),
                                        reg_bits_max(precision));
       if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
       p->hprog.push_back(std::move(hp));

@@ -14,6 +14,14 @@ int uncut_tile_bits(int precision);
 int seg_tile_bits(int precision);
 }  // namespace cc
 
+struct cc_plan;
+namespace cc {
+// cc_plan_create with an explicit largest segment tile (bits, in
+// low_tile_bits + 1 .. max_tile_bits).
+cc_status create_plan(const cc_gate* gates, int n_gates, int q, const int* seg_sizes, int n_seg,
+                      int decomp, int precision, int seg_kmax, cc_plan** out);
+}  // namespace cc
+
 struct cc_plan {
   struct Cut {
     int q0, q1, kind, s0, s1;

@@ -184,52 +184,56 @@ __device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const
   }
 }
 
-template <typename R, int RB>
-__global__ void __launch_bounds__(512)
-    stage_kernel(typename CT<R>::C* __restrict__ vec, const DPass* __restrict__ pass,
-                 const DStage* __restrict__ stages, const DOp* __restrict__ ops,
-                 const DTerm* __restrict__ terms, const R* __restrict__ mats,
-                 const R* __restrict__ tabs, int64_t n_tiles) {
+// Load, transform and store tile T of one pass.  n_active threads (a power
+// of two, 2^(k - rbits)) take part in the register stages; every thread of
+// the block shares the loads and stores.  CG loads through L2 only, for
+// vectors that other CTAs of the same launch wrote.
+template <typename R, int RB, bool CG>
+__device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, const DPass& P,
+                                         const DPass* __restrict__ pass,
+                                         const DStage* __restrict__ stages,
+                                         const DOp* __restrict__ ops,
+                                         const DTerm* __restrict__ terms,
+                                         const R* __restrict__ mats, const R* __restrict__ tabs,
+                                         int64_t T, typename CT<R>::C* s, uint32_t n_active) {
   using C = typename CT<R>::C;
   using V = typename CT<R>::V;
   constexpr int PV = CT<R>::PV;
   constexpr int N = 1 << RB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  const DPass P = *pass;
   const uint32_t n = 1u << P.k;
   const uint32_t nt = blockDim.x, tid = threadIdx.x;
   const uint32_t low_mask = (P.low >= 32) ? 0xffffffffu : ((1u << P.low) - 1u);
   const uint32_t kmask = n - 1u;
   const int8_t* __restrict__ hi_bits = pass->tile_bit + P.low;
+  const bool active = tid < n_active;
 
-  for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x) {
-    const uint64_t vbase = (uint64_t)T << P.k;
-    int64_t gbase = 0;
-    for (int b = 0; b < P.n_rest; ++b) gbase |= ((T >> b) & 1) << pass->rest_bit[b];
-    const bool rest_zero = (((uint64_t)T) & P.zero_rest) == 0;
+  const uint64_t vbase = (uint64_t)T << P.k;
+  int64_t gbase = 0;
+  for (int b = 0; b < P.n_rest; ++b) gbase |= ((T >> b) & 1) << pass->rest_bit[b];
+  const bool rest_zero = (((uint64_t)T) & P.zero_rest) == 0;
 
-    if (!P.init_zero) {
+  if (!P.init_zero) {
 #pragma unroll 4
-      for (uint32_t u = tid; u < n / PV; u += nt) {
-        const uint32_t l = u * PV;
-        const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-        V val = *reinterpret_cast<const V*>(vec + g);
-        const uint32_t pl = swz(l);
-        if (PV == 2 && (pl & 1u)) {  // the swizzle swapped the pair
-          V sw = val;
-          reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
-                                                      reinterpret_cast<float4&>(val).w,
-                                                      reinterpret_cast<float4&>(val).x,
-                                                      reinterpret_cast<float4&>(val).y);
-          val = sw;
-        }
-        *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = val;
+    for (uint32_t u = tid; u < n / PV; u += nt) {
+      const uint32_t l = u * PV;
+      const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
+      V val = CG ? __ldcg(reinterpret_cast<const V*>(vec + g)) : *reinterpret_cast<const V*>(vec + g);
+      const uint32_t pl = swz(l);
+      if (PV == 2 && (pl & 1u)) {  // the swizzle swapped the pair
+        V sw = val;
+        reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
+                                                    reinterpret_cast<float4&>(val).w,
+                                                    reinterpret_cast<float4&>(val).x,
+                                                    reinterpret_cast<float4&>(val).y);
+        val = sw;
       }
-      __syncthreads();
+      *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = val;
     }
+    __syncthreads();
+  }
 
-    for (int si = P.stage_begin; si < P.stage_end; ++si) {
+  for (int si = P.stage_begin; si < P.stage_end; ++si) {
+    if (active) {
       const DStage st = stages[si];
       StageRegs<RB> sr;
       sr.rmask = 0;
@@ -299,26 +303,131 @@ __global__ void __launch_bounds__(512)
 
 #pragma unroll
       for (int j = 0; j < N; ++j) s[swz(dep(j))] = a[j];
-      __syncthreads();
-    }
-
-#pragma unroll 4
-    for (uint32_t u = tid; u < n / PV; u += nt) {
-      const uint32_t l = u * PV;
-      const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-      const uint32_t pl = swz(l);
-      V val = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
-      if (PV == 2 && (pl & 1u)) {
-        V sw = val;
-        reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
-                                                    reinterpret_cast<float4&>(val).w,
-                                                    reinterpret_cast<float4&>(val).x,
-                                                    reinterpret_cast<float4&>(val).y);
-        val = sw;
-      }
-      *reinterpret_cast<V*>(vec + g) = val;
     }
     __syncthreads();
+  }
+
+#pragma unroll 4
+  for (uint32_t u = tid; u < n / PV; u += nt) {
+    const uint32_t l = u * PV;
+    const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
+    const uint32_t pl = swz(l);
+    V val = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
+    if (PV == 2 && (pl & 1u)) {
+      V sw = val;
+      reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
+                                                  reinterpret_cast<float4&>(val).w,
+                                                  reinterpret_cast<float4&>(val).x,
+                                                  reinterpret_cast<float4&>(val).y);
+      val = sw;
+    }
+    *reinterpret_cast<V*>(vec + g) = val;
+  }
+  __syncthreads();
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(512)
+    stage_kernel(typename CT<R>::C* __restrict__ vec, const DPass* __restrict__ pass,
+                 const DStage* __restrict__ stages, const DOp* __restrict__ ops,
+                 const DTerm* __restrict__ terms, const R* __restrict__ mats,
+                 const R* __restrict__ tabs, int64_t n_tiles) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const DPass P = *pass;
+  for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x)
+    run_tile<R, RB, false>(vec, P, pass, stages, ops, terms, mats, tabs, T, s, blockDim.x);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A dependency wait gives up after this many polls (each followed by a
+// ~128 ns sleep): seconds, far beyond any tile of a valid batch.
+constexpr int kBatchWaitPolls = 1 << 25;
+
+// Persistent batched gate passes: every CTA takes queue items (one tile of
+// one job) until the queue is empty.  Jobs are ordered by pass number, so a
+// job's dependency has all its tiles earlier in the queue, taken by CTAs that
+// are already running: the waits always end.
+template <typename R>
+__global__ void __launch_bounds__(512)
+    batch_kernel(typename CT<R>::C* __restrict__ seg_buf, const BJob* __restrict__ jobs,
+                 int n_jobs, long long n_items, int* __restrict__ done,
+                 unsigned long long* __restrict__ head, int* __restrict__ err,
+                 unsigned long long* __restrict__ stamps) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  __shared__ long long s_item;
+  __shared__ int s_job, s_ok;
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const long long it = (long long)atomicAdd(head, 1ull);
+      s_item = it;
+      if (it == 0 && stamps) stamps[0] = global_timer();
+      if (it < n_items) {
+        int lo = 0, hi = n_jobs - 1;  // last job with tile_begin <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (jobs[mid].tile_begin <= it) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+        int ok = 1;
+        const int d = jobs[lo].dep;
+        if (d >= 0) {
+          const int need = (int)jobs[d].n_tiles;
+          int polls = 0;
+          while (ld_acquire(done + d) < need) {
+            if (++polls > kBatchWaitPolls) {
+              ok = 0;
+              atomicExch(err, 1);
+              break;
+            }
+            __nanosleep(128);
+          }
+          __threadfence();
+        }
+        s_ok = ok;
+      }
+    }
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= n_items) break;
+    const int j = s_job;
+    if (s_ok) {
+      const BJob& J = jobs[j];
+      const DPass P = *J.pass;
+      C* vec = seg_buf + J.vec_off;
+      const int64_t T = it - J.tile_begin;
+      const uint32_t na = 1u << (P.k - P.rbits);
+      const R* mats = reinterpret_cast<const R*>(J.mats);
+      const R* tabs = reinterpret_cast<const R*>(J.tabs);
+      switch (P.rbits) {
+        case 1: run_tile<R, 1, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
+        case 2: run_tile<R, 2, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
+        case 3: run_tile<R, 3, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
+        case 4: run_tile<R, 4, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
+        default:
+          run_tile<R, (sizeof(R) == 4 ? 5 : 4), true>(vec, P, J.pass, J.stages, J.ops, J.terms,
+                                                       mats, tabs, T, s, na);
+          break;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(done + j, 1);
   }
 }
 
@@ -370,6 +479,52 @@ cc_status launch_pass(const DeviceProgram& dp, int pi, void* state, cudaStream_t
 }  // namespace
 
 int reg_bits_max(int precision) { return precision == CC_C128 ? 4 : 5; }
+
+int batch_segments_occupancy(int precision, int block, size_t smem) {
+  static int attr_done[64][2] = {{0}};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int pi = precision == CC_C128 ? 1 : 0;
+  const void* kern = precision == CC_C128 ? (const void*)batch_kernel<double>
+                                          : (const void*)batch_kernel<float>;
+  if (dev >= 0 && dev < 64 && !attr_done[dev][pi]) {
+    // the opt-in limit (227 KB per CTA) covers static and dynamic shared memory
+    cudaFuncAttributes fa;
+    size_t static_smem = 0;
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess) static_smem = fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(227 * 1024 - static_smem));
+    cudaGetLastError();
+    attr_done[dev][pi] = 1;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  return occ;
+}
+
+cc_status launch_batch_segments(void* seg_buf, const BJob* jobs, int n_jobs, int64_t n_items,
+                                int* done, unsigned long long* head,
+                                unsigned long long* stamps, int precision, int block,
+                                size_t smem, int grid, void* stream) {
+  if (n_items <= 0) return CC_OK;
+  int* err = device_error_flag();
+  if (!err) return fail(CC_ENOMEM, "device error flag allocation failed");
+  batch_segments_occupancy(precision, block, smem);  // sets the shared-memory attribute once
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == CC_C128)
+    batch_kernel<double><<<grid, block, smem, s>>>(static_cast<double2*>(seg_buf), jobs, n_jobs,
+                                                   n_items, done, head, err, stamps);
+  else
+    batch_kernel<float><<<grid, block, smem, s>>>(static_cast<float2*>(seg_buf), jobs, n_jobs,
+                                                  n_items, done, head, err, stamps);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(CC_ECUDA, std::string("batched gate pass launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
 
 cc_status run_program(const DeviceProgram& dp, int precision, void* state, void* stream) {
   for (int pi = 0; pi < (int)dp.passes.size(); ++pi) {

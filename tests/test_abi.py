@@ -129,3 +129,58 @@ def test_entry_points_reject_null(L):
     assert L.cc_uncut_info(None, None, None, None) == 1
     L.cc_plan_destroy(None)
     L.cc_uncut_destroy(None)
+
+
+def _batch_args(items):
+    arrs = [capi.gate_array(it.gates) for it in items]
+    n = sum(len(it.gates) for it in items)
+    gates = (capi.CGate * max(n, 1))()
+    goff = (c_int64 * (len(items) + 1))()
+    at = 0
+    for i, (it, a) in enumerate(zip(items, arrs)):
+        goff[i] = at
+        for j in range(len(it.gates)):
+            gates[at + j] = a[j]
+        at += len(it.gates)
+    goff[len(items)] = at
+    qs = (c_int32 * len(items))(*[it.q for it in items])
+    sizes = [s for it in items for s in it.seg_sizes]
+    seg_sizes = (c_int32 * len(sizes))(*sizes)
+    soff = (c_int32 * (len(items) + 1))()
+    at = 0
+    for i, it in enumerate(items):
+        soff[i] = at
+        at += len(it.seg_sizes)
+    soff[len(items)] = at
+    return gates, goff, qs, seg_sizes, soff
+
+
+@pytest.mark.parametrize("case", ["no_circuits", "one_segment", "bad_rows", "bad_tile",
+                                  "bad_gate", "bad_offsets"])
+def test_batch_host_validation(L, case):
+    items = w.uneven_batch(3, seed=1, q_range=(12, 14), depths=(4,), c_range=(1, 2))
+    gates, goff, qs, seg_sizes, soff = _batch_args(items)
+    n, tile, rows = len(items), 0, 0
+    if case == "no_circuits":
+        n = 0
+    elif case == "one_segment":  # circuit 0 as a single segment
+        sizes = [items[0].q] + items[1].seg_sizes + items[2].seg_sizes
+        seg_sizes = (c_int32 * len(sizes))(*sizes)
+        n1, n2 = len(items[1].seg_sizes), len(items[2].seg_sizes)
+        soff = (c_int32 * 4)(0, 1, 1 + n1, 1 + n1 + n2)
+    elif case == "bad_rows":
+        rows = 8
+    elif case == "bad_tile":
+        tile = 3
+    elif case == "bad_gate":
+        gates[goff[1] + 2].q0 = 99  # a qubit outside circuit 1
+    elif case == "bad_offsets":
+        goff[2] = goff[1] - 1
+    h = c_void_p()
+    st = L.cc_batch_create(gates, goff, n, qs, seg_sizes, soff, 0, 0, tile, rows, byref(h))
+    want = {"no_circuits": 2, "one_segment": 1, "bad_rows": 1, "bad_tile": 2, "bad_gate": 1,
+            "bad_offsets": 1}[case]
+    assert st == want, (case, st, L.cc_last_error())
+    assert not h.value
+    if case == "bad_gate":
+        assert b"circuit 1" in L.cc_last_error()

@@ -22,4 +22,7 @@ from .circuits import (  # noqa: F401
     random_circuit,
     sample_indices,
     split_cuts,
+    BatchItem,
+    uneven_sizes,
+    uneven_batch,
 )

@@ -172,6 +172,54 @@ def split_cuts(c_total: int, n: int) -> List[int]:
     return [base + (1 if b < extra else 0) for b in range(n - 1)]
 
 
+class BatchItem(NamedTuple):
+    gates: List[Gate]
+    q: int
+    depth: int
+    seg_sizes: List[int]
+    cuts_per_boundary: List[int]
+    seed: int
+
+
+def uneven_sizes(rng: SplitMix64, q: int, n: int, min_size: int = 4) -> List[int]:
+    """n contiguous segment sizes, each >= min_size, summing to q: every
+    segment starts at min_size and each remaining qubit goes to a segment
+    drawn uniformly."""
+    if n * min_size > q:
+        raise ValueError("q too small for n segments of min_size")
+    sizes = [min_size] * n
+    for _ in range(q - n * min_size):
+        sizes[rng.next_u64() % n] += 1
+    return sizes
+
+
+def uneven_batch(
+    n_circ: int,
+    seed: int,
+    q_range: Sequence[int] = (16, 26),
+    depths: Sequence[int] = (8, 16, 32),
+    n_choices: Sequence[int] = (2, 3),
+    c_range: Sequence[int] = (2, 6),
+) -> List[BatchItem]:
+    """Independent random brickwork circuits for a batch: q uniform in
+    q_range (inclusive), depth from depths, n from n_choices, unequal
+    contiguous segments (uneven_sizes), c_total uniform in c_range spread
+    over the boundaries (split_cuts).  Circuit i uses brickwork seed
+    seed * 1000003 + i."""
+    rng = SplitMix64(seed)
+    out: List[BatchItem] = []
+    for i in range(n_circ):
+        q = q_range[0] + int(rng.next_u64() % (q_range[1] - q_range[0] + 1))
+        depth = depths[rng.next_u64() % len(depths)]
+        n = n_choices[rng.next_u64() % len(n_choices)]
+        c = c_range[0] + int(rng.next_u64() % (c_range[1] - c_range[0] + 1))
+        sizes = uneven_sizes(rng, q, n)
+        cpb = split_cuts(c, n)
+        s = seed * 1000003 + i
+        out.append(BatchItem(brickwork_cut(q, depth, s, sizes, cpb), q, depth, sizes, cpb, s))
+    return out
+
+
 def staircase(q: int, blocks: int) -> List[Gate]:
     """The paper's H/T/CX family (Fig. 1).
 
