@@ -300,7 +300,9 @@ cc_status cc_batch_circuit(const cc_batch* b, int32_t i, int64_t* psi_offset, in
 /* cc_batch_run -- simulate and merge every circuit of the batch (asynchronous
  * on `stream`).  stamps: optional device array of n_circ + 1 uint64 that
  * receives %globaltimer (ns) when the persistent launch takes its first tile
- * (stamps[0]) and when circuit i's output is complete (stamps[1 + i]).
+ * (stamps[0]) and when the last store of circuit i's output has been issued
+ * (stamps[1 + i]; the stores land within their memory latency after it).
+ * Stamping costs one counter update per merge tile.
  * Errors: CC_EBUFSIZE, CC_EINVAL; a dependency wait that gives up is
  * reported by cc_sync as CC_ETIMEOUT. */
 cc_status cc_batch_run(const cc_batch* b, void* seg_buf, uint64_t seg_buf_bytes, void* psi,

@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(256)
       }
     }
     if (J.circ >= 0 && stamps) {
-      __threadfence();
+      // counts units whose stores were issued; no fence, so the stamp may
+      // precede the last stores' arrival in memory by their latency
       __syncthreads();
       if (threadIdx.x == 0) {
         const int v = atomicAdd(circ_done + J.circ, 1);

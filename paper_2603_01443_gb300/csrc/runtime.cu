@@ -165,7 +165,7 @@ ImageLayout append_program_image(const HostProgram& hp, int precision,
   L.o_ops = align16(L.o_stages + hp.stages.size() * sizeof(DStage));
   L.o_terms = align16(L.o_ops + hp.ops.size() * sizeof(DOp));
   L.o_mats = align16(L.o_terms + hp.terms.size() * sizeof(DTerm));
-  L.o_tabs = align16(L.o_mats + hp.mats.size() * 2 * rb);
+  L.o_tabs = align16(L.o_mats + hp.ops.size() * 4 * 2 * rb);  // one matrix slot per op
   L.end = align16(L.o_tabs + hp.tabs.size() * 2 * rb);
   img.resize(L.base + L.end, 0);
   unsigned char* p0 = img.data() + L.base;
@@ -186,7 +186,13 @@ ImageLayout append_program_image(const HostProgram& hp, int precision,
       }
     }
   };
-  put(L.o_mats, hp.mats);
+  // The kernels read op o's matrix at slot o, so that it does not wait on the
+  // op's descriptor; diagonal-only ops get a zero slot.
+  std::vector<cd> per_op(hp.ops.size() * 4, cd(0.0, 0.0));
+  for (size_t o = 0; o < hp.ops.size(); ++o)
+    if (hp.ops[o].type == OP_DENSE)
+      for (int e = 0; e < 4; ++e) per_op[4 * o + e] = hp.mats[4 * (size_t)hp.ops[o].mat + e];
+  put(L.o_mats, per_op);
   put(L.o_tabs, hp.tabs);
   return L;
 }

@@ -52,6 +52,49 @@ __device__ __forceinline__ int64_t tile_row_offset(uint32_t h, const int8_t* __r
   return g;
 }
 
+template <int N>
+constexpr int ilog2() {
+  if constexpr (N <= 1) return 0;
+  else return 1 + ilog2<N / 2>();
+}
+
+// Where a thread's load/store vectors sit.  Thread tau (< n_active) moves the
+// vectors l = (tau + it * n_active) * PV, it < NV.  The map from a tile index
+// to its vector offset, (l & low_mask) | tile_row_offset(l >> low), and the
+// shared-memory swizzle are both GF(2)-linear in l, and tau's bits and it's
+// bits are disjoint, so each address is the thread's part XOR the
+// iteration's part, the latter combined from one term per bit of it.
+template <int NVB>
+struct TileMap {
+  int64_t g_t;            // vector offset of l = tau * PV
+  uint32_t p_t;           // swizzled position of l = tau * PV
+  int64_t g_b[NVB > 0 ? NVB : 1];   // offset of l = 2^b * n_active * PV
+  uint32_t p_b[NVB > 0 ? NVB : 1];  // swizzled position of the same
+};
+
+__device__ __forceinline__ int64_t tile_addr(uint32_t l, uint32_t low_mask, int low,
+                                             const int8_t* __restrict__ hi_bits) {
+  return (int64_t)(l & low_mask) | tile_row_offset(l >> low, hi_bits);
+}
+
+template <int PV, int NVB>
+__device__ __forceinline__ TileMap<NVB> make_tile_map(const DPass& P, const DPass* __restrict__ pass,
+                                                      uint32_t n_active) {
+  TileMap<NVB> m;
+  const uint32_t low_mask = (P.low >= 32) ? 0xffffffffu : ((1u << P.low) - 1u);
+  const int8_t* __restrict__ hi_bits = pass->tile_bit + P.low;
+  const uint32_t lt = threadIdx.x * PV;
+  m.g_t = tile_addr(lt, low_mask, P.low, hi_bits);
+  m.p_t = swz(lt);
+#pragma unroll
+  for (int b = 0; b < NVB; ++b) {
+    const uint32_t lb = (n_active * PV) << b;
+    m.g_b[b] = tile_addr(lb, low_mask, P.low, hi_bits);
+    m.p_b[b] = swz(lb);
+  }
+  return m;
+}
+
 template <typename R>
 __device__ __forceinline__ void cmul(R& xr, R& xi, R yr, R yi) {
   const R t = xr * yr - xi * yi;
@@ -161,9 +204,34 @@ struct SlotIndex {
   }
 };
 
+// An op's 2x2 matrix (row-major, interleaved re/im), loaded with 16-byte loads.
+template <typename R>
+struct Mat {
+  R v[8];
+};
+template <typename R>
+__device__ __forceinline__ Mat<R> load_mat(const R* __restrict__ p) {
+  Mat<R> m;
+  if constexpr (sizeof(R) == 4) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    m.v[0] = x.x; m.v[1] = x.y; m.v[2] = x.z; m.v[3] = x.w;
+    m.v[4] = y.x; m.v[5] = y.y; m.v[6] = y.z; m.v[7] = y.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(p) + i);
+      m.v[2 * i] = x.x;
+      m.v[2 * i + 1] = x.y;
+    }
+  }
+  return m;
+}
+
 // 2x2 matrix on register bit RHO of every held pair.
 template <typename R, int RB, int RHO>
-__device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const R* __restrict__ m) {
+__device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const Mat<R>& mm) {
+  const R* m = mm.v;
   using C = typename CT<R>::C;
   constexpr int N = 1 << RB;
   const R u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
@@ -188,46 +256,65 @@ __device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const
 // of two, 2^(k - rbits)) take part in the register stages; every thread of
 // the block shares the loads and stores.  CG loads through L2 only, for
 // vectors that other CTAs of the same launch wrote.
+
+template <typename V>
+__device__ __forceinline__ V swap_pair(V v) {  // (a, b) -> (b, a) for a float4 of two complex64
+  float4 f = reinterpret_cast<float4&>(v);
+  f = make_float4(f.z, f.w, f.x, f.y);
+  return reinterpret_cast<V&>(f);
+}
+
+// Load, transform and store tile T of one pass.  n_active threads (a power
+// of two, 2^(k - RB)) take part; each moves 2^RB amplitudes in NV 16-byte
+// vectors per phase.  CG loads through L2 only, for vectors that other CTAs
+// of the same launch wrote.
 template <typename R, int RB, bool CG>
 __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, const DPass& P,
-                                         const DPass* __restrict__ pass,
                                          const DStage* __restrict__ stages,
                                          const DOp* __restrict__ ops,
                                          const DTerm* __restrict__ terms,
                                          const R* __restrict__ mats, const R* __restrict__ tabs,
-                                         int64_t T, typename CT<R>::C* s, uint32_t n_active) {
+                                         const int8_t* __restrict__ rest_bit, int64_t T,
+                                         typename CT<R>::C* s, uint32_t n_active,
+                                         const TileMap<ilog2<(1 << RB) / CT<R>::PV>()>& tm) {
   using C = typename CT<R>::C;
   using V = typename CT<R>::V;
   constexpr int PV = CT<R>::PV;
   constexpr int N = 1 << RB;
+  constexpr int NV = N / PV;
+  constexpr int NVB = ilog2<NV>();
   const uint32_t n = 1u << P.k;
-  const uint32_t nt = blockDim.x, tid = threadIdx.x;
-  const uint32_t low_mask = (P.low >= 32) ? 0xffffffffu : ((1u << P.low) - 1u);
+  const uint32_t tid = threadIdx.x;
   const uint32_t kmask = n - 1u;
-  const int8_t* __restrict__ hi_bits = pass->tile_bit + P.low;
   const bool active = tid < n_active;
 
   const uint64_t vbase = (uint64_t)T << P.k;
   int64_t gbase = 0;
-  for (int b = 0; b < P.n_rest; ++b) gbase |= ((T >> b) & 1) << pass->rest_bit[b];
+  for (int b = 0; b < P.n_rest; ++b) gbase |= ((T >> b) & 1) << rest_bit[b];
   const bool rest_zero = (((uint64_t)T) & P.zero_rest) == 0;
+  const int64_t g0 = gbase | tm.g_t;
 
   if (!P.init_zero) {
-#pragma unroll 4
-    for (uint32_t u = tid; u < n / PV; u += nt) {
-      const uint32_t l = u * PV;
-      const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-      V val = CG ? __ldcg(reinterpret_cast<const V*>(vec + g)) : *reinterpret_cast<const V*>(vec + g);
-      const uint32_t pl = swz(l);
-      if (PV == 2 && (pl & 1u)) {  // the swizzle swapped the pair
-        V sw = val;
-        reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
-                                                    reinterpret_cast<float4&>(val).w,
-                                                    reinterpret_cast<float4&>(val).x,
-                                                    reinterpret_cast<float4&>(val).y);
-        val = sw;
+    if (active) {
+      V val[NV];
+#pragma unroll
+      for (int it = 0; it < NV; ++it) {
+        int64_t g = g0;
+#pragma unroll
+        for (int b = 0; b < NVB; ++b)
+          if ((it >> b) & 1) g ^= tm.g_b[b];
+        val[it] = CG ? __ldcg(reinterpret_cast<const V*>(vec + g)) : *reinterpret_cast<const V*>(vec + g);
       }
-      *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = val;
+#pragma unroll
+      for (int it = 0; it < NV; ++it) {
+        uint32_t pl = tm.p_t;
+#pragma unroll
+        for (int b = 0; b < NVB; ++b)
+          if ((it >> b) & 1) pl ^= tm.p_b[b];
+        V v = val[it];
+        if (PV == 2 && (pl & 1u)) v = swap_pair(v);  // the swizzle swapped the pair
+        *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = v;
+      }
     }
     __syncthreads();
   }
@@ -272,6 +359,14 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
 #pragma unroll
       for (int j = 0; j < (1 << SlotIndex<RB>::L); ++j) dep.lo[j] |= base;
       const uint64_t cfix = vbase | base;  // the thread's fixed index bits in this stage
+      // swz is GF(2)-linear and dep.lo, dep.hi have disjoint bits:
+      // swz(dep(j)) = swz(dep.lo[.]) ^ swz(dep.hi[.])
+      SlotIndex<RB> sp;
+#pragma unroll
+      for (int j = 0; j < (1 << SlotIndex<RB>::L); ++j) sp.lo[j] = swz(dep.lo[j]);
+#pragma unroll
+      for (int j = 0; j < (1 << SlotIndex<RB>::H); ++j) sp.hi[j] = swz(dep.hi[j]);
+#define CC_SLOT_POS(j) (sp.lo[(j) & ((1 << SlotIndex<RB>::L) - 1)] ^ sp.hi[(j) >> SlotIndex<RB>::L])
 
       C a[N];
       if (P.init_zero && si == P.stage_begin) {
@@ -282,15 +377,17 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < N; ++j) a[j] = s[swz(dep(j))];
+        for (int j = 0; j < N; ++j) a[j] = s[CC_SLOT_POS(j)];
       }
 
+      // op o's matrix sits at mats + 8 o (the image stores one per op), so
+      // the descriptor and the matrix load independently
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const DOp op = ops[o];
+        const Mat<R> m = load_mat<R>(mats + 8 * o);
         if (op.sign_adj != 0 || op.term_end > op.term_begin)
           apply_diag<R, RB>(a, op, cfix, sr, terms, tabs);
         if (op.type == OP_DENSE) {
-          const R* m = mats + 8 * op.mat;
           switch (op.t) {
             case 0: dense_mat<R, RB, 0>(a, m); break;
             case 1: if (RB > 1) dense_mat<R, RB, (RB > 1 ? 1 : 0)>(a, m); break;
@@ -302,26 +399,27 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
       }
 
 #pragma unroll
-      for (int j = 0; j < N; ++j) s[swz(dep(j))] = a[j];
+      for (int j = 0; j < N; ++j) s[CC_SLOT_POS(j)] = a[j];
+#undef CC_SLOT_POS
     }
     __syncthreads();
   }
 
-#pragma unroll 4
-  for (uint32_t u = tid; u < n / PV; u += nt) {
-    const uint32_t l = u * PV;
-    const int64_t g = gbase | (l & low_mask) | tile_row_offset(l >> P.low, hi_bits);
-    const uint32_t pl = swz(l);
-    V val = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
-    if (PV == 2 && (pl & 1u)) {
-      V sw = val;
-      reinterpret_cast<float4&>(sw) = make_float4(reinterpret_cast<float4&>(val).z,
-                                                  reinterpret_cast<float4&>(val).w,
-                                                  reinterpret_cast<float4&>(val).x,
-                                                  reinterpret_cast<float4&>(val).y);
-      val = sw;
+  if (active) {
+#pragma unroll
+    for (int it = 0; it < NV; ++it) {
+      int64_t g = g0;
+      uint32_t pl = tm.p_t;
+#pragma unroll
+      for (int b = 0; b < NVB; ++b)
+        if ((it >> b) & 1) {
+          g ^= tm.g_b[b];
+          pl ^= tm.p_b[b];
+        }
+      V v = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
+      if (PV == 2 && (pl & 1u)) v = swap_pair(v);
+      *reinterpret_cast<V*>(vec + g) = v;
     }
-    *reinterpret_cast<V*>(vec + g) = val;
   }
   __syncthreads();
 }
@@ -336,8 +434,11 @@ __global__ void __launch_bounds__(512)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const DPass P = *pass;
+  constexpr int NVB = ilog2<(1 << RB) / CT<R>::PV>();
+  const TileMap<NVB> tm = make_tile_map<CT<R>::PV, NVB>(P, pass, blockDim.x);
   for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x)
-    run_tile<R, RB, false>(vec, P, pass, stages, ops, terms, mats, tabs, T, s, blockDim.x);
+    run_tile<R, RB, false>(vec, P, stages, ops, terms, mats, tabs, pass->rest_bit, T, s,
+                           blockDim.x, tm);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -415,14 +516,21 @@ __global__ void __launch_bounds__(512)
       const R* mats = reinterpret_cast<const R*>(J.mats);
       const R* tabs = reinterpret_cast<const R*>(J.tabs);
       switch (P.rbits) {
-        case 1: run_tile<R, 1, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
-        case 2: run_tile<R, 2, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
-        case 3: run_tile<R, 3, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
-        case 4: run_tile<R, 4, true>(vec, P, J.pass, J.stages, J.ops, J.terms, mats, tabs, T, s, na); break;
+#define CC_BATCH_TILE(RBV)                                                                       \
+  {                                                                                              \
+    constexpr int NVB = ilog2<(1 << (RBV)) / CT<R>::PV>();                                       \
+    const TileMap<NVB> tm = make_tile_map<CT<R>::PV, NVB>(P, J.pass, na);                       \
+    run_tile<R, (RBV), true>(vec, P, J.stages, J.ops, J.terms, mats, tabs, J.pass->rest_bit, T, \
+                             s, na, tm);                                                         \
+  }
+        case 1: CC_BATCH_TILE(1) break;
+        case 2: CC_BATCH_TILE(2) break;
+        case 3: CC_BATCH_TILE(3) break;
+        case 4: CC_BATCH_TILE(4) break;
         default:
-          run_tile<R, (sizeof(R) == 4 ? 5 : 4), true>(vec, P, J.pass, J.stages, J.ops, J.terms,
-                                                       mats, tabs, T, s, na);
+          CC_BATCH_TILE(sizeof(R) == 4 ? 5 : 4)
           break;
+#undef CC_BATCH_TILE
       }
     }
     __threadfence();
