@@ -7,9 +7,10 @@
 // shared-memory sweeps as possible:
 //   * consecutive one-qubit gates on a qubit multiply into one 2x2 matrix;
 //   * every diagonal factor (CZ, phase gates, cut terms) is deferred and
-//     applied, as a per-amplitude function of index bits, at the start of the
-//     next dense sweep -- diagonal operators commute with each other, and a
-//     deferred factor never touches a qubit whose pending matrix is still open.
+//     applied, as a per-amplitude function of index bits, just before the
+//     first dense matrix on a bit it depends on -- diagonal operators commute
+//     with each other and with matrices on other bits, and a deferred factor
+//     never touches a qubit whose pending matrix is still open.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -259,19 +260,39 @@ struct PassBuilder {
     pend_tab.push_back(t);
   }
 
-  void emit(int type, int t_reg, const cd* u) {
+  // Does a pending diagonal factor depend on index bit vp?
+  bool pending_touches(int vp) const {
+    if ((pend_adj >> vp) & 1ull) return true;
+    if (vp > 0 && ((pend_adj >> (vp - 1)) & 1ull)) return true;
+    for (const auto& d : pend_sign)
+      if (d.p0 == vp || d.p1 == vp) return true;
+    for (const auto& d : pend_tab)
+      if (d.p0 == vp || d.p1 == vp) return true;
+    return false;
+  }
+
+  // Emit an op on index bit vp.  Pending diagonal factors commute with a
+  // matrix on a bit they do not depend on, so they stay pending until an op
+  // whose bit one of them depends on (or the pass's final OP_DIAG); then all
+  // of them ride on that op at once, and a layer of CZs costs one sign sweep.
+  void emit(int type, int t_reg, const cd* u, int vp) {
     DOp op{};
     op.type = type;
     op.t = t_reg;
-    op.sign_adj = pend_adj;
+    const bool attach = type == OP_DIAG || pending_touches(vp);
+    op.sign_adj = attach ? pend_adj : 0;
     op.term_begin = (int32_t)hp.terms.size();
-    for (auto& d : pend_sign) hp.terms.push_back(d);
+    if (attach)
+      for (auto& d : pend_sign) hp.terms.push_back(d);
     op.term_sign_end = (int32_t)hp.terms.size();
-    for (auto& d : pend_tab) hp.terms.push_back(d);
+    if (attach)
+      for (auto& d : pend_tab) hp.terms.push_back(d);
     op.term_end = (int32_t)hp.terms.size();
-    pend_sign.clear();
-    pend_tab.clear();
-    pend_adj = 0;
+    if (attach) {
+      pend_sign.clear();
+      pend_tab.clear();
+      pend_adj = 0;
+    }
     op.mat = -1;
     if (u) {
       op.mat = (int32_t)(hp.mats.size() / 4);
@@ -289,7 +310,7 @@ struct PassBuilder {
     if (is_zero(u[1]) && is_zero(u[2])) {
       add_diag1(j, u[0], u[3]);
     } else {
-      emit(OP_DENSE, reg_of[j], u);
+      emit(OP_DENSE, reg_of[j], u, vpos[j]);
     }
   }
 
@@ -344,7 +365,7 @@ struct PassBuilder {
   // pending into the next stage of the same pass.
   void end_stage(DStage& st, bool last) {
     for (int j = 0; j < nq; ++j) flush(j);
-    if (last && pending_terms()) emit(OP_DIAG, 0, nullptr);
+    if (last && pending_terms()) emit(OP_DIAG, 0, nullptr, -1);
     st.op_end = (int32_t)hp.ops.size();
   }
 };

@@ -1,7 +1,7 @@
 // FP64 verification reductions (max |a - b|, max |b|, <a|b>, <a|a>, <b|b>) and
-// the sampled-amplitude gather.  Every product and sum is taken in double
-// precision whatever the storage precision; complex64 inputs are widened
-// exactly before use.
+// the sampled-amplitude gather.  complex128 inputs: every product and sum in
+// FP64.  complex64 inputs: exact FP32 products, double-float runs, FP64
+// across runs (see compare_partial_c64).
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -47,6 +47,68 @@ __device__ Acc6 block_reduce(Acc6 v) {
     for (int m = 16; m >= 1; m >>= 1) combine(v, shfl_xor(v, m));
   }
   return v;
+}
+
+// Double-float accumulator (hi + lo, two FP32): exact products via FMA
+// (Dekker's TwoProduct) added with Knuth's TwoSum, so a run of R products
+// carries a relative error of about R * 2^-48 instead of R * 2^-24.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF& s, float x, float y) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);  // x*y = p + e exactly
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+
+constexpr int kRun = 64;  // elements per thread between FP64 accumulations
+
+// complex64 inputs: the products are formed exactly in FP32 and summed in
+// double-float over runs of kRun elements per thread; each run's sum is then
+// added in FP64.  GB300's FP64 rate (1/64 of FP32) would otherwise bound the
+// pass at ~20 FP64 operations per element, far below the HBM rate.  The
+// maxima are taken in FP32 (the differences of nearby FP32 values are
+// exact; the squares carry 2^-24 relative error).
+__global__ void __launch_bounds__(RB)
+    compare_partial_c64(const float2* __restrict__ a, const float2* __restrict__ b, int64_t n,
+                        double* __restrict__ partials) {
+  Acc6 v{0, 0, 0, 0, 0, 0};
+  float d2 = 0.f, b2 = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * RB;
+  int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x;
+  while (i < n) {
+    DF re{0.f, 0.f}, im{0.f, 0.f}, na{0.f, 0.f}, nb{0.f, 0.f};
+    for (int r = 0; r < kRun && i < n; ++r, i += stride) {
+      const float2 x = __ldcs(a + i), y = __ldcs(b + i);
+      const float dr = x.x - y.x, di = x.y - y.y;
+      d2 = fmaxf(d2, fmaf(dr, dr, di * di));
+      b2 = fmaxf(b2, fmaf(y.x, y.x, y.y * y.y));
+      df_add_prod(re, x.x, y.x);  // Re conj(a) b = ar br + ai bi
+      df_add_prod(re, x.y, y.y);
+      df_add_prod(im, x.x, y.y);  // Im conj(a) b = ar bi - ai br
+      df_add_prod(im, -x.y, y.x);
+      df_add_prod(na, x.x, x.x);
+      df_add_prod(na, x.y, x.y);
+      df_add_prod(nb, y.x, y.x);
+      df_add_prod(nb, y.y, y.y);
+    }
+    v.re += df_value(re);
+    v.im += df_value(im);
+    v.na += df_value(na);
+    v.nb += df_value(nb);
+  }
+  v.d2 = d2;
+  v.b2 = b2;
+  v = block_reduce(v);
+  if (threadIdx.x == 0) {
+    double* p = partials + 8 * blockIdx.x;
+    p[0] = v.d2; p[1] = v.b2; p[2] = v.re; p[3] = v.im; p[4] = v.na; p[5] = v.nb;
+  }
 }
 
 template <typename C>
@@ -106,7 +168,7 @@ cc_status launch_compare(const void* a, const void* b, int64_t n, int precision,
   if (precision == CC_C128)
     compare_partial<double2><<<n_blocks, RB, 0, s>>>((const double2*)a, (const double2*)b, n, partials);
   else
-    compare_partial<float2><<<n_blocks, RB, 0, s>>>((const float2*)a, (const float2*)b, n, partials);
+    compare_partial_c64<<<n_blocks, RB, 0, s>>>((const float2*)a, (const float2*)b, n, partials);
   compare_final<<<1, RB, 0, s>>>(partials, n_blocks, out_dev);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("compare launch: ") + cudaGetErrorString(e));
