@@ -161,7 +161,12 @@ void cc_plan_destroy(cc_plan* plan);
  * 2^{c_i} 2^{q_i}), variant r at seg_offset[i] + r 2^{q_i}.  Bit t of r
  * selects the term of the t-th cut adjacent to segment i (circuit order).
  * seg_buf_bytes must be >= info.seg_buf_bytes (else CC_EBUFSIZE).
- * Asynchronous on `stream`. */
+ * All passes of all segments run in one persistent launch (a queue of
+ * (pass, tile) items, each pass waiting with a bounded poll for the previous
+ * pass of its segment); its per-run counters live in the plan, so calls on
+ * one plan must not overlap in time (use one plan per concurrent stream).
+ * CUTSIM_SEG_LAUNCH=passes selects one launch per pass instead.
+ * Asynchronous on `stream`; an expired wait is reported by cc_sync. */
 cc_status cc_simulate_segments(const cc_plan* plan, void* seg_buf, uint64_t seg_buf_bytes,
                                void* stream);
 

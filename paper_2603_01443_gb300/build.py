@@ -46,6 +46,7 @@ def commands(ptxas_verbose: bool = False):
     nvcc = _nvcc()
     cxx = _cxx()
     inc = ["-I", INCLUDE, "-I", CSRC]
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
     jobs = []
     for src in CU_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
@@ -56,7 +57,7 @@ def commands(ptxas_verbose: bool = False):
         jobs.append((cmd, obj))
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-c",
+        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I", cuda_inc, "-c",
                os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
     link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB] + [o for _, o in jobs]

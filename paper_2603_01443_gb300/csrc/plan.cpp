@@ -16,6 +16,8 @@
 // ... .  For n >= 3 segments on a line, the merge absorbs one segment at a
 // time (see merge stages below), which needs every cut between neighbouring
 // segments.
+#include <cuda_runtime.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -242,14 +244,73 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     const size_t tab_off = (img.size() + 255) & ~size_t(255);
     img.resize(tab_off + tab.size() * sizeof(int32_t));
     if (!tab.empty()) std::memcpy(img.data() + tab_off, tab.data(), tab.size() * sizeof(int32_t));
-    p->arena = device_alloc_copy(img.data(), img.size());
-    if (!p->arena) return fail(CC_ENOMEM, "device allocation of the plan tables failed");
+    // The segment passes as jobs of one persistent launch (see
+    // cc_simulate_segments), then that launch's per-run counters.
+    int n_jobs = 0, max_pass = 0;
+    for (int i = 0; i < n_seg; ++i) {
+      n_jobs += (int)p->hprog[i].passes.size();
+      max_pass = std::max(max_pass, (int)p->hprog[i].passes.size());
+    }
+    const size_t jobs_off = (img.size() + 255) & ~size_t(255);
+    const size_t state_off = (jobs_off + n_jobs * sizeof(BJob) + 255) & ~size_t(255);
+    const size_t head_off = (state_off + n_jobs * sizeof(int) + 15) & ~size_t(15);
+    img.resize(head_off + sizeof(unsigned long long), 0);
+    void* arena = nullptr;
+    if (cudaMalloc(&arena, img.size()) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CC_ENOMEM, "device allocation of the plan tables failed");
+    }
+    p->arena = arena;
     unsigned char* dev = static_cast<unsigned char*>(p->arena);
     for (int i = 0; i < n_seg; ++i) {
       DeviceProgram dp;
       bind_program(dp, p->hprog[i], dev, lay[i]);
       p->dprog.push_back(dp);
     }
+    std::vector<BJob> jobs;
+    std::vector<std::vector<int>> job_of(n_seg);
+    int64_t n_items = 0;
+    int block = 32, kmax = 0;
+    for (int pi = 0; pi < max_pass; ++pi)
+      for (int i = 0; i < n_seg; ++i) {
+        const DeviceProgram& dp = p->dprog[i];
+        if (pi >= (int)dp.passes.size()) continue;
+        const DPass& P = dp.passes[pi];
+        BJob J{};
+        J.vec_off = p->seg_off[i];
+        J.pass = reinterpret_cast<const DPass*>(static_cast<const char*>(dp.passes_dev) +
+                                                sizeof(DPass) * pi);
+        J.stages = dp.stages;
+        J.ops = dp.ops;
+        J.terms = dp.terms;
+        J.mats = dp.mats;
+        J.tabs = dp.tabs;
+        J.tile_begin = n_items;
+        J.n_tiles = int64_t(1) << (P.nq - P.k);
+        J.dep = pi > 0 ? job_of[i][pi - 1] : -1;
+        job_of[i].push_back((int)jobs.size());
+        jobs.push_back(J);
+        n_items += J.n_tiles;
+        block = std::max(block, 1 << (P.k - P.rbits));
+        kmax = std::max(kmax, P.k);
+      }
+    if (!jobs.empty()) std::memcpy(img.data() + jobs_off, jobs.data(), jobs.size() * sizeof(BJob));
+    if (cudaMemcpy(arena, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CC_ECUDA, "upload of the plan tables failed");
+    }
+    p->seg_jobs = reinterpret_cast<const BJob*>(dev + jobs_off);
+    p->seg_state = dev + state_off;
+    p->seg_state_bytes = img.size() - state_off;
+    p->seg_done = reinterpret_cast<int*>(dev + state_off);
+    p->seg_head = reinterpret_cast<unsigned long long*>(dev + head_off);
+    p->seg_n_jobs = (int)jobs.size();
+    p->seg_n_items = n_items;
+    p->seg_block = block;
+    p->seg_smem = (size_t)ab << kmax;
+    const int occ = batch_segments_occupancy(precision, block, p->seg_smem);
+    p->seg_grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)num_sms() * std::max(occ, 1)));
+    if (!device_error_flag()) return fail(CC_ENOMEM, "device error flag allocation failed");
     p->tables_dev = tab.empty() ? nullptr : dev + tab_off;
     p->table_bytes = img.size();
     *out = p.release();

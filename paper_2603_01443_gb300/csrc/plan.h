@@ -12,6 +12,7 @@ void* device_alloc_copy(const void* host, size_t bytes);  // NULL on failure
 void device_free(void* p);
 int uncut_tile_bits(int precision);
 int seg_tile_bits(int precision);
+bool seg_launch_per_pass();  // CUTSIM_SEG_LAUNCH=passes: one launch per segment pass
 }  // namespace cc
 
 struct cc_plan;
@@ -47,6 +48,15 @@ struct cc_plan {
   int64_t n_sub = 0;
   uint64_t seg_buf_bytes = 0, psi_bytes = 0, workspace_bytes = 0, table_bytes = 0;
   uint64_t chain_ws_amps = 0;  // amplitudes of one chained-merge intermediate buffer
+  // Every segment pass as one job of a persistent launch (inside arena).
+  const cc::BJob* seg_jobs = nullptr;
+  void* seg_state = nullptr;  // per-run counters, zeroed before each launch
+  size_t seg_state_bytes = 0;
+  int* seg_done = nullptr;
+  unsigned long long* seg_head = nullptr;
+  int seg_n_jobs = 0, seg_block = 32, seg_grid = 1;
+  int64_t seg_n_items = 0;
+  size_t seg_smem = 0;
 
   ~cc_plan();
 };

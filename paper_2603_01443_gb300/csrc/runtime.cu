@@ -144,6 +144,11 @@ int seg_tile_bits(int precision) {
   return k;
 }
 
+bool seg_launch_per_pass() {
+  const char* e = std::getenv("CUTSIM_SEG_LAUNCH");
+  return e && std::strcmp(e, "passes") == 0;
+}
+
 int uncut_tile_bits(int precision) {
   // 2^13 as for segments: two CTAs per SM hide the tile load/store latency
   // (measured ~5% faster than 2^14 on the 30-qubit brickwork)
@@ -253,13 +258,22 @@ extern "C" cc_status cc_simulate_segments(const cc_plan* p, void* seg_buf, uint6
                                  std::to_string(p->seg_buf_bytes));
   cc_status st = check_device();
   if (st != CC_OK) return st;
-  const int ab = amp_bytes(p->precision);
-  for (int i = 0; i < p->n_seg; ++i) {
-    char* base = static_cast<char*>(seg_buf) + p->seg_off[i] * ab;
-    st = run_program(p->dprog[i], p->precision, base, stream);
-    if (st != CC_OK) return st;
+  if (seg_launch_per_pass()) {  // one launch per pass and segment
+    const int ab = amp_bytes(p->precision);
+    for (int i = 0; i < p->n_seg; ++i) {
+      char* base = static_cast<char*>(seg_buf) + p->seg_off[i] * ab;
+      st = run_program(p->dprog[i], p->precision, base, stream);
+      if (st != CC_OK) return st;
+    }
+    return CC_OK;
   }
-  return CC_OK;
+  // Default: every pass of every segment in one persistent launch, so the
+  // segments' passes overlap instead of running one after another.
+  const cudaError_t e = cudaMemsetAsync(p->seg_state, 0, p->seg_state_bytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
+  return launch_batch_segments(seg_buf, p->seg_jobs, p->seg_n_jobs, p->seg_n_items, p->seg_done,
+                               p->seg_head, nullptr, p->precision, p->seg_block, p->seg_smem,
+                               p->seg_grid, stream);
 }
 
 extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t seg_bytes,

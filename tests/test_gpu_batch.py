@@ -104,3 +104,20 @@ def test_batch_rejects_small_buffers(cuda_lib):
     with pytest.raises(capi.CutsimError) as e:
         b.launch()
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_persistent_segment_launch_equals_per_pass(cuda_lib, monkeypatch, prec):
+    # cc_simulate_segments runs every segment pass in one persistent launch by
+    # default; one launch per pass must give the same bits
+    for segs, c, depth in (([9, 10], 4, 8), ([6, 7, 7], [2, 3], 12), ([15, 5], 3, 6)):
+        q = sum(segs)
+        gates = w.brickwork_cut(q, depth, 17, segs, c)
+        monkeypatch.delenv("CUTSIM_SEG_LAUNCH", raising=False)
+        psi_a, seg_a, _ = gpu_cut(gates, q, segs, "s_sdg", prec, "fma")
+        monkeypatch.setenv("CUTSIM_SEG_LAUNCH", "passes")
+        psi_b, seg_b, _ = gpu_cut(gates, q, segs, "s_sdg", prec, "fma")
+        sync()
+        assert torch.equal(seg_a, seg_b)
+        assert torch.equal(psi_a, psi_b)
+        assert rel_err(psi_a.cpu().numpy(), sv.simulate(q, gates)) <= TOL[prec]
