@@ -51,7 +51,7 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["boundary", "batch"], default=None,
+    p.add_argument("--sweep", choices=["boundary", "batch", "paper"], default=None,
                    help="run a measurement sweep instead of the single-line benchmark")
     p.add_argument("--sweep-cmax", type=int, default=20,
                    help="largest c_total of the boundary sweep (capped by the depth)")
@@ -345,6 +345,142 @@ def sweep_boundary(a):
     return 0
 
 
+def measure_point(gates, q, segs, prec, decomp, reps=3):
+    """Mean (T_pre, T_sub, T_merge, T_orig) of one circuit over `reps` runs
+    after one warm-up; buffers allocated outside the timing."""
+    import torch
+
+    from paper_2603_01443_gb300 import api, capi
+
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    packed = capi.GateArray(gates)
+    probe = api.CutPlan(packed, q, segs, decomp, prec)
+    seg, psi, ws = probe.alloc_seg_buf(), probe.alloc_psi(), probe.alloc_workspace()
+    probe.close()
+    psi_u = torch.empty_like(psi)
+    rec = []
+    for rep in range(1 + reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = api.CutPlan(packed, q, segs, decomp, prec)
+        t_pre = time.perf_counter() - t0
+        ev[0].record(stream)
+        plan.simulate_segments(seg, stream)
+        ev[1].record(stream)
+        plan.merge(seg, psi, ws, "auto", stream)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        t1 = time.perf_counter()
+        up = api.UncutPlan(packed, q, prec)
+        t_up = time.perf_counter() - t1
+        ev[3].record(stream)
+        up.simulate(psi_u, stream)
+        ev[4].record(stream)
+        ev[4].synchronize()
+        if rep:
+            rec.append((t_pre, ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3,
+                        t_up + ev[3].elapsed_time(ev[4]) / 1e3))
+        plan.close()
+        up.close()
+    capi.check(capi.lib().cc_sync(stream.cuda_stream), "cc_sync")
+    return tuple(statistics.mean(x) for x in zip(*rec))
+
+
+def fit_boundary(points, iters=4000, lr=0.05):
+    """Linear boundary c = slope * q + intercept between the speedup (Delta < 0)
+    and slowdown points of a (q, c_total) grid: a class-balanced linear
+    soft-margin SVM (hinge loss, L2 penalty) fitted by subgradient descent on
+    standardised features, as the paper fits its measured boundary with a
+    weighted SVM.  Returns None when one class is empty."""
+    import numpy as np
+
+    X = np.array([[p[0], p[1]] for p in points], dtype=float)
+    y = np.array([1.0 if p[2] > 0 else -1.0 for p in points])
+    if (y > 0).all() or (y < 0).all():
+        return None
+    mu, sd = X.mean(0), X.std(0) + 1e-12
+    Z = (X - mu) / sd
+    wts = np.where(y > 0, 0.5 / (y > 0).mean(), 0.5 / (y < 0).mean())
+    w = np.zeros(2)
+    b = 0.0
+    lam = 1e-3
+    for t in range(iters):
+        m = y * (Z @ w + b)
+        act = m < 1
+        gw = lam * w - (wts[act, None] * y[act, None] * Z[act]).sum(0) / len(y)
+        gb = -(wts[act] * y[act]).sum() / len(y)
+        step = lr / (1 + t / 500)
+        w -= step * gw
+        b -= step * gb
+    # back to (q, c): w0 (q - mu0)/sd0 + w1 (c - mu1)/sd1 + b = 0
+    a0, a1 = w[0] / sd[0], w[1] / sd[1]
+    c0 = b - a0 * mu[0] - a1 * mu[1]
+    if abs(a1) < 1e-12:
+        return None
+    return {"slope": float(-a0 / a1), "intercept": float(-c0 / a1)}
+
+
+def sweep_paper(a):
+    """The paper's own workload on this GPU (Sec. V.B, V.C): the H/T/CX
+    staircase (Fig. 1; c_total = blocks x (n - 1)), equal partitions, the
+    Delta grids of Fig. 4 -- n = 2: q = 2..24 step 2 (extended to 28),
+    c_total = 1..10; n = 3: q = 3..24 step 3 (extended to 27), c_total =
+    2..14 step 2 -- with a fitted linear boundary next to the paper's fits
+    (0.70 q - 7.30, 1.00 q - 11.50) and Eqs. 13-14; then the depth sweep
+    (10^p T/X layers on the edge qubits, p = 0, 2, 3, 4) at n = 2."""
+    import math
+
+    import torch
+
+    import workload as w
+
+    torch.cuda.set_device(0)
+    prec = a.prec
+    fits = {}
+    grids = {2: ([*range(2, 25, 2), 26, 28], list(range(1, 11))),
+             3: ([*range(3, 25, 3), 27], list(range(2, 15, 2)))}
+    for n, (qs, cs) in grids.items():
+        pts = []
+        for q in qs:
+            segs = w.equal_partition(q, n)
+            for c in cs:
+                blocks = c // (n - 1)
+                gates = w.staircase(q, blocks)
+                pre, sub, mer, orig = measure_point(gates, q, segs, prec, a.decomp)
+                cut = pre + sub + mer
+                delta = (cut - orig) / orig
+                pts.append((q, c, delta))
+                print(json.dumps({"sweep": "paper", "family": "staircase", "precision": prec,
+                                  "n": n, "q": q, "c_total": c, "pre_s": pre, "sub_s": sub,
+                                  "merge_s": mer, "cut_s": cut, "orig_s": orig, "delta": delta}),
+                      flush=True)
+        fits[f"n{n}"] = fit_boundary(pts)
+    depth = {}
+    for pexp in (0, 2, 3, 4):
+        pts = []
+        for q in range(4, 25, 4):
+            for c in range(1, 11):
+                gates = w.staircase_depth(q, c, pexp)
+                pre, sub, mer, orig = measure_point(gates, q, w.equal_partition(q, 2), prec,
+                                                    a.decomp, reps=2)
+                cut = pre + sub + mer
+                delta = (cut - orig) / orig
+                pts.append((q, c, delta))
+                print(json.dumps({"sweep": "paper", "family": "staircase_depth", "p": pexp,
+                                  "precision": prec, "n": 2, "q": q, "c_total": c,
+                                  "n_gates": len(gates), "pre_s": pre, "sub_s": sub,
+                                  "merge_s": mer, "cut_s": cut, "orig_s": orig,
+                                  "delta": delta}), flush=True)
+        depth[f"p{pexp}"] = fit_boundary(pts)
+    print(json.dumps({"sweep": "paper", "precision": prec, "fit": fits, "depth_fit": depth,
+                      "paper_fit": {"n2": {"slope": 0.70, "intercept": -7.30},
+                                    "n3": {"slope": 1.00, "intercept": -11.50}},
+                      "theory": {"n2": {"slope": 0.5, "intercept": 0.0},
+                                 "n3": {"slope": 2.0 / 3.0, "intercept": math.log2(3)}}}))
+    return 0
+
+
 def sweep_batch(a, n_circ=64):
     """Batched uneven workload: n_circ independent random brickwork circuits
     (q uniform in 16..26, depth in {8, 16, 32}, n in {2, 3} unequal segments,
@@ -461,6 +597,8 @@ def main(argv=None):
         return sweep_boundary(a)
     if a.sweep == "batch":
         return sweep_batch(a)
+    if a.sweep == "paper":
+        return sweep_paper(a)
 
     import torch
     import torch.distributed as dist

@@ -121,6 +121,20 @@ def test_staircase_cx_cuts(cuda_lib, prec, segs):
     assert_parity(psi.cpu().numpy(), sv.simulate(12, gates), prec, "staircase")
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("p", [0, 2, 3])
+def test_depth_augmented_staircase(cuda_lib, prec, p):
+    # 10^p T/X layers on the edge qubits (the paper's depth sweep family)
+    q = 10
+    gates = w.staircase_depth(q, 4, p)
+    for segs in ([5, 5], [4, 3, 3]):
+        psi, _, plan = gpu_cut(gates, q, segs, "projector", prec)
+        assert plan.info["c_total"] == 4 * (len(segs) - 1)
+        assert_parity(psi.cpu().numpy(), sv.simulate(q, gates), prec, f"depth p={p}")
+    psi_u, _ = gpu_uncut(gates, q, prec)
+    assert_parity(psi_u.cpu().numpy(), sv.simulate(q, gates), prec, "uncut depth")
+
+
 def test_ghz_closed_form(cuda_lib):
     q = 16
     psi, _, _ = gpu_cut(w.ghz(q), q, [8, 8], "projector", "c128")

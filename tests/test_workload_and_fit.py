@@ -1,0 +1,60 @@
+"""Host logic with no GPU: the workload generators' structure (batched
+uneven circuits, the depth-augmented staircase) and the boundary fit used by
+the paper-workload sweep."""
+
+import math
+
+import pytest
+
+import bench
+import workload as w
+
+
+def test_uneven_batch_obeys_its_ranges():
+    items = w.uneven_batch(64, 0)
+    assert len(items) == 64
+    for it in items:
+        assert 16 <= it.q <= 26 and it.depth in (8, 16, 32)
+        assert len(it.seg_sizes) in (2, 3) and sum(it.seg_sizes) == it.q
+        assert min(it.seg_sizes) >= 4
+        assert 2 <= sum(it.cuts_per_boundary) <= 6
+        # the boundary CZs are exactly the requested cuts
+        bounds, acc = [], 0
+        for s in it.seg_sizes[:-1]:
+            acc += s
+            bounds.append(acc)
+        crossing = sum(1 for g in it.gates if g.kind == "CZ" and g.q1 in bounds and g.q0 == g.q1 - 1)
+        assert crossing == sum(it.cuts_per_boundary)
+    assert w.uneven_batch(8, 3) == w.uneven_batch(8, 3)  # seeded
+
+
+def test_staircase_depth_structure():
+    q, blocks, p = 7, 3, 2
+    base = w.staircase(q, blocks)
+    g = w.staircase_depth(q, blocks, p)
+    assert len(g) == len(base) + 2 * 10 ** p
+    pad_top = g[q:q + 100]
+    assert [x.kind for x in pad_top[:4]] == ["T", "X", "T", "X"]
+    assert all(x.q0 == 0 for x in pad_top)
+    assert all(x.q0 == q - 1 for x in g[-100:])
+    assert g[:q] == base[:q] and g[q + 100:-100] == base[q:]
+    # cut count unchanged: one boundary CX per block for n = 2
+    cuts = sum(1 for x in g if x.kind == "CX" and x.q0 < q // 2 <= x.q1)
+    assert cuts == blocks
+
+
+@pytest.mark.parametrize("slope,intercept", [(0.5, 0.0), (0.7, -7.3), (1.0, -11.5)])
+def test_fit_boundary_recovers_a_separating_line(slope, intercept):
+    pts = [(q, c, c - (slope * q + intercept)) for q in range(2, 31, 2) for c in range(0, 15)
+           if abs(c - (slope * q + intercept)) > 1e-9]
+    fit = bench.fit_boundary(pts)
+    # every grid point is classified as the line it was drawn from classifies it,
+    # except possibly points within one grid step of the line
+    for q, c, d in pts:
+        side = c - (fit["slope"] * q + fit["intercept"])
+        if abs(d) > 1.0:
+            assert math.copysign(1, side) == math.copysign(1, d), (q, c, d, fit)
+
+
+def test_fit_boundary_needs_both_classes():
+    assert bench.fit_boundary([(4, 1, -0.5), (6, 2, -0.1)]) is None

@@ -17,6 +17,7 @@ from .circuits import (  # noqa: F401
     brickwork,
     brickwork_cut,
     staircase,
+    staircase_depth,
     ghz,
     graph_state,
     random_circuit,

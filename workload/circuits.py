@@ -240,6 +240,18 @@ def staircase(q: int, blocks: int) -> List[Gate]:
     return gates
 
 
+def staircase_depth(q: int, blocks: int, p: int) -> List[Gate]:
+    """The depth-augmented staircase of the paper's depth sweep (Sec. V.C,
+    supplementary Fig. 8): after the H layer, 10^p single-qubit layers on
+    qubit 0, alternating T and X (T first); then the staircase blocks; then
+    10^p more such layers on qubit q-1.  q and the cut count are unchanged."""
+    n_layers = 10 ** p
+    base = staircase(q, blocks)
+    pad_top = [Gate("T" if i % 2 == 0 else "X", 0) for i in range(n_layers)]
+    pad_bot = [Gate("T" if i % 2 == 0 else "X", q - 1) for i in range(n_layers)]
+    return base[:q] + pad_top + base[q:] + pad_bot
+
+
 def ghz(q: int) -> List[Gate]:
     """H on qubit 0, then the CX chain 0->1->...->q-1."""
     return [Gate("H", 0)] + [Gate("CX", j, j + 1) for j in range(q - 1)]
