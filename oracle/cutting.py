@@ -16,6 +16,14 @@ Follows the paper's three phases (Eq. 3, Appendix B):
                                only (same terms, same alpha_m), for q where the
                                2^q vector is too large to build on the host.
 
+Schmidt-rank-4 gates (SWAP, ISWAP, CAN; Eq. 1 with k = 4) are cut with the
+operator-Schmidt decomposition itself, U = sum_l s_l A_l (x) B_l, computed as
+the singular value decomposition of U realigned so that its rows index the
+first qubit's (out, in) pair and its columns the second's (the textbook
+construction); term l puts s_l A_l on the first qubit and B_l on the second.
+A cut with k_j terms contributes a base-k_j digit to the variant and merge
+indices (mixed radix; for k = 2 this is the bit slicing below).
+
 Cut decompositions (Schmidt rank k = 2, Eq. 1):
 
 * ``"s_sdg"``      -- Eq. 2: CZ = [S (x) S + i S^dag (x) S^dag] / (1+i).
@@ -66,10 +74,10 @@ class Preprocessed:
     seg_sizes: List[int]
     seg_starts: List[int]
     cuts: List[CutInfo]
-    coefs: List[Tuple[complex, complex]]   # per cut j: (coef for b=0, coef for b=1)
+    coefs: List[Tuple[complex, ...]]       # per cut j: coefficient of each term
     seg_cuts: List[List[int]]              # per segment: adjacent cut indices, circuit order
     fragments: List[List[List[sv.Op]]]     # per segment: F_i^(0..c_i) (local qubit indices)
-    subcircuits: List[List[List[sv.Op]]]   # per segment: S_i^(r), r = 0..2^{c_i}-1
+    subcircuits: List[List[List[sv.Op]]]   # per segment: S_i^(r), r = 0..prod k - 1
     merge_table: List[Tuple[int, ...]] = field(default_factory=list)  # M[m] = (r_1..r_n)
 
     @property
@@ -77,13 +85,41 @@ class Preprocessed:
         return len(self.cuts)
 
     @property
+    def ranks(self) -> List[int]:
+        return [len(c) for c in self.coefs]
+
+    @property
+    def n_terms(self) -> int:
+        return len(self.merge_table)
+
+    @property
     def n_sub(self) -> int:
         return sum(len(s) for s in self.subcircuits)
 
 
-def local_terms(kind: str, decomp: str):
-    """Per term b in {0,1}: (coefficient, operator on the gate's first qubit,
-    operator on its second qubit)."""
+def schmidt_terms(u: np.ndarray, rtol: float = 1e-12):
+    """Operator-Schmidt decomposition (Eq. 1) of a 4x4 matrix in the basis
+    |x_a x_b>: U = sum_l s_l kron(A_l, B_l).  Realign U into
+    R[(out_a, in_a), (out_b, in_b)] and take its SVD R = W diag(s) V^H; then
+    A_l = W[:, l] and B_l = V^H[l, :], each reshaped to 2x2.  Terms with
+    s_l <= rtol * s_0 are dropped, so len(result) is the Schmidt rank k."""
+    r = u.reshape(2, 2, 2, 2).transpose(0, 2, 1, 3).reshape(4, 4)
+    w, sig, vh = np.linalg.svd(r)
+    keep = [l for l in range(4) if sig[l] > rtol * sig[0]]
+    coef = tuple(complex(sig[l]) for l in keep)
+    first = tuple(w[:, l].reshape(2, 2) for l in keep)
+    second = tuple(vh[l, :].reshape(2, 2) for l in keep)
+    return coef, first, second
+
+
+def local_terms(kind: str, decomp: str, gate=None):
+    """Per term: (coefficient, operator on the gate's first qubit, operator on
+    its second qubit).  CZ and CX use the chosen rank-2 split; SWAP, ISWAP
+    and CAN the operator-Schmidt decomposition of their matrix."""
+    if kind in ("SWAP", "ISWAP", "CAN"):
+        if gate is None or gate.kind != kind:
+            raise ValueError(f"a {kind} cut needs its gate")
+        return schmidt_terms(sv.gate_matrix(gate))
     if decomp == "s_sdg":
         coef = (1.0 / (1.0 + 1.0j), 1.0j / (1.0 + 1.0j))
         first = (sv.S, sv.SDG)
@@ -99,6 +135,22 @@ def local_terms(kind: str, decomp: str):
     elif kind != "CZ":
         raise ValueError(f"cannot cut a {kind} gate with a rank-2 decomposition")
     return coef, first, second
+
+
+def digit(r: int, radix: Sequence[int], t: int) -> int:
+    """Digit t of r in the mixed radix `radix` (digit 0 least significant)."""
+    for k in radix[:t]:
+        r //= k
+    return r % radix[t]
+
+
+def compose(digits: Sequence[int], radix: Sequence[int]) -> int:
+    """Inverse of digit(): sum_t digits[t] * prod(radix[:t])."""
+    r, w = 0, 1
+    for d, k in zip(digits, radix):
+        r += d * w
+        w *= k
+    return r
 
 
 def segment_map(q: int, seg_sizes: Sequence[int]):
@@ -123,6 +175,7 @@ def preprocess(q: int, gates: Sequence, seg_sizes: Sequence[int],
     # Scan C and identify the gates that straddle partition boundaries; every
     # other gate goes, with local qubit indices, into its segment's item list.
     cuts: List[CutInfo] = []
+    cut_gates = []
     items: List[list] = [[] for _ in range(n)]
     for g in gates:
         m, qs = sv.gate_op(g)
@@ -130,6 +183,7 @@ def preprocess(q: int, gates: Sequence, seg_sizes: Sequence[int],
         if len(qs) == 2 and segs[0] != segs[1]:
             j = len(cuts)
             cuts.append(CutInfo(j, g.kind, (qs[0], qs[1]), (segs[0], segs[1])))
+            cut_gates.append(g)
             items[segs[0]].append(("cut", j, 0, qs[0] - starts[segs[0]]))
             items[segs[1]].append(("cut", j, 1, qs[1] - starts[segs[1]]))
         else:
@@ -137,11 +191,12 @@ def preprocess(q: int, gates: Sequence, seg_sizes: Sequence[int],
             items[s].append(("gate", (m, tuple(x - starts[s] for x in qs))))
 
     coefs, firsts, seconds = [], [], []
-    for c in cuts:
-        co, fi, se = local_terms(c.kind, decomp)
+    for c, g in zip(cuts, cut_gates):
+        co, fi, se = local_terms(c.kind, decomp, g)
         coefs.append(co)
         firsts.append(fi)
         seconds.append(se)
+    ranks = [len(co) for co in coefs]
 
     seg_cuts: List[List[int]] = []
     fragments: List[List[List[sv.Op]]] = []
@@ -158,23 +213,25 @@ def preprocess(q: int, gates: Sequence, seg_sizes: Sequence[int],
                 frags.append([])
         seg_cuts.append([mk[0] for mk in markers])
         fragments.append(frags)
-        ci = len(markers)
+        radix = [ranks[mk[0]] for mk in markers]
         subs = []
-        for r in range(1 << ci):
+        for r in range(int(np.prod(radix, dtype=np.int64)) if radix else 1):
             ops = list(frags[0])
             for t, (j, side, lq) in enumerate(markers):
-                b = (r >> t) & 1
+                b = digit(r, radix, t)
                 op_mat = firsts[j][b] if side == 0 else seconds[j][b]
                 ops.append((op_mat, (lq,)))
                 ops.extend(frags[t + 1])
             subs.append(ops)
         subcircuits.append(subs)
 
-    # Merge index table: global combination m -> per-segment indices.
+    # Merge index table: global combination m (one base-k_j digit per cut)
+    # -> per-segment indices (the digits of the segment's adjacent cuts).
     table = []
-    for m in range(1 << len(cuts)):
+    n_terms = int(np.prod(ranks, dtype=np.int64)) if ranks else 1
+    for m in range(n_terms):
         table.append(tuple(
-            sum(((m >> j) & 1) << t for t, j in enumerate(seg_cuts[i]))
+            compose([digit(m, ranks, j) for j in seg_cuts[i]], [ranks[j] for j in seg_cuts[i]])
             for i in range(n)
         ))
     return Preprocessed(q, list(seg_sizes), starts, cuts, coefs, seg_cuts,
@@ -189,10 +246,11 @@ def simulate_subcircuits(pre: Preprocessed) -> List[List[np.ndarray]]:
 
 def alphas(pre: Preprocessed) -> np.ndarray:
     """alpha_m = prod_j coef_j[m_j] for every global combination m."""
-    out = np.ones(1 << pre.c_total, dtype=np.complex128)
-    for m in range(1 << pre.c_total):
+    ranks = pre.ranks
+    out = np.ones(pre.n_terms, dtype=np.complex128)
+    for m in range(pre.n_terms):
         for j in range(pre.c_total):
-            out[m] *= pre.coefs[j][(m >> j) & 1]
+            out[m] *= pre.coefs[j][digit(m, ranks, j)]
     return out
 
 

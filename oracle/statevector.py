@@ -12,7 +12,9 @@ throughout):
   their inverses, H, X, Z the textbook matrices;
 * a two-qubit matrix acting on (qubit a, qubit b) is written in the basis
   |x_a x_b>, i.e. row/column index 2*x_a + x_b, so kron(A, B) puts A on qubit a.
-  CZ = diag(1, 1, 1, -1); CX(control a, target b) flips x_b when x_a = 1.
+  CZ = diag(1, 1, 1, -1); CX(control a, target b) flips x_b when x_a = 1;
+  SWAP exchanges x_a and x_b; ISWAP does so with a factor i on |01>, |10>;
+  CAN(tx, ty, tz) = exp(-i (tx XX + ty YY + tz ZZ) / 2).
 
 The simulator applies the matrices one at a time to a complex128 vector of
 length 2^q by reshaping it so that the target qubit is its own tensor axis.
@@ -42,8 +44,26 @@ CX = np.array(
     [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.complex128
 )
 
+SWAP = np.array(
+    [[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128
+)
+ISWAP = np.array(
+    [[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=np.complex128
+)
+Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+
 FIXED_1Q = {"H": H, "X": X, "Z": Z, "S": S, "SDG": SDG, "T": T, "TDG": TDG}
-FIXED_2Q = {"CZ": CZ, "CX": CX}
+FIXED_2Q = {"CZ": CZ, "CX": CX, "SWAP": SWAP, "ISWAP": ISWAP}
+TWO_QUBIT = ("CZ", "CX", "SWAP", "ISWAP", "CAN")
+
+
+def can(tx: float, ty: float, tz: float) -> np.ndarray:
+    """Canonical two-qubit gate exp(-i (tx XX + ty YY + tz ZZ) / 2), by a
+    library matrix exponential of the Hermitian generator."""
+    from scipy.linalg import expm
+
+    gen = tx * np.kron(X, X) + ty * np.kron(Y, Y) + tz * np.kron(Z, Z)
+    return expm(-0.5j * gen)
 
 
 def u3(theta: float, phi: float, lam: float) -> np.ndarray:
@@ -66,6 +86,8 @@ def gate_matrix(gate) -> np.ndarray:
         return FIXED_1Q[gate.kind]
     if gate.kind in FIXED_2Q:
         return FIXED_2Q[gate.kind]
+    if gate.kind == "CAN":
+        return can(gate.theta, gate.phi, gate.lam)
     raise ValueError(f"unknown gate kind {gate.kind!r}")
 
 
@@ -125,7 +147,7 @@ def simulate(q: int, gates: Sequence) -> np.ndarray:
 
 def check_circuit(q: int, gates: Sequence) -> None:
     for g in gates:
-        qs = (g.q0,) if g.kind not in FIXED_2Q else (g.q0, g.q1)
+        qs = (g.q0,) if g.kind not in TWO_QUBIT else (g.q0, g.q1)
         for x in qs:
             if not 0 <= x < q:
                 raise ValueError(f"qubit {x} out of range for q={q}")

@@ -150,6 +150,76 @@ def test_sampled_amplitudes_match_full_merge(decomp):
 
 def test_uncuttable_gate_rejected():
     with pytest.raises(ValueError):
-        ct.local_terms("SWAP", "projector")
+        ct.local_terms("FOO", "projector")
+    with pytest.raises(ValueError):
+        ct.local_terms("SWAP", "projector")  # a rank-4 cut needs its gate
     with pytest.raises(ValueError):
         ct.preprocess(4, [w.Gate("H", 0)], [2, 1])
+
+
+# ----------------------------------------------------------- rank-4 cuts
+def test_canonical_gate_closed_forms():
+    # CAN(tx, ty, tz) = exp(-i (tx XX + ty YY + tz ZZ) / 2): special angles
+    # reduce to SWAP (up to the phase e^{i pi/4}), ISWAP and textbook forms
+    h = math.pi / 2
+    assert np.max(np.abs(sv.can(-h, -h, -h) - np.exp(1j * math.pi / 4) * sv.SWAP)) < 1e-15
+    assert np.max(np.abs(sv.can(-h, -h, 0.0) - sv.ISWAP)) < 1e-15
+    th = 0.731
+    zz = np.diag(np.exp(-0.5j * th * np.array([1, -1, -1, 1])))
+    assert np.max(np.abs(sv.can(0.0, 0.0, th) - zz)) < 1e-15
+    xx = math.cos(th / 2) * np.eye(4) - 1j * math.sin(th / 2) * np.kron(sv.X, sv.X)
+    assert np.max(np.abs(sv.can(th, 0.0, 0.0) - xx)) < 1e-15
+    # SWAP exchanges the two qubits' basis states
+    for a in range(2):
+        for b in range(2):
+            e = np.zeros(4)
+            e[2 * a + b] = 1
+            assert np.array_equal(sv.SWAP @ e, np.eye(4)[2 * b + a])
+
+
+@pytest.mark.parametrize("gate,rank", [
+    (w.Gate("SWAP", 0, 1), 4), (w.Gate("ISWAP", 0, 1), 4),
+    (w.Gate("CAN", 0, 1, 0.3, 1.1, 2.9), 4), (w.Gate("CAN", 0, 1, 0.0, 0.0, 0.8), 2),
+    (w.Gate("CAN", 0, 1, 1.4, 0.0, 0.0), 2)])
+def test_operator_schmidt_terms_rebuild_the_gate(gate, rank):
+    coef, first, second = ct.local_terms(gate.kind, "projector", gate)
+    assert len(coef) == rank == pins.schmidt_rank(sv.gate_matrix(gate))
+    u = sum(c * np.kron(a, b) for c, a, b in zip(coef, first, second))
+    assert np.max(np.abs(u - sv.gate_matrix(gate))) < 1e-14
+
+
+@pytest.mark.parametrize("kind", ["SWAP", "ISWAP", "CAN"])
+@pytest.mark.parametrize("segs,c", [([5, 5], 2), ([4, 3, 3], [1, 2]), ([3, 4, 3], 1)])
+def test_cut_equals_uncut_rank4_boundaries(kind, segs, c):
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 6, 7, segs, c, boundary_kind=kind)
+    pre = ct.preprocess(q, gates, segs)
+    cpb = [c] * (len(segs) - 1) if isinstance(c, int) else c
+    assert pre.c_total == sum(cpb) and all(k == 4 for k in pre.ranks)
+    # every segment has prod_{adjacent cuts} k_j variants
+    assert pre.n_sub == sum(4 ** len(x) for x in pre.seg_cuts)
+    assert pins.pin_cut_equals_uncut(q, gates, segs, "projector") < 1e-13
+
+
+@pytest.mark.parametrize("seed", [101, 105, 112])
+def test_cut_equals_uncut_mixed_ranks_random_positions(seed):
+    kinds = ("U3", "H", "T", "CZ", "CX", "SWAP", "CAN")
+    gates = w.random_circuit(9, 18, seed, kinds)
+    pre = ct.preprocess(9, gates, [3, 3, 3], "s_sdg")
+    assert pre.n_terms <= 4096, pre.ranks  # keeps the literal merge small
+    assert pins.pin_bruteforce(9, gates) < 1e-13
+    assert pins.pin_cut_equals_uncut(9, gates, [3, 3, 3], "s_sdg") < 1e-12
+
+
+def test_mixed_radix_merge_table():
+    segs = [4, 4, 4]
+    gates = w.brickwork_cut(12, 6, 2, segs, [1, 1], boundary_kind="SWAP")
+    gates = gates + [w.Gate("CZ", 3, 4)]  # one rank-2 cut after the rank-4 ones
+    pre = ct.preprocess(12, gates, segs)
+    assert pre.ranks == [4, 4, 2] and pre.n_terms == 32
+    for m, rs in enumerate(pre.merge_table):
+        d = [m % 4, (m // 4) % 4, m // 16]
+        for i, r in enumerate(rs):
+            radix = [pre.ranks[j] for j in pre.seg_cuts[i]]
+            assert [ct.digit(r, radix, t) for t in range(len(radix))] == \
+                [d[j] for j in pre.seg_cuts[i]]

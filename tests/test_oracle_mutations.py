@@ -24,8 +24,8 @@ def caught(*errs):
 def test_wrong_eq2_coefficient_sign(monkeypatch):
     orig = ct.local_terms
 
-    def bad(kind, decomp):
-        coef, a, b = orig(kind, decomp)
+    def bad(kind, decomp, gate=None):
+        coef, a, b = orig(kind, decomp, gate)
         return (coef[0], -coef[1]), a, b
 
     monkeypatch.setattr(ct, "local_terms", bad)
@@ -36,8 +36,8 @@ def test_wrong_eq2_coefficient_sign(monkeypatch):
 def test_projector_terms_swapped_on_one_side(monkeypatch):
     orig = ct.local_terms
 
-    def bad(kind, decomp):
-        coef, a, b = orig(kind, decomp)
+    def bad(kind, decomp, gate=None):
+        coef, a, b = orig(kind, decomp, gate)
         return coef, a, (b[1], b[0])
 
     monkeypatch.setattr(ct, "local_terms", bad)
@@ -47,7 +47,7 @@ def test_projector_terms_swapped_on_one_side(monkeypatch):
 def test_cx_target_without_hadamards(monkeypatch):
     orig = ct.local_terms
 
-    def bad(kind, decomp):
+    def bad(kind, decomp, gate=None):
         return orig("CZ", decomp)
 
     monkeypatch.setattr(ct, "local_terms", bad)

@@ -12,6 +12,8 @@ from .circuits import (  # noqa: F401
     GATE_KINDS,
     ONE_QUBIT_KINDS,
     TWO_QUBIT_KINDS,
+    RANK4_KINDS,
+    ALL_TWO_QUBIT_KINDS,
     equal_partition,
     cut_layers,
     brickwork,

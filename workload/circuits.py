@@ -35,13 +35,18 @@ MASK64 = (1 << 64) - 1
 ONE_QUBIT_KINDS = ("U3", "H", "X", "Z", "S", "SDG", "T", "TDG")
 TWO_QUBIT_KINDS = ("CZ", "CX")
 GATE_KINDS = ONE_QUBIT_KINDS + TWO_QUBIT_KINDS
+# Schmidt-rank-4 gates (Eq. 1 with k = 4); CAN carries its three angles in
+# (theta, phi, lam).
+RANK4_KINDS = ("SWAP", "ISWAP", "CAN")
+ALL_TWO_QUBIT_KINDS = TWO_QUBIT_KINDS + RANK4_KINDS
 
 
 class Gate(NamedTuple):
     """One gate of a circuit.
 
     ``q1`` is -1 for one-qubit gates.  For CX, ``q0`` is the control and
-    ``q1`` the target.  ``theta, phi, lam`` are only meaningful for U3.
+    ``q1`` the target.  ``theta, phi, lam`` are only meaningful for U3 and,
+    as the angles (t_x, t_y, t_z), for CAN.
     """
 
     kind: str
@@ -122,9 +127,13 @@ def brickwork_cut(
     seed: int,
     seg_sizes: Sequence[int],
     cuts_per_boundary: Union[int, Sequence[int]],
+    boundary_kind: str = "CZ",
 ) -> List[Gate]:
     """Brickwork whose boundary-crossing CZs are chosen to give an exact cut
-    count.
+    count.  ``boundary_kind`` replaces every boundary gate by "SWAP",
+    "ISWAP" or "CAN" (a canonical gate whose three angles come, in order,
+    from a second SplitMix64 stream seeded with seed ^ 0x5EED, uniform in
+    [0, 2*pi)); the brickwork's own angle stream is unchanged.
 
     Boundary b sits between qubits (p-1, p), p = sum(seg_sizes[:b+1]).  All
     natural CZs on boundary pairs are removed; boundary b instead gets a CZ in
@@ -149,14 +158,21 @@ def brickwork_cut(
         bpos.append(acc)
     layer_sets = [set(cut_layers(depth, c)) for c in cpb]
     boundary_lower = {p - 1: b for b, p in enumerate(bpos)}
+    if boundary_kind not in ("CZ",) + RANK4_KINDS:
+        raise ValueError(f"unsupported boundary gate {boundary_kind!r}")
     rng = SplitMix64(seed)
+    rng_can = SplitMix64(seed ^ 0x5EED)
     gates: List[Gate] = []
     for layer in range(depth):
         gates.extend(_u3_layer(rng, q))
         for i in range(0, q - 1):
             if i in boundary_lower:
                 if layer in layer_sets[boundary_lower[i]]:
-                    gates.append(Gate("CZ", i, i + 1))
+                    if boundary_kind == "CAN":
+                        t, p, l = rng_can.next_angle(), rng_can.next_angle(), rng_can.next_angle()
+                        gates.append(Gate("CAN", i, i + 1, t, p, l))
+                    else:
+                        gates.append(Gate(boundary_kind, i, i + 1))
             elif i % 2 == layer % 2:
                 gates.append(Gate("CZ", i, i + 1))
     return gates
@@ -275,13 +291,17 @@ def random_circuit(
     gates: List[Gate] = []
     for _ in range(n_gates):
         kind = kinds[rng.next_u64() % len(kinds)]
-        if kind in TWO_QUBIT_KINDS and q >= 2:
+        if kind in ALL_TWO_QUBIT_KINDS and q >= 2:
             a = rng.next_u64() % q
             b = rng.next_u64() % (q - 1)
             if b >= a:
                 b += 1
-            gates.append(Gate(kind, int(a), int(b)))
-        elif kind in TWO_QUBIT_KINDS:
+            if kind == "CAN":
+                t, p, l = rng.next_angle(), rng.next_angle(), rng.next_angle()
+                gates.append(Gate(kind, int(a), int(b), t, p, l))
+            else:
+                gates.append(Gate(kind, int(a), int(b)))
+        elif kind in ALL_TWO_QUBIT_KINDS:
             continue
         elif kind == "U3":
             t, p, l = rng.next_angle(), rng.next_angle(), rng.next_angle()
