@@ -43,7 +43,7 @@ extern "C" {
 
 #define CC_MAX_QUBITS 34   /* 2^34 complex64 = 128 GiB */
 #define CC_MAX_SEGMENTS 8
-#define CC_MAX_CUTS 24     /* c_total <= 24, at most 2^24 merge terms */
+#define CC_MAX_CUTS 24     /* cut bits <= 24, at most 2^24 merge terms */
 
 typedef enum {
   CC_OK = 0,
@@ -94,11 +94,15 @@ typedef enum {
   CC_GATE_T = 6,   /* diag(1, e^{i pi/4}) */
   CC_GATE_TDG = 7, /* diag(1, e^{-i pi/4}) */
   CC_GATE_CZ = 8,  /* diag(1, 1, 1, -1) on (q0, q1) */
-  CC_GATE_CX = 9   /* control q0, target q1 */
+  CC_GATE_CX = 9,  /* control q0, target q1 */
+  /* Schmidt rank 4 (Eq. 1 with k = 4), basis |x_q0 x_q1>: */
+  CC_GATE_SWAP = 10,  /* exchanges x_q0 and x_q1 */
+  CC_GATE_ISWAP = 11, /* SWAP with a factor i on |01> and |10> */
+  CC_GATE_CAN = 12    /* exp(-i (tx XX + ty YY + tz ZZ) / 2), (tx, ty, tz) = (theta, phi, lambda) */
 } cc_gate_kind;
 
 /* One gate.  q1 = -1 for one-qubit gates; theta, phi, lambda are read for U3
- * only.  40 bytes, natural alignment. */
+ * and CAN only.  40 bytes, natural alignment. */
 typedef struct {
   int32_t kind;
   int32_t q0;
@@ -114,7 +118,7 @@ typedef struct {
   int32_t q, n_seg, c_total, precision, decomp;
   int32_t seg_qubits[CC_MAX_SEGMENTS];  /* q_i */
   int32_t seg_start[CC_MAX_SEGMENTS];   /* first qubit of segment i */
-  int32_t seg_cuts[CC_MAX_SEGMENTS];    /* c_i: cuts adjacent to segment i */
+  int32_t seg_cuts[CC_MAX_SEGMENTS];    /* c_i: variant bits of segment i (1 per adjacent rank-2 cut, 2 per rank-4) */
   int32_t seg_passes[CC_MAX_SEGMENTS];  /* gate passes of segment i's program */
   int32_t seg_ops[CC_MAX_SEGMENTS];     /* fused gate operations of segment i */
   int64_t seg_offset[CC_MAX_SEGMENTS];  /* amplitude offset of segment i in seg_buf */
@@ -123,6 +127,8 @@ typedef struct {
   uint64_t psi_bytes;                   /* bytes of the 2^q output */
   uint64_t workspace_bytes;             /* device workspace cc_merge needs (any form) */
   uint64_t table_bytes;                 /* device bytes of the plan's own tables */
+  int32_t cut_bits;                     /* merge terms = 2^cut_bits: 1 bit per rank-2 cut, 2 per rank-4 cut */
+  int32_t reserved0;
 } cc_plan_info_t;
 
 /* cc_plan_create -- preprocessing, Algorithm 1 (T_pre).
@@ -132,10 +138,16 @@ typedef struct {
  *   decomp          cc_decomp;  precision  cc_precision.
  *   out             receives a plan the caller frees with cc_plan_destroy.
  * Every two-qubit gate whose qubits lie in different segments becomes cut j
- * (j in circuit order).  Segment i gets one shared gate program whose 2^{c_i}
- * variants differ only in the diagonal local term selected by the variant's
- * bit for each adjacent cut; the coefficient of cut j is folded into the term
- * on the segment of the gate's first qubit, so merging needs no alpha_m.
+ * (j in circuit order).  Segment i gets one shared gate program whose
+ * variants differ only in the diagonal local terms selected by the variant's
+ * bits for each adjacent cut; the coefficient of cut j is folded into the
+ * term on the segment of the gate's first qubit, so merging needs no alpha_m.
+ * A CZ or CX cut (rank 2) takes one variant bit.  A SWAP, ISWAP or CAN cut
+ * (rank 4) is expanded in Pauli products, sum over (a, b) of w_ab
+ * (X^a Z^b) (x) (X^a Z^b), X^a applied as H Z^a H, and takes two variant
+ * bits (one when only one of them carries weight).  Inside a segment (or in
+ * the uncut program) these gates run as X/Y/Z-basis changes around diagonal
+ * ZZ phases.
  * The plan's tables are uploaded to the current device (synchronously).
  * Errors: CC_EINVAL (NULL, bad enum, bad qubit, sizes not summing to q),
  * CC_ERANGE (q, n_seg or c_total too large, a segment too large to simulate),

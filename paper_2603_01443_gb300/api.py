@@ -70,7 +70,7 @@ class CutPlan:
             "seg_ops": list(info.seg_ops[:n]), "seg_offset": list(info.seg_offset[:n]),
             "n_sub": info.n_sub, "seg_buf_bytes": info.seg_buf_bytes,
             "psi_bytes": info.psi_bytes, "workspace_bytes": info.workspace_bytes,
-            "table_bytes": info.table_bytes,
+            "table_bytes": info.table_bytes, "cut_bits": info.cut_bits,
         }
 
     def close(self):

@@ -26,7 +26,9 @@ STATUS = {
 PRECISION = {"c64": 0, "c128": 1}
 DECOMP = {"projector": 0, "s_sdg": 1}
 MERGE_FORM = {"auto": 0, "fma": 1, "tf32x3": 2, "bf16x3": 3}
-GATE_KIND = {"U3": 0, "H": 1, "X": 2, "Z": 3, "S": 4, "SDG": 5, "T": 6, "TDG": 7, "CZ": 8, "CX": 9}
+GATE_KIND = {"U3": 0, "H": 1, "X": 2, "Z": 3, "S": 4, "SDG": 5, "T": 6, "TDG": 7, "CZ": 8, "CX": 9,
+             "SWAP": 10, "ISWAP": 11, "CAN": 12}
+TWO_QUBIT = ("CZ", "CX", "SWAP", "ISWAP", "CAN")
 
 
 class CGate(ctypes.Structure):
@@ -46,7 +48,7 @@ class CPlanInfo(ctypes.Structure):
         ("seg_offset", c_int64 * CC_MAX_SEGMENTS),
         ("n_sub", c_int64),
         ("seg_buf_bytes", c_uint64), ("psi_bytes", c_uint64), ("workspace_bytes", c_uint64),
-        ("table_bytes", c_uint64),
+        ("table_bytes", c_uint64), ("cut_bits", c_int32), ("reserved0", c_int32),
     ]
 
 
@@ -146,7 +148,7 @@ def gate_array(gates):
     for i, g in enumerate(gates):
         arr[i].kind = GATE_KIND[g.kind]
         arr[i].q0 = g.q0
-        arr[i].q1 = g.q1 if g.kind in ("CZ", "CX") else -1
+        arr[i].q1 = g.q1 if g.kind in TWO_QUBIT else -1
         arr[i].reserved = 0
         arr[i].theta = g.theta
         arr[i].phi = g.phi

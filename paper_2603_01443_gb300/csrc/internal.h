@@ -95,14 +95,15 @@ struct HostProgram {
 };
 
 // One operation of a (segment or uncut) program before pass planning.
-enum ItemKind : int { IT_DENSE = 0, IT_DIAG1 = 1, IT_CZ = 2, IT_VAR = 3 };
+enum ItemKind : int { IT_DENSE = 0, IT_DIAG1 = 1, IT_CZ = 2, IT_VAR = 3, IT_DIAG2 = 4 };
 struct Item {
   int kind = IT_DENSE;
-  int a = -1, b = -1;  // qubits (IT_CZ: the second qubit; IT_VAR: the variant bit)
+  int a = -1, b = -1;  // qubits (IT_CZ, IT_DIAG2: the second qubit; IT_VAR: the variant bit)
   cd u[4];             // IT_DENSE: matrix; IT_DIAG1: u[0], u[3] diagonal
   int slot = -1;       // IT_VAR: variant bit number (b = n_state + slot)
   bool var_sign = false;  // IT_VAR: factor is Z^b (a sign term)
-  cd d[2][2];             // IT_VAR: factor d[b][x] for variant bit b, index bit x
+  cd d[2][2];             // IT_VAR: factor d[b][x] for variant bit b, index bit x of a;
+                          // IT_DIAG2: factor d[x_b][x_a] on qubits a, b
 };
 
 // Build the program of a list of items on an nq-bit vector whose low n_state
@@ -112,8 +113,13 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
                             int low, int rb_max);
 int reg_bits_max(int precision);
 
-// Gate -> items (CX as H CZ H on the target; diagonal one-qubit gates as IT_DIAG1).
+// Gate -> items (CX as H CZ H on the target; diagonal one-qubit gates as
+// IT_DIAG1; SWAP, ISWAP, CAN as basis changes around diagonal ZZ phases).
 cc_status gate_items(const cc_gate& g, int qoff, std::vector<Item>& out);
+bool is_two_qubit(int kind);
+bool is_rank4(int kind);
+// Pauli weights of a rank-4 gate: U = c[0] II + c[1] XX + c[2] YY + c[3] ZZ.
+void pauli_weights(const cc_gate& g, cd c[4]);
 cc_status check_gates(const cc_gate* gates, int n_gates, int q);
 
 // Device image of a program: one allocation holding ops, terms, matrices and

@@ -65,6 +65,17 @@ Item cut_item(int decomp, bool first_side, int local_qubit, int slot, int seg_qu
   return it;
 }
 
+// Z^v on local qubit a, v the variant bit `slot`: a sign when both are set.
+Item var_sign_item(int a, int slot, int seg_qubits) {
+  Item it;
+  it.kind = IT_VAR;
+  it.a = a;
+  it.slot = slot;
+  it.b = seg_qubits + slot;
+  it.var_sign = true;
+  return it;
+}
+
 Item hadamard(int a) {
   Item h;
   h.kind = IT_DENSE;
@@ -119,36 +130,87 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
       acc += seg_sizes[i];
     }
 
-    // Scan the circuit for boundary gates (cut j in circuit order).
+    // Scan the circuit for boundary gates (cut j in circuit order).  Each cut
+    // adds one or two global bits; seg_cut_ids[i] lists segment i's bits in
+    // order, and bit t of its variant number is its t-th entry.
     std::vector<std::vector<Item>> items(n_seg);
     p->seg_cut_ids.assign(n_seg, {});
     for (int g = 0; g < n_gates; ++g) {
       const cc_gate& gt = gates[g];
-      const bool two = gt.kind == CC_GATE_CZ || gt.kind == CC_GATE_CX;
+      const bool two = is_two_qubit(gt.kind);
       const int s0 = seg_of_qubit(p.get(), gt.q0);
       const int s1 = two ? seg_of_qubit(p.get(), gt.q1) : s0;
-      if (s0 == s1) {
+      cd w[4];  // rank-4 Pauli weights (II, XX, YY, ZZ)
+      bool use_a = false, use_b = false;
+      if (s0 != s1 && is_rank4(gt.kind)) {
+        pauli_weights(gt, w);
+        use_a = w[1] != cd(0.0) || w[2] != cd(0.0);
+        use_b = w[3] != cd(0.0) || w[2] != cd(0.0);
+      }
+      if (s0 == s1 || (is_rank4(gt.kind) && !use_a && !use_b)) {  // (the identity needs no cut)
         st = gate_items(gt, p->seg_start[s0], items[s0]);
         if (st != CC_OK) return st;
         continue;
       }
-      if ((int)p->cuts.size() >= CC_MAX_CUTS)
-        return fail(CC_ERANGE, "more than 24 cut gates");
+      const int width = is_rank4(gt.kind) ? (int)use_a + (int)use_b : 1;
+      if ((int)p->bits.size() + width > CC_MAX_CUTS)
+        return fail(CC_ERANGE, "more than 24 cut bits");
       if (n_seg >= 3 && std::abs(s0 - s1) != 1)
         return fail(CC_EUNSUPPORTED, "gate " + std::to_string(g) +
                                          " crosses non-adjacent segments; the chained merge needs "
                                          "every cut between neighbouring segments");
       const int j = (int)p->cuts.size();
       p->cuts.push_back({gt.q0, gt.q1, gt.kind, s0, s1});
-      const int slot0 = (int)p->seg_cut_ids[s0].size();
-      const int slot1 = (int)p->seg_cut_ids[s1].size();
-      p->seg_cut_ids[s0].push_back(j);
-      p->seg_cut_ids[s1].push_back(j);
+      auto new_bit = [&](int& slot0, int& slot1) {
+        slot0 = (int)p->seg_cut_ids[s0].size();
+        slot1 = (int)p->seg_cut_ids[s1].size();
+        const int bit = (int)p->bits.size();
+        p->bits.push_back({j, s0, s1});
+        p->seg_cut_ids[s0].push_back(bit);
+        p->seg_cut_ids[s1].push_back(bit);
+      };
       const int l0 = gt.q0 - p->seg_start[s0], l1 = gt.q1 - p->seg_start[s1];
-      items[s0].push_back(cut_item(decomp, true, l0, slot0, p->seg_q[s0]));
-      if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
-      items[s1].push_back(cut_item(decomp, false, l1, slot1, p->seg_q[s1]));
-      if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
+      if (!is_rank4(gt.kind)) {
+        int slot0, slot1;
+        new_bit(slot0, slot1);
+        items[s0].push_back(cut_item(decomp, true, l0, slot0, p->seg_q[s0]));
+        if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
+        items[s1].push_back(cut_item(decomp, false, l1, slot1, p->seg_q[s1]));
+        if (gt.kind == CC_GATE_CX) items[s1].push_back(hadamard(l1));
+        continue;
+      }
+      // Rank 4: U = sum_{a,b} w_ab (X^a Z^b) (x) (X^a Z^b) with w_00 = c_II,
+      // w_10 = c_XX, w_01 = c_ZZ, w_11 = -c_YY (X Z = -i Y, so (XZ)(x)(XZ) = -YY).
+      // Both sides apply Z^b, then X^a = H Z^a H; the weight rides on the
+      // first side as a table over its two variant bits.
+      int a0 = -1, a1 = -1, b0 = -1, b1 = -1;
+      if (use_a) new_bit(a0, a1);
+      if (use_b) new_bit(b0, b1);
+      const int side_seg[2] = {s0, s1}, side_q[2] = {l0, l1};
+      const int side_a[2] = {a0, a1}, side_b[2] = {b0, b1};
+      for (int side = 0; side < 2; ++side) {
+        const int sg = side_seg[side], lq = side_q[side], nq_s = p->seg_q[sg];
+        if (use_b) items[sg].push_back(var_sign_item(lq, side_b[side], nq_s));
+        if (use_a) {
+          items[sg].push_back(hadamard(lq));
+          items[sg].push_back(var_sign_item(lq, side_a[side], nq_s));
+          items[sg].push_back(hadamard(lq));
+        }
+      }
+      const cd w00 = w[0], w10 = w[1], w01 = w[3], w11 = -w[2];
+      Item co;
+      co.kind = IT_VAR;
+      if (use_a && use_b) {  // d[bit b][bit a]
+        co.a = p->seg_q[s0] + a0;
+        co.b = p->seg_q[s0] + b0;
+        co.d[0][0] = w00; co.d[0][1] = w10; co.d[1][0] = w01; co.d[1][1] = w11;
+      } else {  // one bit: the table is read at (bit, bit)
+        const int slot = use_a ? a0 : b0;
+        co.a = co.b = p->seg_q[s0] + slot;
+        co.d[0][0] = w00; co.d[0][1] = 0.0; co.d[1][0] = 0.0; co.d[1][1] = use_a ? w10 : w01;
+      }
+      co.slot = -1;
+      items[s0].push_back(co);
     }
     p->c_total = (int)p->cuts.size();
 
@@ -183,8 +245,8 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     std::vector<int32_t> tab;
     if (n_seg >= 2) {
       std::vector<std::vector<int>> bcuts(n_seg - 1);
-      for (int j = 0; j < p->c_total; ++j)
-        bcuts[std::min(p->cuts[j].s0, p->cuts[j].s1)].push_back(j);
+      for (int bit = 0; bit < (int)p->bits.size(); ++bit)
+        bcuts[std::min(p->bits[bit].s0, p->bits[bit].s1)].push_back(bit);
       int qa = p->seg_q[0];
       uint64_t u_max = 0;
       for (int s = 1; s < n_seg; ++s) {
@@ -328,6 +390,7 @@ extern "C" cc_status cc_plan_info(const cc_plan* p, cc_plan_info_t* info) {
   info->q = p->q;
   info->n_seg = p->n_seg;
   info->c_total = p->c_total;
+  info->cut_bits = (int32_t)p->bits.size();
   info->precision = p->precision;
   info->decomp = p->decomp;
   for (int i = 0; i < p->n_seg; ++i) {

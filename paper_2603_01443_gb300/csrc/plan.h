@@ -38,7 +38,11 @@ struct cc_plan {
   int q = 0, n_seg = 0, c_total = 0, precision = 0, decomp = 0;
   std::vector<int> seg_q, seg_start, seg_c;
   std::vector<int64_t> seg_off;
-  std::vector<std::vector<int>> seg_cut_ids;
+  struct Bit {
+    int cut, s0, s1;  // the cut it belongs to and its two segments
+  };
+  std::vector<Bit> bits;                      // global cut bits (1 per rank-2 cut, 2 per rank-4)
+  std::vector<std::vector<int>> seg_cut_ids;  // per segment: its bits in variant-bit order
   std::vector<Cut> cuts;
   std::vector<cc::HostProgram> hprog;
   std::vector<cc::DeviceProgram> dprog;

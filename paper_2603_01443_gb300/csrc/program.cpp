@@ -40,17 +40,46 @@ void mat_lmul(const cd* a, cd* u) {
 
 }  // namespace
 
+bool is_two_qubit(int kind) {
+  return kind == CC_GATE_CZ || kind == CC_GATE_CX || is_rank4(kind);
+}
+bool is_rank4(int kind) {
+  return kind == CC_GATE_SWAP || kind == CC_GATE_ISWAP || kind == CC_GATE_CAN;
+}
+
+// exp(-i (tx XX + ty YY + tz ZZ) / 2) = prod over P of (cos(t_P/2) II - i sin(t_P/2) PP);
+// the three factors commute and XX YY = -ZZ, XX ZZ = -YY, YY ZZ = -XX.
+void pauli_weights(const cc_gate& g, cd c[4]) {
+  const cd I(0.0, 1.0);
+  if (g.kind == CC_GATE_SWAP) {  // (II + XX + YY + ZZ) / 2
+    c[0] = c[1] = c[2] = c[3] = 0.5;
+    return;
+  }
+  if (g.kind == CC_GATE_ISWAP) {  // (II + ZZ) / 2 + i (XX + YY) / 2
+    c[0] = c[3] = 0.5;
+    c[1] = c[2] = 0.5 * I;
+    return;
+  }
+  const cd cx = std::cos(0.5 * g.theta), sx = -I * std::sin(0.5 * g.theta);
+  const cd cy = std::cos(0.5 * g.phi), sy = -I * std::sin(0.5 * g.phi);
+  const cd cz = std::cos(0.5 * g.lambda), sz = -I * std::sin(0.5 * g.lambda);
+  c[0] = cx * cy * cz - sx * sy * sz;
+  c[1] = sx * cy * cz - cx * sy * sz;
+  c[2] = cx * sy * cz - sx * cy * sz;
+  c[3] = cx * cy * sz - sx * sy * cz;
+}
+
 cc_status check_gates(const cc_gate* gates, int n_gates, int q) {
   if (n_gates < 0) return fail(CC_EINVAL, "n_gates < 0");
   if (n_gates > 0 && !gates) return fail(CC_EINVAL, "gates is NULL");
   for (int i = 0; i < n_gates; ++i) {
     const cc_gate& g = gates[i];
-    if (g.kind < CC_GATE_U3 || g.kind > CC_GATE_CX)
+    if (g.kind < CC_GATE_U3 || g.kind > CC_GATE_CAN)
       return fail(CC_EINVAL, "gate " + std::to_string(i) + ": unknown kind " + std::to_string(g.kind));
     if (g.q0 < 0 || g.q0 >= q)
       return fail(CC_EINVAL, "gate " + std::to_string(i) + ": qubit " + std::to_string(g.q0) +
                                  " out of range for q=" + std::to_string(q));
-    const bool two = g.kind == CC_GATE_CZ || g.kind == CC_GATE_CX;
+    const bool two = is_two_qubit(g.kind);
     if (two) {
       if (g.q1 < 0 || g.q1 >= q)
         return fail(CC_EINVAL, "gate " + std::to_string(i) + ": qubit " + std::to_string(g.q1) +
@@ -59,9 +88,9 @@ cc_status check_gates(const cc_gate* gates, int n_gates, int q) {
         return fail(CC_EINVAL, "gate " + std::to_string(i) + ": two-qubit gate on one qubit");
     }
     if (g.reserved != 0) return fail(CC_EINVAL, "gate " + std::to_string(i) + ": reserved != 0");
-    if (g.kind == CC_GATE_U3 &&
+    if ((g.kind == CC_GATE_U3 || g.kind == CC_GATE_CAN) &&
         !(std::isfinite(g.theta) && std::isfinite(g.phi) && std::isfinite(g.lambda)))
-      return fail(CC_EINVAL, "gate " + std::to_string(i) + ": non-finite U3 angle");
+      return fail(CC_EINVAL, "gate " + std::to_string(i) + ": non-finite angle");
   }
   return CC_OK;
 }
@@ -111,6 +140,61 @@ cc_status gate_items(const cc_gate& g, int qoff, std::vector<Item>& out) {
       out.push_back(h);
       return CC_OK;
     }
+    case CC_GATE_SWAP: case CC_GATE_ISWAP: case CC_GATE_CAN: {
+      // U = exp(-i (tx XX + ty YY + tz ZZ)/2) times a global phase:
+      // SWAP = e^{-i pi/4} CAN(-pi/2, -pi/2, -pi/2), ISWAP = CAN(-pi/2, -pi/2, 0).
+      // Each factor is a ZZ phase conjugated into the X basis (H) or the Y
+      // basis (V = S H maps Z to Y: V Z V^dag = Y).
+      const int b = g.q1 - qoff;
+      double t[3] = {g.theta, g.phi, g.lambda};
+      cd phase = 1.0;
+      if (g.kind != CC_GATE_CAN) {
+        t[0] = t[1] = -0.5 * M_PI;
+        t[2] = g.kind == CC_GATE_SWAP ? -0.5 * M_PI : 0.0;
+        if (g.kind == CC_GATE_SWAP) phase = std::polar(1.0, -0.25 * M_PI);
+      }
+      auto dense = [&](int q, const cd* u) {
+        Item d;
+        d.kind = IT_DENSE;
+        d.a = q;
+        for (int e = 0; e < 4; ++e) d.u[e] = u[e];
+        out.push_back(d);
+      };
+      auto zz = [&](double th) {  // exp(-i th/2 ZZ): e^{-i th/2} on equal bits, e^{+i th/2} else
+        if (th == 0.0) return;
+        Item d;
+        d.kind = IT_DIAG2;
+        d.a = a;
+        d.b = b;
+        const cd e0 = std::polar(1.0, -0.5 * th), e1 = std::polar(1.0, 0.5 * th);
+        d.d[0][0] = e0; d.d[0][1] = e1; d.d[1][0] = e1; d.d[1][1] = e0;
+        out.push_back(d);
+      };
+      cd h[4];
+      mat_h(h);
+      const double r = 1.0 / std::sqrt(2.0);
+      const cd vdag[4] = {r, -I * r, r, I * r};  // (S H)^dag = H S^dag
+      const cd v[4] = {r, r, I * r, -I * r};     // S H
+      zz(t[2]);
+      if (t[0] != 0.0) {
+        dense(a, h); dense(b, h);
+        zz(t[0]);
+        dense(a, h); dense(b, h);
+      }
+      if (t[1] != 0.0) {
+        dense(a, vdag); dense(b, vdag);
+        zz(t[1]);
+        dense(a, v); dense(b, v);
+      }
+      if (phase != cd(1.0)) {
+        Item d;
+        d.kind = IT_DIAG1;
+        d.a = a;
+        d.u[0] = phase; d.u[1] = 0.0; d.u[2] = 0.0; d.u[3] = phase;
+        out.push_back(d);
+      }
+      return CC_OK;
+    }
     default:
       return fail(CC_EINVAL, "unknown gate kind");
   }
@@ -120,7 +204,7 @@ namespace {
 
 inline uint64_t item_mask(const Item& it) {
   uint64_t m = 1ull << it.a;
-  if (it.kind == IT_CZ || it.kind == IT_VAR) m |= 1ull << it.b;
+  if (it.kind == IT_CZ || it.kind == IT_VAR || it.kind == IT_DIAG2) m |= 1ull << it.b;
   return m;
 }
 
@@ -330,6 +414,18 @@ struct PassBuilder {
         flush(it.b);
         add_sign(vpos[it.a], vpos[it.b]);
         return;
+      case IT_DIAG2: {
+        flush(it.a);
+        flush(it.b);
+        DTerm t{};
+        t.kind = TERM_TABLE;
+        t.p0 = (uint8_t)vpos[it.a];
+        t.p1 = (uint8_t)vpos[it.b];
+        cd tab[4] = {it.d[0][0], it.d[0][1], it.d[1][0], it.d[1][1]};  // x_a + 2 x_b
+        t.tab = add_table(tab);
+        pend_tab.push_back(t);
+        return;
+      }
       case IT_VAR: {
         flush(it.a);
         if (it.var_sign) {
