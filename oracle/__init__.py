@@ -16,10 +16,12 @@ cutting      -- Algorithm 1 (preprocessing), Algorithm 2 (subcircuit
                 the Algorithm 3 sum for vectors too large to materialise.
 thresholds   -- the cost-model thresholds (Eqs. 12-15, Table II).
 reductions   -- the FP64 verification quantities (max |d psi|, fidelity, norm).
+mlp          -- the planner network's forward pass, loss gradient and Adam
+                steps in FP64 (pinned by finite differences and closed forms).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests (closed
 forms, brute-force unitaries, cut == uncut, the Table II values); none is
 "parity unpinned".
 """
 
-from . import statevector, cutting, thresholds, reductions  # noqa: F401
+from . import statevector, cutting, thresholds, reductions, mlp  # noqa: F401
