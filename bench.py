@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,8 +52,10 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["boundary", "batch", "paper"], default=None,
+    p.add_argument("--sweep", choices=["boundary", "batch", "paper", "planner"], default=None,
                    help="run a measurement sweep instead of the single-line benchmark")
+    p.add_argument("--planner-instances", type=int, default=4000,
+                   help="timed instances of the planner sweep")
     p.add_argument("--sweep-cmax", type=int, default=20,
                    help="largest c_total of the boundary sweep (capped by the depth)")
     p.add_argument("--sweep-both", action="store_true",
@@ -345,9 +348,10 @@ def sweep_boundary(a):
     return 0
 
 
-def measure_point(gates, q, segs, prec, decomp, reps=3):
+def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True):
     """Mean (T_pre, T_sub, T_merge, T_orig) of one circuit over `reps` runs
-    after one warm-up; buffers allocated outside the timing."""
+    after one warm-up (unless warmup=False); buffers allocated outside the
+    timing."""
     import torch
 
     from paper_2603_01443_gb300 import api, capi
@@ -360,7 +364,8 @@ def measure_point(gates, q, segs, prec, decomp, reps=3):
     probe.close()
     psi_u = torch.empty_like(psi)
     rec = []
-    for rep in range(1 + reps):
+    first = 1 if warmup else 0
+    for rep in range(first + reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan = api.CutPlan(packed, q, segs, decomp, prec)
@@ -378,7 +383,7 @@ def measure_point(gates, q, segs, prec, decomp, reps=3):
         up.simulate(psi_u, stream)
         ev[4].record(stream)
         ev[4].synchronize()
-        if rep:
+        if rep >= first:
             rec.append((t_pre, ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3,
                         t_up + ev[3].elapsed_time(ev[4]) / 1e3))
         plan.close()
@@ -478,6 +483,148 @@ def sweep_paper(a):
                                     "n3": {"slope": 1.00, "intercept": -11.50}},
                       "theory": {"n2": {"slope": 0.5, "intercept": 0.0},
                                  "n3": {"slope": 2.0 / 3.0, "intercept": math.log2(3)}}}))
+    return 0
+
+
+def planner_instance_features(q, depth, segs, cpb, gates):
+    from paper_2603_01443_gb300 import planner as pl
+
+    n = len(segs)
+    seg_c = [(cpb[i - 1] if i > 0 else 0) + (cpb[i] if i < n - 1 else 0) for i in range(n)]
+    n_sub = sum(1 << c for c in seg_c)
+    max_seg_bits = max(s + c for s, c in zip(segs, seg_c))
+    dense = sum(1 for g in gates if g.kind in ("U3", "H", "X"))
+    two = sum(1 for g in gates if g.q1 >= 0)
+    return pl.features(q, depth, n, sum(cpb), n_sub, max_seg_bits, dense, two), seg_c
+
+
+def sweep_planner(a, n_inst=4000):
+    """Learned planner: time n_inst random brickwork instances (q 14..30,
+    depth 4..64, n in {2, 3, 4} equal segments, c_total 0..16) stage by
+    stage on this GPU, train an ensemble of FP32 networks (3 hidden layers of
+    64, hand-written CUDA kernels) on an 80/20 split to predict log10 stage
+    seconds, and report the prediction error on the held-out 20 %, the
+    cut/no-cut decisions of the model, of the closed-form threshold and of the
+    model with its fallback (ensemble spread > 20 %), the choice of n on
+    separate circuit families, and the largest q that fits a 10-minute budget
+    with and without cutting.  Instances whose segment buffers would exceed
+    2^31 amplitudes or whose merge would exceed 2^39 amplitude-terms are
+    redrawn (their cost is out of proportion to what they teach)."""
+    import numpy as np
+
+    import torch
+
+    import workload as w
+    from paper_2603_01443_gb300 import planner as pl
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(a.seed + 4242)
+    measure_point(w.brickwork_cut(16, 4, 0, [8, 8], 1), 16, [8, 8], a.prec, a.decomp, reps=1)
+    X, Y, meta = [], [], []
+    t0 = time.perf_counter()
+    while len(X) < n_inst:
+        q = int(rng.integers(14, 31))
+        depth = int(rng.integers(4, 65))
+        n = int(rng.integers(2, 5))
+        c = int(rng.integers(0, min(16, depth * (n - 1)) + 1))
+        segs = w.equal_partition(q, n)
+        cpb = w.split_cuts(c, n)
+        seg_c = [(cpb[i - 1] if i > 0 else 0) + (cpb[i] if i < n - 1 else 0) for i in range(n)]
+        if sum(1 << (s_ + c_) for s_, c_ in zip(segs, seg_c)) > (1 << 31) or q + max(cpb) > 39:
+            continue
+        gates = w.brickwork_cut(q, depth, int(rng.integers(1 << 30)), segs, cpb)
+        pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1, warmup=False)
+        f, _ = planner_instance_features(q, depth, segs, cpb, gates)
+        X.append(f)
+        Y.append([pre, sub, mer, orig])
+        meta.append((q, depth, n, c))
+    t_data = time.perf_counter() - t0
+    X, Y = np.array(X), np.array(Y)
+    perm = rng.permutation(len(X))
+    n_tr = int(0.8 * len(X))
+    tr, te = perm[:n_tr], perm[n_tr:]
+    t1 = time.perf_counter()
+    P = pl.StagePlanner(n_models=4, seed=a.seed)
+    curves = P.fit(X[tr], Y[tr], epochs=3000, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    pr = P.predict(X[te])
+    err = {}
+    for i, s in enumerate(pl.STAGES):
+        rel = np.abs(pr[s] - Y[te, i]) / Y[te, i]
+        err[s] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90))}
+    t_cut_meas = Y[te, 0] + Y[te, 1] + Y[te, 2]
+    rel = np.abs(pr["cut"] - t_cut_meas) / t_cut_meas
+    err["cut"] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90))}
+    truth = t_cut_meas < Y[te, 3]
+    model = pr["cut"] < pr["orig"]
+    closed = np.array([meta[k][3] < pl.threshold(meta[k][0], meta[k][2]) for k in te])
+    fb = pr["spread"] > P.fallback_spread
+    combined = np.where(fb, closed, model)
+    decisions = {"test_instances": int(len(te)), "cut_wins_measured": float(truth.mean()),
+                 "accuracy_model": float((model == truth).mean()),
+                 "accuracy_closed_form": float((closed == truth).mean()),
+                 "accuracy_model_with_fallback": float((combined == truth).mean()),
+                 "fallback_rate": float(fb.mean())}
+    print(json.dumps({"sweep": "planner", "part": "data", "instances": int(len(X)),
+                      "data_s": t_data, "train_s": t_train,
+                      "final_train_loss": [float(c[-1]) for c in curves],
+                      "features": list(pl.FEATURES), "stages": list(pl.STAGES)}), flush=True)
+    print(json.dumps({"sweep": "planner", "part": "prediction_error_test", "error": err,
+                      "decisions": decisions}), flush=True)
+
+    # choice of n on separate circuit families: uncut, or cut into n = 2, 3, 4
+    fam_rng = np.random.default_rng(a.seed + 77)
+    agree, regret, n_fb, rows = 0, [], 0, []
+    for k in range(48):
+        q = int(fam_rng.integers(18, 31))
+        depth = int(fam_rng.choice([8, 16, 32, 64]))
+        cpb1 = int(fam_rng.integers(1, 6))
+        seed = int(fam_rng.integers(1 << 30))
+        opts, times = [], {}
+        t_orig = None
+        for n in (2, 3, 4):
+            segs = w.equal_partition(q, n)
+            cpb = [cpb1] * (n - 1)
+            gates = w.brickwork_cut(q, depth, seed, segs, cpb)
+            pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1)
+            times[n] = pre + sub + mer
+            t_orig = orig if t_orig is None else min(t_orig, orig)
+            f, seg_c = planner_instance_features(q, depth, segs, cpb, gates)
+            opts.append({"n": n, "features": f, "cut_bits": sum(cpb),
+                         "n_sub": sum(1 << c_ for c_ in seg_c)})
+        times[0] = t_orig
+        d = P.decide(q, opts)
+        best = min(times, key=times.get)
+        agree += int(d["choice"] == best)
+        n_fb += int(d["fallback"])
+        regret.append(times[d["choice"]] / times[best] - 1.0)
+        rows.append({"q": q, "depth": depth, "c_per_boundary": cpb1, "choice": d["choice"],
+                     "best": best, "fallback": d["fallback"],
+                     "measured_s": {str(n): t for n, t in times.items()}})
+    print(json.dumps({"sweep": "planner", "part": "choose_n", "families": 48,
+                      "agreement": agree / 48.0, "fallback_rate": n_fb / 48.0,
+                      "mean_regret": float(np.mean(regret)), "max_regret": float(np.max(regret)),
+                      "rows": rows}), flush=True)
+
+    # largest q within a 10-minute budget (brickwork depth 16, n = 2, c_total = 6)
+    def predict(q, which):
+        qq = min(q, 30)
+        segs = w.equal_partition(qq, 2)
+        gates = w.brickwork_cut(qq, 16, 0, segs, [6])
+        f, _ = planner_instance_features(qq, 16, segs, [6], gates)
+        p = P.predict(np.array([f]))
+        t = float(p["cut"][0] if which == "cut" else p["orig"][0])
+        return t * 2.0 ** (q - qq)  # state-vector work doubles per qubit beyond the data
+    hbm = torch.cuda.get_device_properties(0).total_memory
+    amp = 8 if a.prec == "c64" else 16
+    q_mem = int(math.floor(math.log2(hbm * 0.9 / amp)))  # one 2^q vector (+ small segment buffers)
+    res = {w_: pl.max_feasible_q(lambda q: predict(q, w_), 600.0, q_mem, 14) for w_ in ("cut", "orig")}
+    print(json.dumps({"sweep": "planner", "part": "max_feasible_q", "budget_s": 600.0,
+                      "workload": "brickwork depth 16, n = 2, c_total = 6",
+                      "memory_cap_q": q_mem, "cut": res["cut"], "uncut": res["orig"],
+                      "pred_s_at_cap": {"cut": predict(q_mem, "cut"),
+                                        "uncut": predict(q_mem, "orig")}}), flush=True)
     return 0
 
 
@@ -599,6 +746,8 @@ def main(argv=None):
         return sweep_batch(a)
     if a.sweep == "paper":
         return sweep_paper(a)
+    if a.sweep == "planner":
+        return sweep_planner(a, a.planner_instances)
 
     import torch
     import torch.distributed as dist

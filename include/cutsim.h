@@ -350,6 +350,34 @@ cc_status cc_batch_autotune(cc_batch* b, void* seg_buf, uint64_t seg_buf_bytes, 
 
 void cc_batch_destroy(cc_batch* b);
 
+/* ------------------------------------------------------ learned planner
+ * A small fully connected FP32 network (hand-written forward, backward and
+ * Adam kernels) that the planner trains on stage times measured on this GPU
+ * and uses to choose cut/no-cut and the segment count; the closed-form
+ * thresholds (Eqs. 13-14) are its fallback.  Layers map dims[l] ->
+ * dims[l+1], l < n_layers (1..8 layers, widths 1..1024); hidden layers use
+ * ReLU, the last is linear.  params (device, float) packs per layer
+ * W_l (dims[l+1] x dims[l], row-major) then b_l; inputs x are n x dims[0]
+ * row-major, outputs n x dims[n_layers].  work is a device scratch of
+ * cc_mlp_work_bytes(dims, n_layers, n) bytes. */
+int64_t cc_mlp_param_count(const int32_t* dims, int32_t n_layers);  /* -1 on bad dims */
+uint64_t cc_mlp_work_bytes(const int32_t* dims, int32_t n_layers, int64_t n); /* 0 on bad dims */
+
+/* cc_mlp_forward -- y = net(x) for n samples (asynchronous on `stream`). */
+cc_status cc_mlp_forward(const int32_t* dims, int32_t n_layers, const float* params,
+                         const float* x, int64_t n, float* y, float* work, uint64_t work_bytes,
+                         void* stream);
+
+/* cc_mlp_train -- `epochs` full-batch Adam steps (beta1 0.9, beta2 0.999,
+ * eps 1e-8, step lr) on the mean squared error between net(x) and the
+ * targets t (n x dims[n_layers]).  params, adam_m, adam_v (zero-initialised
+ * by the caller for a fresh run) are updated in place; each call counts its
+ * steps from 1 for Adam's bias correction; loss (device, may be NULL)
+ * receives the loss of every epoch before its update. */
+cc_status cc_mlp_train(const int32_t* dims, int32_t n_layers, float* params, float* adam_m,
+                       float* adam_v, const float* x, const float* t, int64_t n, int32_t epochs,
+                       float lr, float* loss, float* work, uint64_t work_bytes, void* stream);
+
 /* cc_sync -- synchronize `stream`, then report CC_ETIMEOUT if any kernel of
  * this library on the current device gave up a bounded wait since the last
  * cc_sync (the flag is cleared by the call).  Asynchronous entry points

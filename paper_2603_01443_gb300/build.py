@@ -22,7 +22,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcutsim.so")
 
 CU_SOURCES = ["runtime.cu", "sv_kernels.cu", "merge_kernels.cu", "merge_tc.cu", "reduce_kernels.cu",
-              "batch.cu",
+              "batch.cu", "mlp.cu",
               "gather_static.cu"]
 CPP_SOURCES = ["program.cpp", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

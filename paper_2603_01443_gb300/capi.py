@@ -102,6 +102,13 @@ _SIGNATURES = {
                                     c_uint64, c_void_p, c_int32, POINTER(c_int32),
                                     POINTER(c_int32), POINTER(c_int32), POINTER(ctypes.c_float)]),
     "cc_batch_destroy": (None, [c_void_p]),
+    "cc_mlp_param_count": (c_int64, [POINTER(c_int32), c_int32]),
+    "cc_mlp_work_bytes": (c_uint64, [POINTER(c_int32), c_int32, c_int64]),
+    "cc_mlp_forward": (c_int32, [POINTER(c_int32), c_int32, c_void_p, c_void_p, c_int64, c_void_p,
+                                 c_void_p, c_uint64, c_void_p]),
+    "cc_mlp_train": (c_int32, [POINTER(c_int32), c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_int64, c_int32, ctypes.c_float, c_void_p, c_void_p,
+                               c_uint64, c_void_p]),
     "cc_sync": (c_int32, [c_void_p]),
     "cc_last_error": (c_char_p, []),
     "cc_version": (c_char_p, []),

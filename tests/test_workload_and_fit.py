@@ -58,3 +58,15 @@ def test_fit_boundary_recovers_a_separating_line(slope, intercept):
 
 def test_fit_boundary_needs_both_classes():
     assert bench.fit_boundary([(4, 1, -0.5), (6, 2, -0.1)]) is None
+
+
+def test_planner_threshold_matches_the_oracle():
+    # the planner's own Eqs. 13-14 (product code) against the oracle's
+    from oracle import thresholds as th
+    from paper_2603_01443_gb300 import planner
+
+    for n in (2, 3, 4, 6, 8):
+        for q in range(4, 40):
+            assert planner.threshold(q, n) == pytest.approx(th.threshold(q, n), abs=1e-12)
+    with pytest.raises(ValueError):
+        planner.threshold(10, 1)
