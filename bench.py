@@ -899,7 +899,7 @@ def main(argv=None):
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": alu_src}
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        "tf32x3" if (a.prec == "c64" and 16 <= K <= 64) else "fma")
+        "tf32x3" if (a.prec == "c64" and K >= 16) else "fma")
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
         # complex FMA merge: 8 flops per term per output amplitude on the ALU pipes

@@ -68,13 +68,15 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
 /* Merge arithmetic (cc_merge).
  * CC_MERGE_FMA     : complex FMA on CUDA cores in the plan's precision.
  * CC_MERGE_TF32X3  : tcgen05 tensor cores, kind::tf32, each operand split
- *                    x = hi + lo and hi*hi + hi*lo + lo*hi accumulated in FP32
- *                    (CC_C64 plans, K <= 64 terms, both factors >= 2^7
+ *                    x = hi + lo and hi*hi + hi*lo + lo*hi accumulated in FP32,
+ *                    at most 64 terms per tensor-core accumulation (longer K
+ *                    adds its 64-term partial sums with FP32 tensor
+ *                    reduce-add stores) (CC_C64 plans, both factors >= 2^7
  *                    amplitudes; max|dpsi|/max|psi| <= 2e-6).
  * CC_MERGE_BF16X3  : tcgen05 tensor cores, kind::f16 with bf16 operands, the
  *                    same three-product split, FP32 accumulation (CC_C64,
  *                    factors >= 2^7; max|dpsi|/max|psi| <= 5e-5).
- * CC_MERGE_AUTO    : TF32X3 where it applies and 16 <= K <= 64, else FMA.
+ * CC_MERGE_AUTO    : TF32X3 where it applies and K >= 16, else FMA.
  * For n_seg >= 3 the form applies to the last (2^q-sized) stage of the chain;
  * the earlier, smaller stages always use FMA. */
 typedef enum {

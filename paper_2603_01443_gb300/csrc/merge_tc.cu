@@ -51,7 +51,9 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STG_TOTAL + 1024 /*align*/ + 2
 constexpr int TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 232448;  // opt-in dynamic shared memory per CTA on sm_103
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second
-constexpr int64_t kTf32MaxTerms = 64;        // 3xTF32 stays within 2e-6 relative up to here
+// 3xTF32 stays within 2e-6 relative while one tensor-core accumulation runs
+// over at most 2 x 64 real products; longer K is summed in groups of that length.
+constexpr int64_t kTf32GroupTerms = 64;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -180,11 +182,16 @@ __host__ __device__ constexpr uint32_t idesc_value() {
          | ((uint32_t)(BM >> 4) << 24);                       // M / 16
 }
 
+// Long K runs in groups of group_kb K blocks: each group accumulates into a
+// fresh TMEM accumulator and the epilogue writes group 0 with plain tensor
+// stores and adds every later group with tensor reduce-add stores (FP32 adds
+// in L2, after the warp's earlier stores of the tile have completed), so no
+// single tensor-core accumulation runs longer than group_kb K blocks.
 template <int KIND>
 __global__ void __launch_bounds__(192, 1)
     merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
-                    int kblocks, int* err) {
+                    int kblocks, int group_kb, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -273,39 +280,42 @@ __global__ void __launch_bounds__(192, 1)
       int iter = 0;
       bool ok = true;
       bool any_mma = false;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++iter) {
-        const int a = iter & 1;
-        if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
-        for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int kb0 = 0; kb0 < kblocks && ok; kb0 += group_kb, ++iter) {
+          const int a = iter & 1;
+          if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-          const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
-          const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
+          const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
+          const int kb1 = min(kblocks, kb0 + group_kb);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+            const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
+            const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
 #pragma unroll
-          for (int k = 0; k < KB_BYTES / 32; ++k) {
-            const uint64_t adv = (uint64_t)((k * 32) >> 4);
-            umma<KIND>(dtmem, rh + adv, ch + adv, idesc, (kb | k) != 0);
-            umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
-            umma<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
+            for (int k = 0; k < KB_BYTES / 32; ++k) {
+              const uint64_t adv = (uint64_t)((k * 32) >> 4);
+              umma<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
+              umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
+              umma<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
+            }
+            any_mma = true;
+            umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+            if (++s == STAGES) {
+              s = 0;
+              ++use;
+            }
           }
-          any_mma = true;
-          umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
-          if (++s == STAGES) {
-            s = 0;
-            ++use;
-          }
+          if (!ok) break;
+          umma_commit(&tfull[a]);  // accumulator a holds this group's sum
         }
-        if (!ok) break;
-        umma_commit(&tfull[a]);  // accumulator a is complete
       }
       if (!ok && any_mma) {  // let our own MMAs finish before TMEM is freed
         umma_commit(drain);
@@ -321,44 +331,62 @@ __global__ void __launch_bounds__(192, 1)
     unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
     int buf = 0;
     int iter = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++iter) {
-      const int a = iter & 1;
-      // one lane waits, the warp follows its verdict (tcgen05.ld needs the whole warp)
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      tc_fence_after();
-      const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
+    bool ok_all = true;
+    for (int t = blockIdx.x; t < n_tiles && ok_all; t += gridDim.x) {
+      for (int kb0 = 0; kb0 < kblocks; kb0 += group_kb, ++iter) {
+        const int a = iter & 1;
+        // one lane waits, the warp follows its verdict (tcgen05.ld needs the whole warp)
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          ok_all = false;
+          break;
+        }
+        tc_fence_after();
+        const bool add = kb0 > 0;  // later groups add onto the stored partial sums
+        if (add) {
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+          __syncwarp();
+        }
+        const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tbase + (uint32_t)(c * 32), r);
-        unsigned char* sb = stg + buf * STG_BYTES;
-        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        __syncwarp();
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t r[32];
+          tmem_ld32(tbase + (uint32_t)(c * 32), r);
+          unsigned char* sb = stg + buf * STG_BYTES;
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
-          *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          for (int j = 0; j < 8; ++j) {
+            float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
+            *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            if (add)
+              asm volatile(
+                  "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group"
+                  " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(&map_out)),
+                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+                  : "memory");
+            else
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                      reinterpret_cast<uint64_t>(&map_out)),
+                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+                  : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          buf ^= 1;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          asm volatile(
-              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                  reinterpret_cast<uint64_t>(&map_out)),
-              "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
-              : "memory");
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-        buf ^= 1;
+        if (lane == 0) mbar_arrive(&tempty[a]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[a]);
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     __syncwarp();
@@ -733,10 +761,6 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   if (st.qa + st.qb > 40) return fail(CC_ERANGE, "merge output too large");
   const uint64_t need = merge_tc_workspace_bytes(st.qa, st.qb, st.K, form);
   if (need == 0) return fail(CC_EUNSUPPORTED, "tensor-core merge shape unsupported");
-  if (form == CC_MERGE_TF32X3 && st.K > kTf32MaxTerms)
-    return fail(CC_EUNSUPPORTED,
-                "3xTF32 merge is limited to 64 terms: beyond that the FP32 accumulation in the "
-                "tensor core exceeds the complex64 tolerance");
   if (ws_bytes < need) return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CC_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
@@ -811,11 +835,16 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   const int n_tiles = (n_rows / BM) * (n_cols / BN);
   const int grid = std::min(n_tiles, num_sms());
   const int kblocks = KR * eb / KB_BYTES;
+  // 3xTF32: accumulate at most 2 x kTf32GroupTerms real products per pass
+  // through TMEM (the K blocks of 2 x 64 TF32 elements).
+  const int group_kb = form == CC_MERGE_TF32X3
+                           ? std::max(1, (int)(2 * kTf32GroupTerms * eb / KB_BYTES))
+                           : kblocks;
   // Row-operand-stationary form when the 128-row R tile (hi and lo, all K
   // blocks) leaves room for at least two 32 KB column stages.
   const int r_bytes = 2 * kblocks * R_TILE;
   const int rs_stages = std::min(RS_MAX_STAGES, (SMEM_LIMIT - 1024 - 256 - STG_TOTAL - r_bytes) / RS_C_STAGE);
-  if (rs_stages >= 2 && tc_stationary_requested()) {
+  if (rs_stages >= 2 && kblocks <= group_kb && tc_stationary_requested()) {
     const int smem_rs = r_bytes + rs_stages * RS_C_STAGE + STG_TOTAL + 1024 + 256;
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_rs_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
@@ -823,7 +852,8 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   } else {
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_kernel<CC_MERGE_TF32X3>;
-    kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, err);
+    kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks,
+                                       std::min(group_kb, kblocks), err);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(e));

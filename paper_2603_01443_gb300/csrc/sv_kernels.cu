@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 
 #include "internal.h"
@@ -586,7 +587,14 @@ cc_status launch_pass(const DeviceProgram& dp, int pi, void* state, cudaStream_t
 
 }  // namespace
 
-int reg_bits_max(int precision) { return precision == CC_C128 ? 4 : 5; }
+int reg_bits_max(int precision) {
+  const int hi = precision == CC_C128 ? 4 : 5;
+  if (const char* e = std::getenv("CUTSIM_REG_BITS")) {  // fewer register bits: more, lighter threads
+    const int v = std::atoi(e);
+    if (v >= 2 && v <= hi) return v;
+  }
+  return hi;
+}
 
 int batch_segments_occupancy(int precision, int block, size_t smem) {
   static int attr_done[64][2] = {{0}};

@@ -30,9 +30,11 @@ def run(gates, q, segs, form, decomp="projector"):
 CASES = [([7, 7], 0), ([7, 7], 3), ([8, 9], 5), ([9, 8], 6), ([10, 10], 4), ([8, 8], 6)]
 
 
-@pytest.mark.parametrize("form,segs,c", [("tf32x3",) + x for x in CASES] +
-                         [("bf16x3",) + x for x in CASES + [([8, 8], 7), ([8, 8], 8), ([8, 8], 10),
-                                                          ([8, 8], 12)]])
+DEEP = [([8, 8], 7), ([8, 8], 8), ([8, 8], 10), ([8, 8], 12), ([9, 10], 9)]
+
+
+@pytest.mark.parametrize("form,segs,c", [("tf32x3",) + x for x in CASES + DEEP] +
+                         [("bf16x3",) + x for x in CASES + DEEP])
 def test_tc_merge_vs_oracle(cuda_lib, form, segs, c):
     q = sum(segs)
     gates = w.brickwork_cut(q, 12, 21 + c, segs, c)
@@ -67,14 +69,17 @@ def test_tc_merge_rejects_small_workspace(cuda_lib):
     assert e.value.status == 5
 
 
-def test_tf32x3_refuses_deep_merges(cuda_lib):
-    # beyond 64 terms the tensor-core FP32 accumulation exceeds 2e-6
-    gates = w.brickwork_cut(16, 12, 1, [8, 8], 7)
-    with pytest.raises(capi.CutsimError) as e:
-        run(gates, 16, [8, 8], "tf32x3")
-    assert e.value.status == 3
-    psi, _ = run(gates, 16, [8, 8], "auto")  # AUTO falls back to the FMA form
-    assert rel_err(psi.cpu().numpy(), sv.simulate(16, gates)) <= TOL["c64"]
+def test_tf32x3_deep_merge_matches_fma_at_scale(cuda_lib):
+    # K = 256: four 64-term groups, the later ones added by tensor reduce-add stores
+    q, segs, c = 24, [12, 12], 8
+    gates = w.brickwork_cut(q, 12, 2, segs, c)
+    psi_tc, _ = run(gates, q, segs, "tf32x3")
+    psi_fma, _ = run(gates, q, segs, "fma")
+    st = api.compare(psi_tc, psi_fma, "c64")
+    assert st["max_abs_diff"] <= TOL["c64"] * st["max_abs_b"], st
+    assert 1 - st["fidelity"] <= FID_TOL
+    psi_auto, _ = run(gates, q, segs, "auto")
+    assert torch.equal(psi_auto, psi_tc)  # AUTO picks 3xTF32 at K = 256
 
 
 @pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "auto"])
