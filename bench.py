@@ -899,7 +899,7 @@ def main(argv=None):
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": alu_src}
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        "tf32x3" if (a.prec == "c64" and K >= 16) else "fma")
+        "tf32x3" if (a.prec == "c64" and (1 << cpb[-1]) >= 16) else "fma")
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
         # complex FMA merge: 8 flops per term per output amplitude on the ALU pipes
@@ -909,8 +909,11 @@ def main(argv=None):
                            "frac": fma_flops / mean["merge"] / 1e12 / alu_peak,
                            "peak_source": alu_src}
     if tc_form in ("tf32x3", "bf16x3"):
-        # three split products of the real GEMM: 3 x 8K flops per output amplitude
-        tc_flops = 3.0 * 8 * K * n_amp
+        # three split products of the real GEMM of the last (2^q-sized) merge
+        # stage: 3 x 8 K_last flops per output amplitude, K_last = 2^(cuts on
+        # the last boundary) (all of c_total for n = 2)
+        k_last = 1 << cpb[-1]
+        tc_flops = 3.0 * 8 * k_last * n_amp
         tc_peak = bf16 * (0.5 if tc_form == "tf32x3" else 1.0)  # nominal TF32:BF16 = 1:2
         merge_rf["tensor"] = {"achieved": tc_flops / mean["merge"] / 1e12, "peak": tc_peak,
                               "unit": "TFLOP/s", "form": tc_form,

@@ -477,6 +477,7 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
   while (low < P.k && tile_bits[low] == low) ++low;
   P.low = low;
   P.rbits = std::max(1, std::min(rb_max, P.k - 5));
+  P.rbits = std::max(P.rbits, P.k - 9);  // at most 512 threads per CTA
   P.rbits = std::min(P.rbits, P.k);
   uint64_t tmask = 0;
   for (int t = 0; t < P.k; ++t) {
