@@ -848,7 +848,7 @@ def main(argv=None):
             plan = api.CutPlan(packed, a.q, segs, a.decomp, a.prec)
             plan.simulate_segments(seg, stream)
             plan.merge(seg, psi, ws, a.merge_form, stream)
-            host_psi.copy_(psi, non_blocking=True)
+            api.copy_to_host(psi, host_psi, stream)
             torch.cuda.synchronize()
             if i >= a.warmup:
                 times.append(time.perf_counter() - t0)

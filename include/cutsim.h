@@ -386,6 +386,23 @@ cc_status cc_mlp_train(const int32_t* dims, int32_t n_layers, float* params, flo
  * cannot return that status themselves. */
 cc_status cc_sync(void* stream);
 
+/* cc_copy_to_host -- copy `bytes` from device memory to host memory (a
+ * result vector to the caller).  For a page-locked host buffer that is mapped
+ * into the device address space (cudaHostAlloc / pinned allocations under
+ * unified addressing) the SMs copy it with 16-byte loads and stores through
+ * the mapped address, which on a Grace host runs over NVLink-C2C faster than
+ * one copy engine; any other host buffer goes through cudaMemcpyAsync.  Both
+ * pointers 16-byte aligned.  Asynchronous on `stream`. */
+cc_status cc_copy_to_host(const void* src, void* host, uint64_t bytes, void* stream);
+
+/* cc_check_wait_expiry -- exercise the failure path of the bounded device
+ * waits without any fault: one thread polls a device word that nothing
+ * writes, `polls` times (1..2^20, about 1 us apart), gives up and raises the
+ * device error flag exactly as an expired wait in the engine does; the next
+ * cc_sync on the stream then returns CC_ETIMEOUT and clears the flag.
+ * Asynchronous on `stream`. */
+cc_status cc_check_wait_expiry(int32_t polls, void* stream);
+
 /* cc_last_error -- thread-local message of the last failure (never NULL). */
 const char* cc_last_error(void);
 

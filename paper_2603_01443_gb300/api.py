@@ -174,6 +174,14 @@ def compare(a: torch.Tensor, b: torch.Tensor, precision: str, stream=None) -> di
     }
 
 
+def copy_to_host(src: torch.Tensor, host: torch.Tensor, stream=None) -> None:
+    """src (device) -> host (a pinned CPU tensor of the same size), asynchronous."""
+    if host.is_cuda or not host.is_contiguous() or _nbytes(host) < _nbytes(src):
+        raise ValueError("host must be a contiguous CPU tensor at least as large as src")
+    capi.check(capi.lib().cc_copy_to_host(_ptr(src), host.data_ptr(), _nbytes(src),
+                                          _stream(stream)), "cc_copy_to_host")
+
+
 def gather(psi: torch.Tensor, idx: Sequence[int], precision: str, stream=None) -> np.ndarray:
     """psi[idx] copied to the host (synchronizes)."""
     idx_arr = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))

@@ -109,6 +109,8 @@ _SIGNATURES = {
     "cc_mlp_train": (c_int32, [POINTER(c_int32), c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_int64, c_int32, ctypes.c_float, c_void_p, c_void_p,
                                c_uint64, c_void_p]),
+    "cc_check_wait_expiry": (c_int32, [c_int32, c_void_p]),
+    "cc_copy_to_host": (c_int32, [c_void_p, c_void_p, c_uint64, c_void_p]),
     "cc_sync": (c_int32, [c_void_p]),
     "cc_last_error": (c_char_p, []),
     "cc_version": (c_char_p, []),

@@ -236,6 +236,10 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
 // ----------------------------------------------------------- reductions
 cc_status launch_compare(const void* a, const void* b, int64_t n, int precision, double* out_dev,
                          double* partials, int n_blocks, void* stream);
+// SM-driven copy of `bytes` from device memory to a host buffer's mapped address.
+cc_status launch_copy_to_host(const void* src, void* host_mapped, uint64_t bytes, void* stream);
+// One bounded wait on a word nothing writes: raises the device error flag.
+cc_status launch_expired_wait(int polls, void* stream);
 cc_status launch_gather(const void* psi, int precision, const int64_t* idx_dev, int64_t n,
                         void* out_dev, void* stream);
 

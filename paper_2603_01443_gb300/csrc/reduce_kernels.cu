@@ -4,6 +4,8 @@
 // across runs (see compare_partial_c64).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace cc {
@@ -160,7 +162,71 @@ __global__ void gather_kernel(const C* __restrict__ psi, const int64_t* __restri
     out[i] = psi[idx[i]];
 }
 
+// Device -> host copy by the SMs themselves: 16-byte loads from HBM and
+// 16-byte stores through the host buffer's mapped address (NVLink-C2C on a
+// Grace host), four vectors in flight per thread.
+__global__ void __launch_bounds__(256) copy_to_host_kernel(const int4* __restrict__ src,
+                                                           int4* __restrict__ dst, int64_t n16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const int4 a = __ldcs(src + i), b = __ldcs(src + i + stride);
+    const int4 c = __ldcs(src + i + 2 * stride), d = __ldcs(src + i + 3 * stride);
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = __ldcs(src + i);
+}
+
+// Polls a device word that nothing writes, `polls` times ~1 us apart, then
+// raises the error flag the way an expired wait in the engine does.
+__global__ void expired_wait_kernel(const int* __restrict__ never_set, int polls,
+                                    int* __restrict__ err) {
+  int seen = 0;
+  for (int i = 0; i < polls && !seen; ++i) {
+    seen = *(volatile const int*)never_set;
+    __nanosleep(1000);
+  }
+  if (!seen) atomicExch(err, 1);
+}
+
 }  // namespace
+
+cc_status launch_copy_to_host(const void* src, void* host_mapped, uint64_t bytes, void* stream) {
+  const int64_t n16 = (int64_t)(bytes / 16);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n16 > 0) {
+    const int64_t grid = std::min<int64_t>((n16 + 255) / 256, (int64_t)num_sms() * 8);
+    copy_to_host_kernel<<<(unsigned)grid, 256, 0, s>>>(static_cast<const int4*>(src),
+                                                       static_cast<int4*>(host_mapped), n16);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy launch: ") + cudaGetErrorString(e));
+  }
+  const uint64_t tail = bytes - (uint64_t)n16 * 16;
+  if (tail) {
+    const cudaError_t e = cudaMemcpyAsync(static_cast<char*>(host_mapped) + n16 * 16,
+                                          static_cast<const char*>(src) + n16 * 16, tail,
+                                          cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+  }
+  return CC_OK;
+}
+
+cc_status launch_expired_wait(int polls, void* stream) {
+  int* err = device_error_flag();
+  if (!err) return fail(CC_ENOMEM, "device error flag allocation failed");
+  int* word = static_cast<int*>(scratch(sizeof(int)));
+  if (!word) return fail(CC_ENOMEM, "scratch allocation failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(word, 0, sizeof(int), s);
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
+  expired_wait_kernel<<<1, 1, 0, s>>>(word, polls, err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("wait probe launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
 
 cc_status launch_compare(const void* a, const void* b, int64_t n, int precision, double* out_dev,
                          double* partials, int n_blocks, void* stream) {

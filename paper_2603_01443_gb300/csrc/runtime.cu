@@ -419,6 +419,29 @@ extern "C" cc_status cc_sync(void* stream) {
   return CC_OK;
 }
 
+extern "C" cc_status cc_copy_to_host(const void* src, void* host, uint64_t bytes, void* stream) {
+  if (!src || !host) return fail(CC_EINVAL, "NULL buffer");
+  if (bytes == 0) return CC_OK;
+  if (!aligned16(src) || !aligned16(host)) return fail(CC_EINVAL, "buffers must be 16-byte aligned");
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  void* mapped = nullptr;
+  if (cudaHostGetDevicePointer(&mapped, host, 0) != cudaSuccess || !mapped) {
+    cudaGetLastError();  // not page-locked and mapped: the copy engines do it
+    const cudaError_t e = cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(CC_ECUDA, std::string("copy: ") + cudaGetErrorString(e));
+    return CC_OK;
+  }
+  return launch_copy_to_host(src, mapped, bytes, stream);
+}
+
+extern "C" cc_status cc_check_wait_expiry(int32_t polls, void* stream) {
+  if (polls < 1 || polls > (1 << 20)) return fail(CC_ERANGE, "polls must be in 1..2^20");
+  cc_status st = check_device();
+  if (st != CC_OK) return st;
+  return launch_expired_wait(polls, stream);
+}
+
 extern "C" const char* cc_last_error(void) { return g_error.c_str(); }
 
 extern "C" const char* cc_version(void) { return "cutsim 0.1 (sm_103a)"; }

@@ -205,3 +205,31 @@ def test_error_paths_on_device(cuda_lib):
     with pytest.raises(capi.CutsimError) as e:
         up.simulate(up.alloc_psi()[:100])
     assert e.value.status == 5
+
+
+def test_expired_wait_is_reported_and_cleared(cuda_lib):
+    # the error path of every bounded device wait, without any fault: a wait
+    # on a word nothing writes gives up, cc_sync reports CC_ETIMEOUT once,
+    # and the context stays usable
+    stream = torch.cuda.current_stream().cuda_stream
+    capi.check(cuda_lib.cc_sync(stream), "cc_sync")
+    capi.check(cuda_lib.cc_check_wait_expiry(2000, stream), "cc_check_wait_expiry")
+    assert cuda_lib.cc_sync(stream) == 7  # CC_ETIMEOUT
+    assert b"bounded device wait" in cuda_lib.cc_last_error()
+    assert cuda_lib.cc_sync(stream) == 0  # cleared
+    psi, _, _ = gpu_cut(w.brickwork(10, 4, 3), 10, [5, 5], "projector", "c128")
+    assert_parity(psi.cpu().numpy(), sv.simulate(10, w.brickwork(10, 4, 3)), "c128", "after")
+    assert cuda_lib.cc_check_wait_expiry(0, stream) == 2  # CC_ERANGE
+
+
+@pytest.mark.parametrize("n", [1, 7, (1 << 20) + 5])
+def test_copy_to_host(cuda_lib, n):
+    src = torch.randn(n, dtype=torch.complex64, device="cuda")
+    pinned = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+    api.copy_to_host(src, pinned)
+    torch.cuda.synchronize()
+    assert torch.equal(pinned, src.cpu())
+    plain = torch.zeros(n, dtype=torch.complex64)  # pageable: the copy-engine path
+    api.copy_to_host(src, plain)
+    torch.cuda.synchronize()
+    assert torch.equal(plain, src.cpu())
