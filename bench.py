@@ -902,8 +902,9 @@ def main(argv=None):
         "tf32x3" if (a.prec == "c64" and (1 << cpb[-1]) >= 16) else "fma")
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
-        # complex FMA merge: 8 flops per term per output amplitude on the ALU pipes
-        fma_flops = 8.0 * K * n_amp
+        # complex FMA merge: 8 flops per term per output amplitude on the ALU
+        # pipes, for the last (2^q-sized) stage's K_last terms
+        fma_flops = 8.0 * (1 << cpb[-1]) * n_amp
         merge_rf["alu"] = {"achieved": fma_flops / mean["merge"] / 1e12, "peak": alu_peak,
                            "unit": "TFLOP/s",
                            "frac": fma_flops / mean["merge"] / 1e12 / alu_peak,
