@@ -182,6 +182,18 @@ __host__ __device__ constexpr uint32_t idesc_value() {
          | ((uint32_t)(BM >> 4) << 24);                       // M / 16
 }
 
+// Output tiles are visited in bands of kBand row tiles: inside a band the
+// row index runs fastest, so a column-operand tile is used by kBand row tiles
+// back to back and the row-operand tiles of the band stay in L2 while the
+// band sweeps the columns.
+constexpr int kBand = 16;
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& m0, int& n0) {
+  const int band = t / (kBand * tiles_n), r = t - band * kBand * tiles_n;
+  const int rows = min(kBand, tiles_m - band * kBand);
+  m0 = (band * kBand + r % rows) * BM;
+  n0 = (r / rows) * BN;
+}
+
 // Long K runs in groups of group_kb K blocks: each group accumulates into a
 // fresh TMEM accumulator and the epilogue writes group 0 with plain tensor
 // stores and adds every later group with tensor reduce-add stores (FP32 adds
@@ -246,7 +258,8 @@ __global__ void __launch_bounds__(192, 1)
       bool ok = true;
       const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+        int m0, n0;
+        tile_coords(t, tiles_m, tiles_n, m0, n0);
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
             ok = false;
@@ -349,7 +362,8 @@ __global__ void __launch_bounds__(192, 1)
           if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
           __syncwarp();
         }
-        const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+        int m0, n0;
+        tile_coords(t, tiles_m, tiles_n, m0, n0);
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {

@@ -184,3 +184,18 @@ def test_batch_host_validation(L, case):
     assert not h.value
     if case == "bad_gate":
         assert b"circuit 1" in L.cc_last_error()
+
+
+def test_cut_bits_limit_is_checked_on_the_host(L):
+    # 13 SWAP cuts need 26 cut bits > CC_MAX_CUTS (24): rejected before any device work
+    gates = [w.Gate("SWAP", 3, 4) for _ in range(13)]
+    arr = capi.gate_array(gates)
+    segs = (c_int32 * 2)(4, 4)
+    h = c_void_p()
+    st = L.cc_plan_create(arr, len(gates), 8, segs, 2, 0, 0, byref(h))
+    assert st == 2 and b"cut bits" in L.cc_last_error()
+    # twelve fit the limit exactly; the plan then fails only for want of a device
+    st = L.cc_plan_create(arr, 12, 8, segs, 2, 0, 0, byref(h))
+    assert st != 2
+    if h.value:
+        L.cc_plan_destroy(h)
