@@ -172,6 +172,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Two 32-column TMEM loads in flight, one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[32], uint32_t (&q)[32]) {
+#define CC_TMEM_LD(ADDR, R)                                                                       \
+  asm volatile(                                                                                 \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, " \
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, " \
+      "%30, %31}, [%32];"                                                                       \
+      : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]),      \
+        "=r"(R[7]), "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]), \
+        "=r"(R[14]), "=r"(R[15]), "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]),           \
+        "=r"(R[20]), "=r"(R[21]), "=r"(R[22]), "=r"(R[23]), "=r"(R[24]), "=r"(R[25]),           \
+        "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]), "=r"(R[30]), "=r"(R[31])            \
+      : "r"(ADDR))
+  CC_TMEM_LD(taddr, r);
+  CC_TMEM_LD(taddr + 32u, q);
+#undef CC_TMEM_LD
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256.
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc_value() {
@@ -366,9 +385,13 @@ __global__ void __launch_bounds__(192, 1)
         tile_coords(t, tiles_m, tiles_n, m0, n0);
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-          uint32_t r[32];
-          tmem_ld32(tbase + (uint32_t)(c * 32), r);
+        for (int c2 = 0; c2 < BN / 32; c2 += 2) {
+          uint32_t rr[2][32];
+          tmem_ld32x2(tbase + (uint32_t)(c2 * 32), rr[0], rr[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+          const int c = c2 + h;
+          uint32_t (&r)[32] = rr[h];
           unsigned char* sb = stg + buf * STG_BYTES;
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           __syncwarp();
@@ -396,6 +419,7 @@ __global__ void __launch_bounds__(192, 1)
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
           buf ^= 1;
+          }
         }
         tc_fence_before();
         __syncwarp();
@@ -408,6 +432,280 @@ __global__ void __launch_bounds__(192, 1)
 
   tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------- paired (multicast) form
+// Two CTAs of a cluster compute the row tiles m and m + 1 of the same column
+// tile n.  Each loads its own row operand and HALF of the shared column
+// operand, multicasting that half into both CTAs' shared memory, so the pair
+// reads each column-operand byte from L2 once: two thirds of the operand L2
+// traffic of the single-CTA form, whose merge is bound by that traffic.
+// A stage is refilled only after both CTAs' MMAs have read it (each MMA warp
+// commits to the empty barrier of both CTAs).  The CTAs meet at a cluster
+// barrier at the start (barriers initialised) and at the end (no multicast
+// or remote arrive in flight toward an exiting CTA); every other wait is
+// bounded.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                               int x, int y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1)
+    merge_tc_pair_kernel(const __grid_constant__ CUtensorMap map_r,
+                         const __grid_constant__ CUtensorMap map_c_half,
+                         const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
+                         int kblocks, int group_kb, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* stg_base = smem + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES], two arrivals: both CTAs' MMAs
+  uint64_t* tfull = bars + 2 * STAGES;   // [2]
+  uint64_t* tempty = bars + 2 * STAGES + 2;  // [2]
+  uint64_t* drain = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 7);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster_rank();
+  const int tiles_n = n_cols / BN;
+  const int pairs_m = n_rows / (2 * BM);
+  const int n_units = pairs_m * tiles_n;
+  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+  constexpr uint16_t kBoth = 0x3;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 2);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the partner's barriers exist before anything targets them
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  // unit u -> (row-tile pair, column tile) in bands of kBand row tiles
+  auto unit_coords = [&](int u, int& m0, int& n0) {
+    int pm, pn;
+    const int band_pairs = kBand / 2;
+    const int band = u / (band_pairs * tiles_n), r = u - band * band_pairs * tiles_n;
+    const int rows = min(band_pairs, pairs_m - band * band_pairs);
+    pm = band * band_pairs + r % rows;
+    pn = r / rows;
+    m0 = (2 * pm + rank) * BM;
+    n0 = pn * BN;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_r)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c_half)) : "memory");
+      int s = 0;
+      uint32_t use = 0;
+      bool issued[STAGES] = {false, false};
+      uint32_t issued_parity[STAGES] = {0, 0};
+      bool ok = true;
+      const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+      for (int u = cluster; u < n_units && ok; u += n_clusters) {
+        int m0, n0;
+        unit_coords(u, m0, n0);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = smem + s * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, m0);
+          tma_load_2d(smem_u32(st + R_TILE), &map_r, fb, kb * kelem, n_rows + m0);
+          // this CTA's half of the column tile, into both CTAs
+          const int half = rank * (BN / 2);
+          tma_load_2d_mc(smem_u32(st + 2 * R_TILE + half * KB_BYTES), &map_c_half, fb, kb * kelem,
+                         n0 + half, kBoth);
+          tma_load_2d_mc(smem_u32(st + 2 * R_TILE + C_TILE + half * KB_BYTES), &map_c_half, fb,
+                         kb * kelem, n_cols + n0 + half, kBoth);
+          issued[s] = true;
+          issued_parity[s] = use & 1;
+          if (++s == STAGES) {
+            s = 0;
+            ++use;
+          }
+        }
+      }
+      if (!ok) {
+        for (int i = 0; i < STAGES; ++i)
+          if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_value<KIND>();
+      int s = 0;
+      uint32_t use = 0;
+      int iter = 0;
+      bool ok = true;
+      bool any_mma = false;
+      for (int u = cluster; u < n_units && ok; u += n_clusters) {
+        for (int kb0 = 0; kb0 < kblocks && ok; kb0 += group_kb, ++iter) {
+          const int a = iter & 1;
+          if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
+          const int kb1 = min(kblocks, kb0 + group_kb);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+            const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
+            const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
+#pragma unroll
+            for (int k = 0; k < KB_BYTES / 32; ++k) {
+              const uint64_t adv = (uint64_t)((k * 32) >> 4);
+              umma<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
+              umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
+              umma<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
+            }
+            any_mma = true;
+            umma_commit_mc(&empty[s], kBoth);  // both CTAs may refill the stage once both read it
+            if (++s == STAGES) {
+              s = 0;
+              ++use;
+            }
+          }
+          if (!ok) break;
+          umma_commit(&tfull[a]);
+        }
+      }
+      if (!ok && any_mma) {
+        umma_commit(drain);
+        mbar_drain(drain, 0);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
+    int buf = 0;
+    int iter = 0;
+    bool ok_all = true;
+    for (int u = cluster; u < n_units && ok_all; u += n_clusters) {
+      int m0, n0;
+      unit_coords(u, m0, n0);
+      for (int kb0 = 0; kb0 < kblocks; kb0 += group_kb, ++iter) {
+        const int a = iter & 1;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          ok_all = false;
+          break;
+        }
+        tc_fence_after();
+        const bool add = kb0 > 0;
+        if (add) {
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+          __syncwarp();
+        }
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+        for (int c2 = 0; c2 < BN / 32; c2 += 2) {
+          uint32_t rr[2][32];
+          tmem_ld32x2(tbase + (uint32_t)(c2 * 32), rr[0], rr[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+          const int c = c2 + h;
+          uint32_t (&r)[32] = rr[h];
+          unsigned char* sb = stg + buf * STG_BYTES;
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
+            *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            if (add)
+              asm volatile(
+                  "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group"
+                  " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(&map_out)),
+                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+                  : "memory");
+            else
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                      reinterpret_cast<uint64_t>(&map_out)),
+                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
+                  : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          buf ^= 1;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[a]);
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncwarp();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // neither CTA exits while the other may still target it
   tc_fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -751,6 +1049,13 @@ bool tc_stationary_requested() {
   return e && e[0] == '1';
 }
 
+// The paired multicast form (two CTAs per column tile) is the default where
+// the row tiles pair up; CUTSIM_TC_PAIR=0 selects the single-CTA form.
+bool tc_pair_requested() {
+  const char* e = std::getenv("CUTSIM_TC_PAIR");
+  return !(e && e[0] == '0');
+}
+
 int kr_of(int64_t K, int form) {
   const int kelem = form == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
   return (int)(((2 * K + kelem - 1) / kelem) * kelem);
@@ -825,6 +1130,17 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand) failed");
   }
 
+  CUtensorMap map_c_half;  // the paired form loads half a column tile per CTA
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(4 * NA)};
+    const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
+    const cuuint32_t box[2] = {box_k, (cuuint32_t)(BN / 2)};
+    if (enc(&map_c_half, dt, 2, c_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand half) failed");
+  }
+
   {
     const cuuint64_t dims[2] = {(cuuint64_t)(2 * NA), (cuuint64_t)NB};
     const cuuint64_t strides[1] = {(cuuint64_t)(2 * NA) * 4};
@@ -843,6 +1159,8 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    cudaFuncSetAttribute(merge_tc_pair_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(merge_tc_pair_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr_done[dev] = 1;
   }
   const int n_rows = (int)NB, n_cols = (int)(2 * NA);
@@ -863,6 +1181,31 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_rs_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
     kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
+  } else if (tc_pair_requested() && (n_rows / BM) % 2 == 0 && num_sms() >= 2) {
+    auto kern = form == CC_MERGE_BF16X3 ? merge_tc_pair_kernel<CC_MERGE_BF16X3>
+                                        : merge_tc_pair_kernel<CC_MERGE_TF32X3>;
+    const int n_units = (n_rows / (2 * BM)) * (n_cols / BN);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * std::min(n_units, num_sms() / 2)), 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, map_r, map_c_half, map_out, n_rows,
+                                              n_cols, kblocks, std::min(group_kb, kblocks), err);
+    if (le != cudaSuccess) {  // no room for 2-CTA clusters here: the single-CTA form
+      cudaGetLastError();
+      auto k1 = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
+                                        : merge_tc_kernel<CC_MERGE_TF32X3>;
+      k1<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks,
+                                       std::min(group_kb, kblocks), err);
+    }
   } else {
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_kernel<CC_MERGE_TF32X3>;
