@@ -88,3 +88,29 @@ def test_rank4_batch_and_scale(cuda_lib):
     st = api.compare(psi, psi_u, "c64")
     assert st["max_abs_diff"] <= 4e-6 * st["max_abs_b"], st
     assert 1 - st["fidelity"] <= FID_TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_general_two_qubit_gates_via_kak(cuda_lib, prec):
+    # random 4x4 unitaries, written as U3 / CAN / U3 by the KAK helper, cut
+    # where they cross the boundary; the oracle applies the 4x4 matrices themselves
+    from scipy.stats import unitary_group
+
+    from paper_2603_01443_gb300 import kak
+
+    q, segs = 10, [5, 5]
+    rng = np.random.default_rng(11)
+    ops, gates = [], []
+    for layer in range(6):
+        for j in range(q):
+            g = w.Gate("U3", j, -1, *rng.uniform(0, 2 * np.pi, 3))
+            gates.append(g)
+            ops.append(sv.gate_op(g))
+        for a in range(layer % 2, q - 1, 2):
+            u = unitary_group.rvs(4, random_state=int(rng.integers(1 << 30)))
+            gates += [w.Gate(*x) for x in kak.kak_gates(u, a, a + 1)]
+            ops.append((u, (a, a + 1)))
+    ref = sv.simulate_ops(q, ops)
+    psi, _, plan = gpu_cut(gates, q, segs, "projector", prec)
+    assert plan.info["c_total"] == 3  # the layers whose pairs straddle qubits 4-5
+    assert_parity(psi.cpu().numpy(), ref, prec, "kak")
