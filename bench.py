@@ -922,7 +922,10 @@ def main(argv=None):
                               "peak_source": peak_src + " bf16 burst" +
                               (" x 0.5 (nominal TF32/BF16)" if tc_form == "tf32x3" else "")}
     dominant = pass_rf if orig_dev > mean["merge"] else merge_rf
-    launches = sum(info["seg_passes"]) + (2 if tc_form != "fma" else 1) + n_pass + 2
+    # per step: one persistent launch for every segment pass, the earlier
+    # chain stages (FMA), the last stage (split + tensor-core kernel, or FMA),
+    # the uncut passes, and the two verification kernels
+    launches = 1 + (info["n_seg"] - 2) + (2 if tc_form != "fma" else 1) + n_pass + 2
     cmp = rec["cmp"][-1]
     cpu = None if a.no_cpu_baseline else cpu_baseline_sample(a)
     out = {
