@@ -57,11 +57,10 @@ def commands(ptxas_verbose: bool = False):
         jobs.append((cmd, obj))
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", *inc, "-I", cuda_inc, "-c",
+        cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I", cuda_inc, "-c",
                os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", LIB] + \
-        [o for _, o in jobs]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB] + [o for _, o in jobs]
     return jobs, link
 
 

@@ -22,7 +22,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
-#include <thread>
 
 #include "internal.h"
 #include "plan.h"
@@ -231,25 +230,14 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     p->seg_buf_bytes = (uint64_t)off * ab;
     p->psi_bytes = (uint64_t(1) << q) * ab;
 
-    // One shared program per segment; segments with enough items are planned
-    // on their own host threads (the planners share nothing).
-    p->hprog.resize(n_seg);
-    {
-      const int lowb = low_tile_bits(precision), rbm = reg_bits_max(precision);
-      auto compile_one = [&](int i) {
-        p->hprog[i] = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i], seg_kmax,
-                                      lowb, rbm);
-      };
-      std::vector<std::thread> pool;
-      for (int i = 1; i < n_seg; ++i) {
-        if (items[i].size() >= 64) pool.emplace_back(compile_one, i);
-        else compile_one(i);
-      }
-      compile_one(0);
-      for (auto& t : pool) t.join();
+    // One shared program per segment.
+    for (int i = 0; i < n_seg; ++i) {
+      HostProgram hp = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
+                                       seg_kmax, low_tile_bits(precision),
+                                       reg_bits_max(precision));
+      if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
+      p->hprog.push_back(std::move(hp));
     }
-    for (int i = 0; i < n_seg; ++i)
-      if (p->hprog[i].nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
 
     // Merge stages: stage s absorbs segment s into the product of segments < s.
     //   U_s[z][x_s * N_{<s} + x_{<s}] = sum_k U_{s-1}[k][x_{<s}] * seg_s[r_s(k, z)][x_s]
