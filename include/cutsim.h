@@ -264,7 +264,10 @@ cc_status cc_gather_static(const void* psi, int64_t n_amp, int32_t precision, co
  *     segment has stored all its tiles;
  *   - then one merge launch per chain level (one for n_seg = 2, two for
  *     n_seg = 3, ...), each over the output tiles of every circuit's stage at
- *     that level, on CUDA cores (CC_MERGE_FMA arithmetic).
+ *     that level, on CUDA cores (CC_MERGE_FMA arithmetic); a circuit's final
+ *     stage with K >= 16 terms and both factors >= 2^7 amplitudes (complex64)
+ *     runs instead as its own 3xTF32 tensor-core merge after its level, as
+ *     CC_MERGE_AUTO would run it (CUTSIM_BATCH_TC=0: all on CUDA cores).
  * The whole sequence can be captured once into a CUDA graph and replayed.
  *
  * Buffers (caller-owned device memory, 16-byte aligned): seg_buf holds every

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -49,6 +50,13 @@ struct Core {
   int64_t n_items = 0;
   std::vector<int> level_begin;      // merge jobs of level L: [level_begin[L], level_begin[L+1])
   std::vector<int64_t> level_units;  // units of level L
+  // Final stages run on the tensor cores (3xTF32) instead, one launch each
+  // after their level's batched launch, sharing one split-operand workspace.
+  struct TcJob {
+    int level, circ;
+    BMergeJob j;
+  };
+  std::vector<TcJob> tc_jobs;
   int block = 32, grid = 1;
   size_t smem = 0;
   ~Core() {
@@ -66,6 +74,8 @@ struct cc_batch {
   // Buffer layout (amplitudes), the same for every tile width.
   std::vector<uint64_t> seg_base, psi_base, work_base;
   uint64_t seg_amps = 0, psi_amps = 0, work_amps = 0;
+  uint64_t tc_off = 0, tc_bytes = 0;  // tensor-core workspace inside the workspace (bytes)
+  bool tc_ok = true;                  // CUTSIM_BATCH_TC=0: every merge on CUDA cores
   int64_t n_sub = 0;
   std::vector<int> c_total;
   std::unique_ptr<Core> core;
@@ -117,7 +127,19 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
     }
     b->seg_amps = so;
     b->psi_amps = po;
-    b->work_amps = wo;
+    // the shared tensor-core workspace follows the chain intermediates
+    uint64_t tcb = 0;
+    if (b->tc_ok && b->precision == CC_C64)
+      for (int i = 0; i < b->n_circ; ++i) {
+        const cc_plan* p = c->plans[i].get();
+        if (p->stages.empty()) continue;
+        const auto& sg = p->stages.back();
+        if (sg.K >= 16 && sg.qa >= 7 && sg.qb >= 7 && sg.Z == 1)
+          tcb = std::max(tcb, merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_TF32X3));
+      }
+    b->tc_off = wo * ab;
+    b->tc_bytes = tcb;
+    b->work_amps = wo + (tcb + ab - 1) / ab;
   }
 
   // Segment jobs, ordered by pass number (then circuit, then segment).
@@ -210,6 +232,12 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
       const int32_t* tabs = static_cast<const int32_t*>(p->tables_dev);
       J.aidx = tabs + sg.aidx_off;
       J.bidx = tabs + sg.bidx_off;
+      if (last && b->tc_ok && b->precision == CC_C64 && sg.K >= 16 && sg.qa >= 7 && sg.qb >= 7 &&
+          sg.Z == 1) {
+        J.circ = i;
+        c->tc_jobs.push_back({L, i, J});
+        continue;
+      }
       J.unit_begin = units;
       J.n_units = merge_batch_units(b->precision, sg.qa, sg.qb, sg.Z, merge_rows, &J.kind);
       J.circ = last ? i : -1;
@@ -271,11 +299,28 @@ cc_status run_core(const cc_batch* b, const Core& c, void* seg, void* psi, void*
   cc_status r = launch_batch_segments(seg, c.jobs, c.n_jobs, c.n_items, c.done, c.head, st,
                                       b->precision, c.block, c.smem, c.grid, stream);
   if (r != CC_OK) return r;
+  const int ab = amp_bytes(b->precision);
+  char* const bufs[3] = {static_cast<char*>(seg), static_cast<char*>(work), static_cast<char*>(psi)};
   for (size_t L = 0; L + 1 < c.level_begin.size(); ++L) {
     const int j0 = c.level_begin[L], j1 = c.level_begin[L + 1];
     r = launch_merge_batch(c.mjobs + j0, j1 - j0, c.level_units[L], seg, work, psi, c.circ_done,
                            st, b->precision, c.merge_rows, stream);
     if (r != CC_OK) return r;
+    for (const auto& t : c.tc_jobs) {
+      if (t.level != (int)L) continue;
+      const BMergeJob& J = t.j;
+      MergeStage ms{bufs[J.a_buf] + J.a_off * ab, bufs[J.b_buf] + J.b_off * ab,
+                    bufs[J.out_buf] + J.out_off * ab, J.qa, J.qb, J.K, 1, J.out_stride, J.aidx,
+                    J.bidx};
+      r = launch_merge_tc(ms, CC_MERGE_TF32X3, static_cast<char*>(work) + b->tc_off, b->tc_bytes,
+                          stream);
+      if (r == CC_EUNSUPPORTED) r = launch_merge_fma(ms, b->precision, stream);
+      if (r != CC_OK) return r;
+      if (st) {
+        r = launch_stamp(st + 1 + t.circ, stream);
+        if (r != CC_OK) return r;
+      }
+    }
   }
   return CC_OK;
 }
@@ -323,6 +368,7 @@ extern "C" cc_status cc_batch_create(const cc_gate* gates, const int64_t* gate_o
     b->q.assign(q, q + n_circ);
     b->seg_off.assign(seg_offset, seg_offset + n_circ + 1);
     b->seg_sizes.assign(seg_sizes, seg_sizes + seg_offset[n_circ]);
+    if (const char* e = std::getenv("CUTSIM_BATCH_TC")) b->tc_ok = e[0] != '0';
 
     // Host checks of every circuit before any device work.
     for (int i = 0; i < n_circ; ++i) {

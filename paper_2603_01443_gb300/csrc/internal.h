@@ -201,6 +201,8 @@ struct BMergeJob {
   int32_t circ;  // circuit whose output this stage completes (-1: intermediate)
   int32_t pad;
 };
+// Writes %globaltimer to *out once the stream reaches it.
+cc_status launch_stamp(unsigned long long* out, void* stream);
 // Work units of a batched merge job for the given tile rows (16 or 32).
 int64_t merge_batch_units(int precision, int qa, int qb, int64_t Z, int rows, int32_t* kind);
 // One launch over every job of one merge level.  circ_done counts finished

@@ -366,6 +366,21 @@ int64_t merge_batch_units(int precision, int qa, int qb, int64_t Z, int rows, in
   return (NA * NB * Z + 255) / 256;
 }
 
+namespace {
+__global__ void stamp_kernel(unsigned long long* out) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *out = t;
+}
+}  // namespace
+
+cc_status launch_stamp(unsigned long long* out, void* stream) {
+  stamp_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, std::string("stamp launch: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
+
 cc_status launch_merge_batch(const BMergeJob* jobs, int n_jobs, int64_t n_units, void* seg_buf,
                              void* work, void* psi, int* circ_done, unsigned long long* stamps,
                              int precision, int rows, void* stream) {

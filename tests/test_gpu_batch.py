@@ -44,16 +44,22 @@ def test_batch_vs_oracle(cuda_lib, prec, decomp, tile_bits, rows):
     assert st[0] > 0 and np.all(st[1:] >= st[0])
 
 
-def test_batch_equals_one_circuit_path_bitwise(cuda_lib):
+@pytest.mark.parametrize("batch_tc,form", [("1", "auto"), ("0", "fma")])
+def test_batch_equals_one_circuit_path_bitwise(cuda_lib, monkeypatch, batch_tc, form):
     # same programs, same tile arithmetic: the batched result is bit-identical
+    # (final stages with K >= 16 on the tensor cores, as AUTO does, by default)
+    monkeypatch.setenv("CUTSIM_BATCH_TC", batch_tc)
     items = w.uneven_batch(8, seed=11, q_range=(14, 20), depths=(8, 16), c_range=(1, 5))
     b = make_batch(items)
     seg, psi, ws = b.alloc_buffers()
-    b.run(seg, psi, ws)
+    stamps = b.alloc_stamps()
+    b.run(seg, psi, ws, stamps)
     sync()
     for i, it in enumerate(items):
-        one, _, _ = gpu_cut(it.gates, it.q, it.seg_sizes, "projector", "c64", "fma")
+        one, _, _ = gpu_cut(it.gates, it.q, it.seg_sizes, "projector", "c64", form)
         assert torch.equal(b.psi_view(psi, i), one), i
+    st = stamps.cpu().numpy().view(np.uint64)
+    assert st[0] > 0 and np.all(st[1:] >= st[0])
 
 
 def test_batch_graph_replay(cuda_lib):
