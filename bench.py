@@ -431,8 +431,11 @@ def sweep_paper(a):
     staircase (Fig. 1; c_total = blocks x (n - 1)), equal partitions, the
     Delta grids of Fig. 4 -- n = 2: q = 2..24 step 2 (extended to 28),
     c_total = 1..10; n = 3: q = 3..24 step 3 (extended to 27), c_total =
-    2..14 step 2 -- with a fitted linear boundary next to the paper's fits
-    (0.70 q - 7.30, 1.00 q - 11.50) and Eqs. 13-14; then the depth sweep
+    2..14 step 2 -- each q continued past the grid's last c_total while
+    cutting still wins (up to c_total 18 / 24 and 32 GiB of segment
+    buffers), so the boundary lies inside the measured points; then a fitted
+    linear boundary next to the paper's fits (0.70 q - 7.30, 1.00 q - 11.50)
+    and Eqs. 13-14, and the largest c_total with a speedup per q; then the depth sweep
     (10^p T/X layers on the edge qubits, p = 0, 2, 3, 4) at n = 2."""
     import math
 
@@ -445,21 +448,37 @@ def sweep_paper(a):
     fits = {}
     grids = {2: ([*range(2, 25, 2), 26, 28], list(range(1, 11))),
              3: ([*range(3, 25, 3), 27], list(range(2, 15, 2)))}
+    cap_c = {2: 18, 3: 24}
+    amp_bytes = 16 if prec == "c128" else 8
+    largest = {}
     for n, (qs, cs) in grids.items():
         pts = []
+        step = cs[1] - cs[0]
+        largest[f"n{n}"] = {}
         for q in qs:
             segs = w.equal_partition(q, n)
-            for c in cs:
+            c, last = cs[0], None
+            while True:
+                if c > cs[-1]:  # past the grid: only while cutting still wins
+                    seg_amps = sum(1 << (s + c // (n - 1) * (2 if 0 < i < n - 1 else 1))
+                                   for i, s in enumerate(segs))
+                    if last is None or last >= 0 or c > cap_c[n] or \
+                            seg_amps * amp_bytes > 32 << 30:
+                        break
                 blocks = c // (n - 1)
                 gates = w.staircase(q, blocks)
                 pre, sub, mer, orig = measure_point(gates, q, segs, prec, a.decomp)
                 cut = pre + sub + mer
                 delta = (cut - orig) / orig
                 pts.append((q, c, delta))
+                if delta < 0:
+                    largest[f"n{n}"][q] = c
                 print(json.dumps({"sweep": "paper", "family": "staircase", "precision": prec,
                                   "n": n, "q": q, "c_total": c, "pre_s": pre, "sub_s": sub,
                                   "merge_s": mer, "cut_s": cut, "orig_s": orig, "delta": delta}),
                       flush=True)
+                last = delta
+                c += step
         fits[f"n{n}"] = fit_boundary(pts)
     depth = {}
     for pexp in (0, 2, 3, 4):
@@ -479,6 +498,7 @@ def sweep_paper(a):
                                   "delta": delta}), flush=True)
         depth[f"p{pexp}"] = fit_boundary(pts)
     print(json.dumps({"sweep": "paper", "precision": prec, "fit": fits, "depth_fit": depth,
+                      "largest_c_total_with_speedup": largest,
                       "paper_fit": {"n2": {"slope": 0.70, "intercept": -7.30},
                                     "n3": {"slope": 1.00, "intercept": -11.50}},
                       "theory": {"n2": {"slope": 0.5, "intercept": 0.0},
