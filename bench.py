@@ -902,9 +902,11 @@ def main(argv=None):
                 "frac": merge_gbs / hbm, "traffic": None,
                 "kernel": "cut_merge", "bytes_per_launch": merge_bytes,
                 "launch_s": mean["merge"], "peak_source": peak_src}
-    # The uncut passes do 8 FMA (16 flops) per amplitude for every dense
-    # one-qubit gate (U3, H, X; a CX is H CZ H on its target) and nothing for
-    # the diagonal ones, which ride along as sign/phase factors: FP32-bound.
+    # Algorithmic work of the uncut passes: a complex 2x2 per amplitude (8 FMA,
+    # 16 flops) for every dense one-qubit gate of the circuit (U3, H, X; a CX
+    # is H CZ H on its target) and nothing for the diagonal ones.  The rotation
+    # engine executes fewer (2 FMA per rotation plus its phase blocks), so a
+    # fraction near or above 1 would not mean the FP32 pipes are saturated.
     n_dense = sum(1 for g in gates if g.kind in ("U3", "H", "X")) + \
         2 * sum(1 for g in gates if g.kind == "CX")
     uncut_flops = 16.0 * n_dense * n_amp

@@ -8,6 +8,12 @@
 
 #include "cutsim.h"
 
+#ifdef __CUDACC__
+#define CC_HD __host__ __device__
+#else
+#define CC_HD
+#endif
+
 namespace cc {
 
 using cd = std::complex<double>;
@@ -34,30 +40,50 @@ cc_status fail(cc_status s, const std::string& msg);
 // matrices act on register bits only, so a stage runs without touching shared
 // memory, and shared memory is used only to re-map bits between stages.
 
-enum : uint8_t { TERM_SIGN = 0, TERM_TABLE = 1 };
+enum : uint8_t { TERM_SIGN = 0, TERM_TABLE = 1, TERM_PBLOCK = 2, TERM_PFIX = 3 };
 
 // Diagonal factor of one amplitude with virtual index v:
-//   TERM_SIGN : multiply by -1 when bit p0 and bit p1 of v are both set
-//   TERM_TABLE: multiply by tab[4*tab + (bit p0) + 2*(bit p1)]
+//   TERM_SIGN  : multiply by -1 when bit p0 and bit p1 of v are both set
+//   TERM_TABLE : multiply by tab[4*tab + (bit p0) + 2*(bit p1)]
+//   TERM_PBLOCK: opens a phase block, a product of one-bit phases: with the
+//                12 entries at tab[4*tab] = (lo[4], hi[8]), lo[l] = K times
+//                the product of h_i over the bits i of l (i < 2) and hi[m]
+//                the product of h_{2+i} over the bits i of m, it multiplies
+//                the amplitude in register slot j by lo[j & 3] hi[j >> 2]
+//   TERM_PFIX  : inside a phase block, multiply by tab[4*tab] when bit p0 of
+//                v (a bit that is not a register bit of the stage) is set
 struct DTerm {
   uint8_t kind, p0, p1, pad;
   int32_t tab;
 };
 
-enum : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
+// OP_ROT and OP_ROTC are real rotations [[c, -s], [s, c]] in tangent form,
+// their scalar factor c (or s) carried by a later phase block:
+//   OP_ROT : (a, b) <- (a - t b, b + t a),  t = s / c  (|t| <= 1)
+//   OP_ROTC: (a, b) <- (t a - b, a + t b),  t = c / s  (|t| <= 1)
+enum : int32_t { OP_DENSE = 0, OP_DIAG = 1, OP_ROT = 2, OP_ROTC = 3 };
 
 // Before its matrix, an op multiplies each amplitude by (-1)^s with
 //   s = popcount(v & (v >> 1) & sign_adj) + sum of the sign terms (bit pairs
 //       not adjacent in v)   (mod 2)
-// and by every table term.  OP_DENSE then applies the 2x2 matrix
-// mats[8*mat ...] (row-major, interleaved re/im) to register bit t;
+// then by its phase block (if any) and every table term.  OP_DENSE then
+// applies the 2x2 matrix mats[8*mat ...] (row-major, interleaved re/im) to
+// register bit t, OP_ROT / OP_ROTC their rotation with t = mats[8*mat];
 // OP_DIAG stops after the diagonal factors.
-struct DOp {
-  int32_t type, t;
-  int32_t term_begin, term_sign_end, term_end;  // sign terms first
+struct alignas(16) DOp {
+  int8_t type, t;
+  // terms [term_begin, +n_sign) are sign terms, the next n_phase the phase
+  // block (TERM_PBLOCK, then TERM_PFIX), the next n_table table terms
+  uint16_t n_sign, n_phase, n_table;
+  int32_t term_begin;
   int32_t mat;
   uint64_t sign_adj;  // bit p set: a sign term on (p, p+1)
+  uint64_t pad;
+  CC_HD int term_sign_end() const { return term_begin + n_sign; }
+  CC_HD int term_phase_end() const { return term_sign_end() + n_phase; }
+  CC_HD int term_end() const { return term_phase_end() + n_table; }
 };
+static_assert(sizeof(DOp) == 32, "two 16-byte loads per op");
 
 struct DStage {
   int32_t op_begin, op_end;

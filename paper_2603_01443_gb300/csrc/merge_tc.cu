@@ -118,6 +118,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes in 8-row (1024-byte) groups.
+// K-major operand with the swizzle width kbb (128, 64 or 32 bytes): rows of kbb
+// bytes in 8-row groups of 8 * kbb bytes (the stride byte offset).
+template <int KBB>
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
+  static_assert(KBB == 128 || KBB == 64 || KBB == 32, "swizzle width");
+  constexpr uint64_t layout = KBB == 128 ? 2 : KBB == 64 ? 4 : 6;  // 128B / 64B / 32B swizzle
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * KBB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= layout << 61;
+  return d;
+}
+
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
@@ -474,24 +489,31 @@ __device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
       : "memory");
 }
 
-template <int KIND>
+// KBB bytes of K per stage (the swizzle width) and NST stages: the operand
+// buffers hold NST * (2 * BM + 2 * BN) * KBB bytes (192 KB for 128 x 2,
+// 64 x 4 and 32 x 8); narrower, more numerous stages keep more of them in
+// flight while the tensor cores read one.
+template <int KIND, int KBB, int NST>
 __global__ void __launch_bounds__(192, 1)
     merge_tc_pair_kernel(const __grid_constant__ CUtensorMap map_r,
                          const __grid_constant__ CUtensorMap map_c_half,
                          const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
                          int kblocks, int group_kb, int* err) {
+  constexpr int RT = BM * KBB, CT = BN * KBB, STB = 2 * RT + 2 * CT;
+  static_assert(NST * STB == STAGES * STAGE_BYTES, "operand buffers as the single-CTA form");
+  static_assert((2 * NST + 8) * 8 <= 256, "barrier area");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stg_base = smem + STAGES * STAGE_BYTES;
+  unsigned char* stg_base = smem + NST * STB;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
-  uint64_t* full = bars;                 // [STAGES]
-  uint64_t* empty = bars + STAGES;       // [STAGES], two arrivals: both CTAs' MMAs
-  uint64_t* tfull = bars + 2 * STAGES;   // [2]
-  uint64_t* tempty = bars + 2 * STAGES + 2;  // [2]
-  uint64_t* drain = bars + 2 * STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 7);
+  uint64_t* full = bars;                  // [NST]
+  uint64_t* empty = bars + NST;           // [NST], two arrivals: both CTAs' MMAs
+  uint64_t* tfull = bars + 2 * NST;       // [2]
+  uint64_t* tempty = bars + 2 * NST + 2;  // [2]
+  uint64_t* drain = bars + 2 * NST + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NST + 7);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (int)cluster_rank();
@@ -502,7 +524,7 @@ __global__ void __launch_bounds__(192, 1)
   constexpr uint16_t kBoth = 0x3;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 2);
     }
@@ -546,10 +568,14 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c_half)) : "memory");
       int s = 0;
       uint32_t use = 0;
-      bool issued[STAGES] = {false, false};
-      uint32_t issued_parity[STAGES] = {0, 0};
+      bool issued[NST];
+      uint32_t issued_parity[NST];
+      for (int i = 0; i < NST; ++i) {
+        issued[i] = false;
+        issued_parity[i] = 0;
+      }
       bool ok = true;
-      const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+      const int kelem = KIND == CC_MERGE_BF16X3 ? KBB / 2 : KBB / 4;
       for (int u = cluster; u < n_units && ok; u += n_clusters) {
         int m0, n0;
         unit_coords(u, m0, n0);
@@ -558,27 +584,27 @@ __global__ void __launch_bounds__(192, 1)
             ok = false;
             break;
           }
-          unsigned char* st = smem + s * STAGE_BYTES;
+          unsigned char* st = smem + s * STB;
           const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(&full[s], STAGE_BYTES);
+          mbar_expect_tx(&full[s], STB);
           tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, m0);
-          tma_load_2d(smem_u32(st + R_TILE), &map_r, fb, kb * kelem, n_rows + m0);
+          tma_load_2d(smem_u32(st + RT), &map_r, fb, kb * kelem, n_rows + m0);
           // this CTA's half of the column tile, into both CTAs
           const int half = rank * (BN / 2);
-          tma_load_2d_mc(smem_u32(st + 2 * R_TILE + half * KB_BYTES), &map_c_half, fb, kb * kelem,
+          tma_load_2d_mc(smem_u32(st + 2 * RT + half * KBB), &map_c_half, fb, kb * kelem,
                          n0 + half, kBoth);
-          tma_load_2d_mc(smem_u32(st + 2 * R_TILE + C_TILE + half * KB_BYTES), &map_c_half, fb,
+          tma_load_2d_mc(smem_u32(st + 2 * RT + CT + half * KBB), &map_c_half, fb,
                          kb * kelem, n_cols + n0 + half, kBoth);
           issued[s] = true;
           issued_parity[s] = use & 1;
-          if (++s == STAGES) {
+          if (++s == NST) {
             s = 0;
             ++use;
           }
         }
       }
       if (!ok) {
-        for (int i = 0; i < STAGES; ++i)
+        for (int i = 0; i < NST; ++i)
           if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
       }
     }
@@ -606,11 +632,11 @@ __global__ void __launch_bounds__(192, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
-            const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
+            const uint32_t st = smem_u32(smem + s * STB);
+            const uint64_t rh = sdesc_sw<KBB>(st), rl = sdesc_sw<KBB>(st + RT);
+            const uint64_t ch = sdesc_sw<KBB>(st + 2 * RT), cl = sdesc_sw<KBB>(st + 2 * RT + CT);
 #pragma unroll
-            for (int k = 0; k < KB_BYTES / 32; ++k) {
+            for (int k = 0; k < KBB / 32; ++k) {
               const uint64_t adv = (uint64_t)((k * 32) >> 4);
               umma<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
               umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
@@ -618,7 +644,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             any_mma = true;
             umma_commit_mc(&empty[s], kBoth);  // both CTAs may refill the stage once both read it
-            if (++s == STAGES) {
+            if (++s == NST) {
               s = 0;
               ++use;
             }
@@ -1056,6 +1082,35 @@ bool tc_pair_requested() {
   return !(e && e[0] == '0');
 }
 
+// Bytes of K per stage of the paired form (2, 4 or 8 stages for 128, 64 or
+// 32).  Measured at q = 30 (merge ms, 128-byte / 64-byte blocks): a K loop of
+// 4 to 8 128-byte blocks per tile runs faster in four 64-byte stages (3xTF32
+// K = 64: 2.64 / 2.41, K = 128: 4.67 / 4.64; split-BF16 K = 128: 2.72 /
+// 2.50); shorter and longer loops run faster in two 128-byte stages (3xTF32
+// K = 32: 1.55 / 1.62, K = 256: 8.76 / 9.36; split-BF16 K = 64: 1.59 /
+// 1.65).  32-byte blocks were slower everywhere.  CUTSIM_TC_KBLOCK = 128,
+// 64 or 32 overrides.
+int tc_pair_kblock(int kblocks128) {
+  const char* e = std::getenv("CUTSIM_TC_KBLOCK");
+  if (e) {
+    const int v = std::atoi(e);
+    if (v == 128 || v == 64 || v == 32) return v;
+  }
+  return kblocks128 >= 4 && kblocks128 <= 8 ? 64 : 128;
+}
+
+CUtensorMapSwizzle swizzle_of(int kbb) {
+  return kbb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                    : kbb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+
+template <int KIND>
+void* pair_kernel_ptr(int kbb) {
+  if (kbb == 128) return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 128, 2>);
+  if (kbb == 64) return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 64, 4>);
+  return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 32, 8>);
+}
+
 int kr_of(int64_t K, int form) {
   const int kelem = form == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
   return (int)(((2 * K + kelem - 1) / kelem) * kelem);
@@ -1130,13 +1185,25 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand) failed");
   }
 
-  CUtensorMap map_c_half;  // the paired form loads half a column tile per CTA
+  // The paired form reads K blocks of pkb bytes (its own swizzle width) and
+  // half a column tile per CTA.
+  const int pkb = tc_pair_kblock(KR * eb / KB_BYTES);
+  CUtensorMap map_r_pair, map_c_half;
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(2 * NB)};
+    const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
+    const cuuint32_t box[2] = {(cuuint32_t)(pkb / eb), (cuuint32_t)BM};
+    if (enc(&map_r_pair, dt, 2, r_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle_of(pkb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (row operand, paired form) failed");
+  }
   {
     const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(4 * NA)};
     const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
-    const cuuint32_t box[2] = {box_k, (cuuint32_t)(BN / 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)(pkb / eb), (cuuint32_t)(BN / 2)};
     if (enc(&map_c_half, dt, 2, c_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            swizzle_of(pkb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand half) failed");
   }
@@ -1159,8 +1226,10 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    cudaFuncSetAttribute(merge_tc_pair_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(merge_tc_pair_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    for (int kbb = 32; kbb <= 128; kbb *= 2) {
+      cudaFuncSetAttribute(pair_kernel_ptr<CC_MERGE_BF16X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      cudaFuncSetAttribute(pair_kernel_ptr<CC_MERGE_TF32X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    }
     attr_done[dev] = 1;
   }
   const int n_rows = (int)NB, n_cols = (int)(2 * NA);
@@ -1182,8 +1251,12 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
     kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
   } else if (tc_pair_requested() && (n_rows / BM) % 2 == 0 && num_sms() >= 2) {
-    auto kern = form == CC_MERGE_BF16X3 ? merge_tc_pair_kernel<CC_MERGE_BF16X3>
-                                        : merge_tc_pair_kernel<CC_MERGE_TF32X3>;
+    const void* kern = form == CC_MERGE_BF16X3 ? pair_kernel_ptr<CC_MERGE_BF16X3>(pkb)
+                                               : pair_kernel_ptr<CC_MERGE_TF32X3>(pkb);
+    const int pkblocks = KR * eb / pkb;
+    const int pgroup_kb = form == CC_MERGE_TF32X3
+                              ? std::max(1, (int)(2 * kTf32GroupTerms * eb / pkb))
+                              : pkblocks;
     const int n_units = (n_rows / (2 * BM)) * (n_cols / BN);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * std::min(n_units, num_sms() / 2)), 1, 1);
@@ -1197,8 +1270,9 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, map_r, map_c_half, map_out, n_rows,
-                                              n_cols, kblocks, std::min(group_kb, kblocks), err);
+    int a_rows = n_rows, a_cols = n_cols, a_kb = pkblocks, a_gkb = std::min(pgroup_kb, pkblocks);
+    void* args[] = {&map_r_pair, &map_c_half, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err};
+    const cudaError_t le = cudaLaunchKernelExC(&cfg, kern, args);
     if (le != cudaSuccess) {  // no room for 2-CTA clusters here: the single-CTA form
       cudaGetLastError();
       auto k1 = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>

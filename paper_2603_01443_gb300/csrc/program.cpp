@@ -10,9 +10,17 @@
 //     applied, as a per-amplitude function of index bits, just before the
 //     first dense matrix on a bit it depends on -- diagonal operators commute
 //     with each other and with matrices on other bits, and a deferred factor
-//     never touches a qubit whose pending matrix is still open.
+//     never touches a qubit whose pending matrix is still open;
+//   * each fused unitary 2x2 matrix u splits as u = g D_L R D_R (Euler
+//     angles: g a scalar, D_L, D_R diagonal phases, R a real rotation), R
+//     runs in tangent form at 2 multiply-adds per amplitude instead of the 8
+//     of a complex matrix, and every one-bit phase and scalar pending at a
+//     flush is applied as one phase block (a few complex products per
+//     amplitude however many phases it holds).  The open matrices of a stage
+//     are flushed together, so their D_R factors share one phase block.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -36,6 +44,79 @@ void mat_lmul(const cd* a, cd* u) {
   r[2] = a[2] * u[0] + a[3] * u[2];
   r[3] = a[2] * u[1] + a[3] * u[3];
   std::memcpy(u, r, sizeof(r));
+}
+
+// Euler split of a unitary 2x2 matrix u (row-major):
+//   u = g diag(e^{iA}, e^{-iA}) T diag(e^{iB}, e^{-iB})
+// with T = [[1, -t], [t, 1]] (rot = OP_ROT, t = s/c) or [[t, -1], [1, t]]
+// (OP_ROTC, t = c/s) and |t| <= 1: u = w [[p, -conj q], [q, conj p]] with
+// w^2 = det u, p = c e^{i theta_p}, q = s e^{i theta_q}, A = (theta_p -
+// theta_q)/2, B = (theta_p + theta_q)/2, and the larger of c, s goes into g.
+// The half-angle phases come from square roots of unit complex numbers (no
+// trigonometric calls); their common sign is fixed by e^{iA} e^{iB} =
+// e^{i theta_p}.  False where the product does not reproduce u to 1e-12 (a
+// matrix that is not unitary).
+struct EulerSplit {
+  int rot;
+  double t;
+  cd g, dl0, dl1, dr0, dr1;
+};
+
+// Square root of a unit complex number z = x + iy, in the right half-plane:
+// the larger component from its half-angle formula, the smaller as
+// y / (2 * larger), which avoids the cancellation in 1 - x near z = 1.
+inline cd unit_sqrt(cd z) {
+  const double x = std::max(-1.0, std::min(1.0, z.real())), y = z.imag();
+  if (x >= 0.0) {
+    const double re = std::sqrt(0.5 * (1.0 + x));
+    return cd(re, y / (2.0 * re));
+  }
+  double im = std::sqrt(0.5 * (1.0 - x));
+  if (y < 0.0) im = -im;
+  return cd(y / (2.0 * im), im);
+}
+
+bool euler_split(const cd* u, EulerSplit& e) {
+  const cd det = u[0] * u[3] - u[1] * u[2];
+  const double ad = std::sqrt(std::norm(det));
+  if (!(ad > 0.5 && ad < 2.0)) return false;
+  const cd w1 = unit_sqrt(det / ad);  // w = w1 sqrt(ad), |w1| = 1
+  const double rw = 1.0 / std::sqrt(ad);
+  const cd w = w1 * std::sqrt(ad);
+  const cd p = u[0] * std::conj(w1) * rw, q = u[2] * std::conj(w1) * rw;
+  const double c = std::sqrt(std::norm(p)), s = std::sqrt(std::norm(q));
+  const cd ep = c > 0.0 ? p / c : cd(1.0), eq = s > 0.0 ? q / s : cd(1.0);
+  cd eA = unit_sqrt(ep * std::conj(eq)), eB = unit_sqrt(ep * eq);
+  if (((eA * eB) * std::conj(ep)).real() < 0.0) eA = -eA;
+  double scale;
+  if (c >= s) {
+    e.rot = OP_ROT;
+    e.t = s / c;
+    scale = c;
+  } else {
+    e.rot = OP_ROTC;
+    e.t = c / s;
+    scale = s;
+  }
+  e.g = w * scale;
+  e.dl0 = eA;
+  e.dl1 = std::conj(eA);
+  e.dr0 = eB;
+  e.dr1 = std::conj(eB);
+  const cd T[4] = {e.rot == OP_ROT ? cd(1.0) : cd(e.t), e.rot == OP_ROT ? cd(-e.t) : cd(-1.0),
+                   e.rot == OP_ROT ? cd(e.t) : cd(1.0), e.rot == OP_ROT ? cd(1.0) : cd(e.t)};
+  const cd dl[2] = {e.dl0, e.dl1}, dr[2] = {e.dr0, e.dr1};
+  for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < 2; ++k)
+      if (std::norm(e.g * dl[r] * T[2 * r + k] * dr[k] - u[2 * r + k]) > 1e-24) return false;
+  return true;
+}
+
+// The rotation engine (Euler split + phase blocks); CUTSIM_ROT=0 applies every
+// fused matrix as a complex 2x2 and every phase as a table term instead.
+bool rot_engine() {
+  const char* e = std::getenv("CUTSIM_ROT");
+  return !(e && e[0] == '0');
 }
 
 }  // namespace
@@ -293,6 +374,16 @@ struct PassBuilder {
   uint64_t pend_adj = 0;
   cd pend_u[64][4];
   bool pend_has[64];
+  // one-bit phases diag(ph0, ph1) on virtual bit p, and a pending scalar
+  const bool rot = rot_engine();
+  cd ph0[64], ph1[64];
+  uint64_t ph_mask = 0;  // virtual bits with a pending one-bit phase
+  cd pend_const = 1.0;
+  int reg_index[64];  // register index of virtual bit p in the current stage, or -1
+  uint64_t reg_mask = 0;  // virtual bits held in registers in the current stage
+  bool overflow = false;  // an op with more than 65535 terms of one kind
+  int js[64];             // flush_all's open matrices and their splits
+  EulerSplit es[64];
 
   PassBuilder(HostProgram& h, int nq_, const std::vector<int>& tile_bits) : hp(h), nq(nq_) {
     const int k = (int)tile_bits.size();
@@ -307,6 +398,7 @@ struct PassBuilder {
     for (int j = 0; j < 64; ++j) {
       pend_has[j] = false;
       reg_of[j] = -1;
+      reg_index[j] = -1;
     }
   }
 
@@ -335,6 +427,18 @@ struct PassBuilder {
       add_sign(vpos[j], vpos[j]);
       return;
     }
+    if (rot && std::abs(d0) > 1e-150 && std::isfinite(std::abs(d1 / d0))) {
+      const int p = vpos[j];
+      if ((ph_mask >> p) & 1ull) {
+        ph0[p] *= d0;
+        ph1[p] *= d1;
+      } else {
+        ph_mask |= 1ull << p;
+        ph0[p] = d0;
+        ph1[p] = d1;
+      }
+      return;
+    }
     DTerm t{};
     t.p0 = (uint8_t)vpos[j];
     t.p1 = (uint8_t)vpos[j];
@@ -346,6 +450,7 @@ struct PassBuilder {
 
   // Does a pending diagonal factor depend on index bit vp?
   bool pending_touches(int vp) const {
+    if ((ph_mask >> vp) & 1ull) return true;
     if ((pend_adj >> vp) & 1ull) return true;
     if (vp > 0 && ((pend_adj >> (vp - 1)) & 1ull)) return true;
     for (const auto& d : pend_sign)
@@ -361,17 +466,24 @@ struct PassBuilder {
   // of them ride on that op at once, and a layer of CZs costs one sign sweep.
   void emit(int type, int t_reg, const cd* u, int vp) {
     DOp op{};
-    op.type = type;
-    op.t = t_reg;
+    op.type = (int8_t)type;
+    op.t = (int8_t)t_reg;
     const bool attach = type == OP_DIAG || pending_touches(vp);
     op.sign_adj = attach ? pend_adj : 0;
-    op.term_begin = (int32_t)hp.terms.size();
+    const size_t t0 = hp.terms.size();
+    op.term_begin = (int32_t)t0;
     if (attach)
       for (auto& d : pend_sign) hp.terms.push_back(d);
-    op.term_sign_end = (int32_t)hp.terms.size();
+    const size_t t1 = hp.terms.size();
+    if (attach) attach_phase_block(type == OP_DIAG);
+    const size_t t2 = hp.terms.size();
     if (attach)
       for (auto& d : pend_tab) hp.terms.push_back(d);
-    op.term_end = (int32_t)hp.terms.size();
+    const size_t t3 = hp.terms.size();
+    if (t1 - t0 > 0xFFFF || t2 - t1 > 0xFFFF || t3 - t2 > 0xFFFF || t3 > 0x7FFFFFFF) overflow = true;
+    op.n_sign = (uint16_t)(t1 - t0);
+    op.n_phase = (uint16_t)(t2 - t1);
+    op.n_table = (uint16_t)(t3 - t2);
     if (attach) {
       pend_sign.clear();
       pend_tab.clear();
@@ -385,16 +497,102 @@ struct PassBuilder {
     hp.ops.push_back(op);
   }
 
-  bool pending_terms() const { return pend_adj || !pend_sign.empty() || !pend_tab.empty(); }
+  // The pending scalar and pending one-bit phases as one phase block.  An op
+  // on a register bit takes the phases on the stage's register bits (they
+  // multiply into h_i; a phase on another bit cannot be needed before a
+  // stage that holds its bit in a register, or the pass's final OP_DIAG);
+  // the final OP_DIAG (all = true) takes every phase, those on other bits as
+  // TERM_PFIX terms.  ph0 of every phase goes into K, so each factor is
+  // ph1 / ph0 on a set bit.  The block's 12 entries are precomputed products:
+  // K {1, h0, h1, h0 h1} and the 8 products of h2, h3, h4.
+  void attach_phase_block(bool all) {
+    const uint64_t take = all ? ph_mask : (ph_mask & reg_mask);
+    if (!take && pend_const == cd(1.0)) return;
+    ph_mask &= ~take;
+    cd K = pend_const;
+    cd h[MAX_REG_BITS];
+    for (auto& x : h) x = 1.0;
+    std::vector<DTerm> fix;
+    for (uint64_t rest = take; rest; rest &= rest - 1) {
+      const int p = __builtin_ctzll(rest);
+      K *= ph0[p];
+      const cd r = ph1[p] / ph0[p];
+      if (reg_index[p] >= 0) {
+        h[reg_index[p]] *= r;
+      } else if (r != cd(1.0)) {
+        const cd tab[4] = {r, 0.0, 0.0, 0.0};
+        DTerm t{};
+        t.kind = TERM_PFIX;
+        t.p0 = (uint8_t)p;
+        t.p1 = (uint8_t)p;
+        t.tab = add_table(tab);
+        fix.push_back(t);
+      }
+    }
+    pend_const = 1.0;
+    const cd t0[4] = {K, K * h[0], K * h[1], K * h[0] * h[1]};
+    const cd t1[4] = {1.0, h[2], h[3], h[2] * h[3]};
+    const cd t2[4] = {h[4], h[2] * h[4], h[3] * h[4], h[2] * h[3] * h[4]};
+    DTerm b{};
+    b.kind = TERM_PBLOCK;
+    b.tab = add_table(t0);
+    add_table(t1);  // consecutive: the block's entries 4..11
+    add_table(t2);
+    hp.terms.push_back(b);
+    for (auto& d : fix) hp.terms.push_back(d);
+  }
+
+  bool pending_terms() const {
+    return pend_adj || !pend_sign.empty() || !pend_tab.empty() || pend_const != cd(1.0) ||
+           ph_mask != 0;
+  }
 
   void flush(int j) {
     if (!pend_has[j]) return;
+    if (rot) {
+      flush_all();
+      return;
+    }
     pend_has[j] = false;
     const cd* u = pend_u[j];
     if (is_zero(u[1]) && is_zero(u[2])) {
       add_diag1(j, u[0], u[3]);
     } else {
       emit(OP_DENSE, reg_of[j], u, vpos[j]);
+    }
+  }
+
+  // Rotation engine: every open matrix at once.  The D_R phases of all of
+  // them are pending before the first rotation, which carries them (and
+  // whatever else is pending) as one phase block; the D_L phases and the
+  // scalars stay pending after the rotations.  Flushing a matrix early is
+  // always valid: it holds every gate so far on its qubit.
+  void flush_all() {
+    int n = 0;
+    for (int j = 0; j < nq; ++j) {
+      if (!pend_has[j]) continue;
+      pend_has[j] = false;
+      const cd* u = pend_u[j];
+      if (is_zero(u[1]) && is_zero(u[2])) {
+        add_diag1(j, u[0], u[3]);
+        continue;
+      }
+      EulerSplit e;
+      if (!euler_split(u, e)) {
+        emit(OP_DENSE, reg_of[j], u, vpos[j]);
+        continue;
+      }
+      js[n] = j;
+      es[n++] = e;
+    }
+    for (int i = 0; i < n; ++i) add_diag1(js[i], es[i].dr0, es[i].dr1);
+    for (int i = 0; i < n; ++i) {
+      const cd m[4] = {es[i].t, 0.0, 0.0, 0.0};
+      emit(es[i].rot, reg_of[js[i]], m, vpos[js[i]]);
+    }
+    for (int i = 0; i < n; ++i) {
+      add_diag1(js[i], es[i].dl0, es[i].dl1);
+      pend_const *= es[i].g;
     }
   }
 
@@ -446,10 +644,18 @@ struct PassBuilder {
 
   // Start a stage whose register bits are the tile bits of `qubits`.
   void begin_stage(const std::vector<int>& qubits, DStage& st) {
-    for (int j = 0; j < 64; ++j) reg_of[j] = -1;
+    for (int j = 0; j < 64; ++j) {
+      reg_of[j] = -1;
+      reg_index[j] = -1;
+    }
     std::vector<int> pos;
     for (int j : qubits) pos.push_back(vpos[j]);
     std::sort(pos.begin(), pos.end());
+    reg_mask = 0;
+    for (size_t i = 0; i < pos.size(); ++i) {
+      reg_index[pos[i]] = (int)i;
+      reg_mask |= 1ull << pos[i];
+    }
     for (int i = 0; i < 8; ++i) st.rb[i] = (int8_t)(i < (int)pos.size() ? pos[i] : 0);
     for (int j : qubits)
       for (size_t i = 0; i < pos.size(); ++i)
@@ -460,6 +666,7 @@ struct PassBuilder {
   // End a stage: every open matrix is emitted; diagonal factors may stay
   // pending into the next stage of the same pass.
   void end_stage(DStage& st, bool last) {
+    if (rot) flush_all();
     for (int j = 0; j < nq; ++j) flush(j);
     if (last && pending_terms()) emit(OP_DIAG, 0, nullptr, -1);
     st.op_end = (int32_t)hp.ops.size();
@@ -517,6 +724,10 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
       return;
     }
     pb.end_stage(st, left == 0);
+    if (pb.overflow) {
+      hp.nq = -1;
+      return;
+    }
     hp.stages.push_back(st);
   } while (left > 0);
   P.stage_end = (int32_t)hp.stages.size();

@@ -195,7 +195,7 @@ ImageLayout append_program_image(const HostProgram& hp, int precision,
   // op's descriptor; diagonal-only ops get a zero slot.
   std::vector<cd> per_op(hp.ops.size() * 4, cd(0.0, 0.0));
   for (size_t o = 0; o < hp.ops.size(); ++o)
-    if (hp.ops[o].type == OP_DENSE)
+    if (hp.ops[o].type != OP_DIAG)
       for (int e = 0; e < 4; ++e) per_op[4 * o + e] = hp.mats[4 * (size_t)hp.ops[o].mat + e];
   put(L.o_mats, per_op);
   put(L.o_tabs, hp.tabs);

@@ -120,6 +120,42 @@ struct StageRegs {
   }
 };
 
+// Apply a phase block: slot j gets Phi lo[j & 3] hi[j >> 2] with the block's
+// precomputed products lo and hi (the host folds the block's constant K into
+// lo) and Phi the product of the ratios of the TERM_PFIX terms whose bit is
+// set in the thread's fixed index bits c (1 when there are none): two complex
+// products per amplitude however many phases the block holds.
+template <typename R, int RB>
+__device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], const DOp& op,
+                                            uint64_t c, const DTerm* __restrict__ terms,
+                                            const R* __restrict__ tabs) {
+  constexpr int L = RB < 2 ? RB : 2;
+  constexpr int H = RB - L;
+  const R* tb = tabs + 8 * terms[op.term_sign_end()].tab;
+  R pr = R(1), pi = R(0);
+  const bool fixed = op.term_phase_end() > op.term_sign_end() + 1;
+  for (int t = op.term_sign_end() + 1; t < op.term_phase_end(); ++t) {
+    const DTerm d = terms[t];
+    if ((c >> d.p0) & 1u) {
+      const R* f = tabs + 8 * d.tab;
+      cmul(pr, pi, f[0], f[1]);
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < (1 << L); ++l) {  // one lo product at a time: few live registers
+    R lr = tb[2 * l], li = tb[2 * l + 1];
+    if (fixed) cmul(lr, li, pr, pi);
+#pragma unroll
+    for (int m = 0; m < (1 << H); ++m) cmul(a[(m << L) | l].x, a[(m << L) | l].y, lr, li);
+  }
+#pragma unroll
+  for (int m = 1; m < (1 << H); ++m) {  // one hi product at a time: few live registers
+    const R hr = tb[8 + 2 * m], hh = tb[9 + 2 * m];
+#pragma unroll
+    for (int l = 0; l < (1 << L); ++l) cmul(a[(m << L) | l].x, a[(m << L) | l].y, hr, hh);
+  }
+}
+
 // Multiply the thread's 2^RB amplitudes by an op's diagonal factors.  With
 // v = c | r (c: the thread's fixed index bits, r: register bits, disjoint),
 // the CZ-type sign (-1)^{popcount(v & (v>>1) & adj)} splits into a constant,
@@ -144,7 +180,7 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
         smask ^= slot_pattern(i) & slot_pattern(i + 1 < RB ? i + 1 : i);
     }
   }
-  for (int t = op.term_begin; t < op.term_sign_end; ++t) {
+  for (int t = op.term_begin; t < op.term_sign_end(); ++t) {
     const DTerm d = terms[t];
     const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
     const uint32_t c0 = (uint32_t)(c >> d.p0) & 1u, c1 = (uint32_t)(c >> d.p1) & 1u;
@@ -172,7 +208,8 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
       }
     }
   }
-  for (int t = op.term_sign_end; t < op.term_end; ++t) {
+  if (op.term_phase_end() > op.term_sign_end()) apply_phase<R, RB>(a, op, c, terms, tabs);
+  for (int t = op.term_phase_end(); t < op.term_end(); ++t) {
     const DTerm d = terms[t];
     const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
     const int c0 = (int)((c >> d.p0) & 1u), c1 = (int)((c >> d.p1) & 1u);
@@ -248,6 +285,36 @@ __device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const
     b0.y = u0r * a0.y + u0i * a0.x + u1r * a1.y + u1i * a1.x;
     b1.x = u2r * a0.x - u2i * a0.y + u3r * a1.x - u3i * a1.y;
     b1.y = u2r * a0.y + u2i * a0.x + u3r * a1.y + u3i * a1.x;
+    a[j0] = b0;
+    a[j1] = b1;
+  }
+}
+
+// Real rotation in tangent form on register bit RHO of every held pair:
+// (a, b) <- (a - t b, b + t a), or with COT (a, b) <- (t a - b, a + t b);
+// two multiply-adds per amplitude.
+template <typename R, int RB, int RHO, bool COT>
+__device__ __forceinline__ void rot_mat(typename CT<R>::C (&a)[1 << RB], R t) {
+  using C = typename CT<R>::C;
+  constexpr int N = 1 << RB;
+#pragma unroll
+  for (int p = 0; p < N / 2; ++p) {
+    constexpr int lo = (1 << RHO) - 1;
+    const int j0 = ((p & ~lo) << 1) | (p & lo);
+    const int j1 = j0 | (1 << RHO);
+    const C a0 = a[j0], a1 = a[j1];
+    C b0, b1;
+    if (COT) {
+      b0.x = t * a0.x - a1.x;
+      b0.y = t * a0.y - a1.y;
+      b1.x = t * a1.x + a0.x;
+      b1.y = t * a1.y + a0.y;
+    } else {
+      b0.x = a0.x - t * a1.x;
+      b0.y = a0.y - t * a1.y;
+      b1.x = a1.x + t * a0.x;
+      b1.y = a1.y + t * a0.y;
+    }
     a[j0] = b0;
     a[j1] = b1;
   }
@@ -386,17 +453,30 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const DOp op = ops[o];
         const Mat<R> m = load_mat<R>(mats + 8 * o);
-        if (op.sign_adj != 0 || op.term_end > op.term_begin)
+        if (op.sign_adj != 0 || op.term_end() > op.term_begin)
           apply_diag<R, RB>(a, op, cfix, sr, terms, tabs);
+#define CC_OP_SWITCH(CALL)                                     \
+  switch (op.t) {                                              \
+    case 0: CALL(0); break;                                    \
+    case 1: if (RB > 1) CALL((RB > 1 ? 1 : 0)); break;         \
+    case 2: if (RB > 2) CALL((RB > 2 ? 2 : 0)); break;         \
+    case 3: if (RB > 3) CALL((RB > 3 ? 3 : 0)); break;         \
+    default: if (RB > 4) CALL((RB > 4 ? 4 : 0)); break;        \
+  }
+#define CC_DENSE(RHO) dense_mat<R, RB, RHO>(a, m)
+#define CC_ROT(RHO) rot_mat<R, RB, RHO, false>(a, m.v[0])
+#define CC_ROTC(RHO) rot_mat<R, RB, RHO, true>(a, m.v[0])
         if (op.type == OP_DENSE) {
-          switch (op.t) {
-            case 0: dense_mat<R, RB, 0>(a, m); break;
-            case 1: if (RB > 1) dense_mat<R, RB, (RB > 1 ? 1 : 0)>(a, m); break;
-            case 2: if (RB > 2) dense_mat<R, RB, (RB > 2 ? 2 : 0)>(a, m); break;
-            case 3: if (RB > 3) dense_mat<R, RB, (RB > 3 ? 3 : 0)>(a, m); break;
-            default: if (RB > 4) dense_mat<R, RB, (RB > 4 ? 4 : 0)>(a, m); break;
-          }
+          CC_OP_SWITCH(CC_DENSE)
+        } else if (op.type == OP_ROT) {
+          CC_OP_SWITCH(CC_ROT)
+        } else if (op.type == OP_ROTC) {
+          CC_OP_SWITCH(CC_ROTC)
         }
+#undef CC_DENSE
+#undef CC_ROT
+#undef CC_ROTC
+#undef CC_OP_SWITCH
       }
 
 #pragma unroll

@@ -108,12 +108,16 @@ def test_tc_forms_stationary_and_streaming(cuda_lib, monkeypatch, stationary, fo
     assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
 
 
+@pytest.mark.parametrize("kblock", ["128", "64", "32"])
 @pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
-@pytest.mark.parametrize("segs,c", [([7, 8], 4), ([9, 10], 6), ([10, 9], 8), ([8, 11], 5)])
-def test_tc_pair_form(cuda_lib, monkeypatch, form, segs, c):
+@pytest.mark.parametrize("segs,c", [([7, 8], 4), ([9, 10], 6), ([10, 9], 8), ([8, 11], 5),
+                                    ([9, 9], 10)])
+def test_tc_pair_form(cuda_lib, monkeypatch, kblock, form, segs, c):
     # two CTAs of a cluster share each column tile by TMA multicast (the
-    # default); CUTSIM_TC_PAIR=0 selects the single-CTA kernel
+    # default), streaming K in blocks of 128, 64 or 32 bytes (2, 4 or 8
+    # stages); CUTSIM_TC_PAIR=0 selects the single-CTA kernel
     monkeypatch.delenv("CUTSIM_TC_PAIR", raising=False)
+    monkeypatch.setenv("CUTSIM_TC_KBLOCK", kblock)
     q = sum(segs)
     gates = w.brickwork_cut(q, 12, 41 + c, segs, c)
     psi, _ = run(gates, q, segs, form)

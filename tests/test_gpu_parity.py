@@ -233,3 +233,32 @@ def test_copy_to_host(cuda_lib, n):
     api.copy_to_host(src, plain)
     torch.cuda.synchronize()
     assert torch.equal(plain, src.cpu())
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", ["brickwork", "random", "staircase_t", "rank4"])
+def test_rotation_engine_on_and_off(cuda_lib, monkeypatch, rot, prec, kind):
+    # Each fused one-qubit matrix as a tangent-form rotation between one-bit
+    # phases collected into phase blocks (CUTSIM_ROT=1, the default), or as a
+    # complex 2x2 with every phase a table term (CUTSIM_ROT=0): both equal the
+    # oracle, on circuits whose fused matrices include diagonal, anti-diagonal
+    # and general ones, in the uncut simulation and in the segments of a cut.
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    if kind == "brickwork":
+        q, segs = 16, [8, 8]
+        gates = w.brickwork_cut(q, 10, 5, segs, 3)
+    elif kind == "random":
+        q, segs = 14, [7, 7]
+        gates = w.random_circuit(q, 160, 7)
+    elif kind == "staircase_t":
+        q, segs = 12, [6, 6]
+        gates = w.staircase_depth(q, 3, 2)
+    else:
+        q, segs = 12, [6, 6]
+        gates = w.brickwork_cut(q, 6, 9, segs, 2, boundary_kind="CAN")
+    ref = sv.simulate(q, gates)
+    u, _ = gpu_uncut(gates, q, prec)
+    assert_parity(u.cpu().numpy(), ref, prec, "uncut")
+    psi, _, _ = gpu_cut(gates, q, segs, "projector", prec)
+    assert_parity(psi.cpu().numpy(), ref, prec, "cut")
