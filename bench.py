@@ -943,6 +943,13 @@ def main(argv=None):
                               "frac": tc_flops / mean["merge"] / 1e12 / tc_peak,
                               "peak_source": peak_src + " bf16 burst" +
                               (" x 0.5 (nominal TF32/BF16)" if tc_form == "tf32x3" else "")}
+    # verification: both 2^q vectors read once (complex64: FP32 exact products
+    # in double-float, HBM-bound; complex128: FP64 arithmetic bounds it)
+    verify_bytes = 2.0 * amp * n_amp
+    verify_rf = {"bound": "hbm", "achieved": verify_bytes / mean["verify"] / 1e9, "peak": hbm,
+                 "unit": "GB/s", "frac": verify_bytes / mean["verify"] / 1e9 / hbm,
+                 "traffic": None, "kernel": "compare_partial", "bytes_per_launch": verify_bytes,
+                 "launch_s": mean["verify"], "peak_source": peak_src}
     dominant = pass_rf if orig_dev > mean["merge"] else merge_rf
     # per step: one persistent launch for every segment pass, the earlier
     # chain stages (FMA), the last stage (split + tensor-core kernel, or FMA),
@@ -979,7 +986,7 @@ def main(argv=None):
                    "fidelity": cmp["fidelity"], "norm2_cut": cmp["norm2_a"],
                    "norm2_uncut": cmp["norm2_b"]},
         "roofline": dominant,
-        "rooflines": {"merge": merge_rf, "uncut_pass": pass_rf},
+        "rooflines": {"merge": merge_rf, "uncut_pass": pass_rf, "verify": verify_rf},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches * a.steps,

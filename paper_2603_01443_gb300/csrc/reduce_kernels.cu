@@ -70,35 +70,74 @@ __device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + 
 
 constexpr int kRun = 64;  // elements per thread between FP64 accumulations
 
+// One element of the complex64 comparison: the maxima in FP32, the four
+// sums as exact products added in double-float.
+__device__ __forceinline__ void cmp_elem(float ar, float ai, float br, float bi, float& d2,
+                                         float& b2, DF& re, DF& im, DF& na, DF& nb) {
+  const float dr = ar - br, di = ai - bi;
+  d2 = fmaxf(d2, fmaf(dr, dr, di * di));
+  b2 = fmaxf(b2, fmaf(br, br, bi * bi));
+  df_add_prod(re, ar, br);  // Re conj(a) b = ar br + ai bi
+  df_add_prod(re, ai, bi);
+  df_add_prod(im, ar, bi);  // Im conj(a) b = ar bi - ai br
+  df_add_prod(im, -ai, br);
+  df_add_prod(na, ar, ar);
+  df_add_prod(na, ai, ai);
+  df_add_prod(nb, br, br);
+  df_add_prod(nb, bi, bi);
+}
+
 // complex64 inputs: the products are formed exactly in FP32 and summed in
 // double-float over runs of kRun elements per thread; each run's sum is then
 // added in FP64.  GB300's FP64 rate (1/64 of FP32) would otherwise bound the
 // pass at ~20 FP64 operations per element, far below the HBM rate.  The
 // maxima are taken in FP32 (the differences of nearby FP32 values are
-// exact; the squares carry 2^-24 relative error).
+// exact; the squares carry 2^-24 relative error).  Each thread reads two
+// amplitudes per 16-byte load (the buffers are 16-byte aligned) with kLoads
+// loads of each vector in flight before any arithmetic; an odd last
+// amplitude is added by thread 0 of block 0.
+constexpr int kLoads = 4;
 __global__ void __launch_bounds__(RB)
     compare_partial_c64(const float2* __restrict__ a, const float2* __restrict__ b, int64_t n,
                         double* __restrict__ partials) {
   Acc6 v{0, 0, 0, 0, 0, 0};
   float d2 = 0.f, b2 = 0.f;
+  const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a);
+  const float4* __restrict__ b4 = reinterpret_cast<const float4*>(b);
+  const int64_t n2 = n >> 1;
   const int64_t stride = (int64_t)gridDim.x * RB;
   int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x;
-  while (i < n) {
+  while (i < n2) {
     DF re{0.f, 0.f}, im{0.f, 0.f}, na{0.f, 0.f}, nb{0.f, 0.f};
-    for (int r = 0; r < kRun && i < n; ++r, i += stride) {
-      const float2 x = __ldcs(a + i), y = __ldcs(b + i);
-      const float dr = x.x - y.x, di = x.y - y.y;
-      d2 = fmaxf(d2, fmaf(dr, dr, di * di));
-      b2 = fmaxf(b2, fmaf(y.x, y.x, y.y * y.y));
-      df_add_prod(re, x.x, y.x);  // Re conj(a) b = ar br + ai bi
-      df_add_prod(re, x.y, y.y);
-      df_add_prod(im, x.x, y.y);  // Im conj(a) b = ar bi - ai br
-      df_add_prod(im, -x.y, y.x);
-      df_add_prod(na, x.x, x.x);
-      df_add_prod(na, x.y, x.y);
-      df_add_prod(nb, y.x, y.x);
-      df_add_prod(nb, y.y, y.y);
+#pragma unroll 1
+    for (int r = 0; r < kRun / (2 * kLoads) && i < n2; ++r, i += kLoads * stride) {
+      float4 x[kLoads], y[kLoads];
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const int64_t j = i + u * stride;
+        if (j < n2) {
+          x[u] = __ldcs(a4 + j);
+          y[u] = __ldcs(b4 + j);
+        } else {  // zeros add nothing to any sum or maximum
+          x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          y[u] = x[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        cmp_elem(x[u].x, x[u].y, y[u].x, y[u].y, d2, b2, re, im, na, nb);
+        cmp_elem(x[u].z, x[u].w, y[u].z, y[u].w, d2, b2, re, im, na, nb);
+      }
     }
+    v.re += df_value(re);
+    v.im += df_value(im);
+    v.na += df_value(na);
+    v.nb += df_value(nb);
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    DF re{0.f, 0.f}, im{0.f, 0.f}, na{0.f, 0.f}, nb{0.f, 0.f};
+    const float2 x = a[n - 1], y = b[n - 1];
+    cmp_elem(x.x, x.y, y.x, y.y, d2, b2, re, im, na, nb);
     v.re += df_value(re);
     v.im += df_value(im);
     v.na += df_value(na);

@@ -186,6 +186,25 @@ def test_compare_and_gather(cuda_lib, prec):
         api.gather(ta, [n], prec)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 15, 4097, 2 * 608 * 256 * 8 + 3, 5 * 608 * 256 * 64 + 1])
+def test_compare_lengths(cuda_lib, n):
+    # complex64 compare reads two amplitudes per load, four loads in flight,
+    # runs of 64 per thread: lengths below one load, odd tails, and lengths
+    # that end inside a run or a grid stride
+    rng = np.random.default_rng(n)
+    a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    b = (a + 1e-3 * rng.standard_normal(n)).astype(np.complex64)
+    got = api.compare(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), "c64")
+    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
+    inner = np.vdot(a64, b64)
+    assert abs(got["max_abs_diff"] - np.max(np.abs(a64 - b64))) <= 1e-7 * np.max(np.abs(a64 - b64))
+    assert abs(got["max_abs_b"] - np.max(np.abs(b64))) <= 1e-7 * np.max(np.abs(b64))
+    assert abs(got["inner_re"] - inner.real) <= 1e-11 * abs(inner)
+    assert abs(got["inner_im"] - inner.imag) <= 1e-11 * abs(inner)
+    assert abs(got["norm2_a"] - np.vdot(a64, a64).real) <= 1e-11 * np.vdot(a64, a64).real
+    assert abs(got["norm2_b"] - np.vdot(b64, b64).real) <= 1e-11 * np.vdot(b64, b64).real
+
+
 def test_error_paths_on_device(cuda_lib):
     gates = w.brickwork(10, 3, 0)
     plan = api.CutPlan(gates, 10, [5, 5], "projector", "c128")
