@@ -497,25 +497,31 @@ struct PassBuilder {
     hp.ops.push_back(op);
   }
 
-  // The pending scalar and pending one-bit phases as one phase block.  An op
-  // on a register bit takes the phases on the stage's register bits (they
-  // multiply into h_i; a phase on another bit cannot be needed before a
-  // stage that holds its bit in a register, or the pass's final OP_DIAG);
-  // the final OP_DIAG (all = true) takes every phase, those on other bits as
-  // TERM_PFIX terms.  ph0 of every phase goes into K, so each factor is
-  // ph1 / ph0 on a set bit.  The block's 12 entries are precomputed products:
-  // K {1, h0, h1, h0 h1} and the 8 products of h2, h3, h4.
+  // The pending one-bit phases as one phase block.  An op on a register bit
+  // takes the phases on the stage's register bits (they multiply into h_i; a
+  // phase on another bit cannot be needed before a stage that holds its bit
+  // in a register, or the pass's final OP_DIAG); the final OP_DIAG
+  // (all = true) takes every phase, those on other bits as TERM_PFIX terms.
+  // ph0 of every phase is a constant factor: it joins the pending scalar,
+  // which only the final OP_DIAG applies (in its K), so each factor is
+  // ph1 / ph0 on a set bit (a block folds the scalar in early once it falls
+  // below 2^-24 in magnitude).  The block's 12 entries are precomputed products
+  // -- K {1, h0, h1, h0 h1} and the 8 products of h2, h3, h4 -- and its p0
+  // holds flags for the kernel to skip products equal to 1: bit 0 lo[0],
+  // bit 1 lo[1..3], bit 2 hi.
   void attach_phase_block(bool all) {
+    // the deferred scalar is folded in early once it is small, so the
+    // amplitudes (which carry its inverse) stay far from FP32 overflow
+    const bool fold = all || std::norm(pend_const) < 0x1p-48;
     const uint64_t take = all ? ph_mask : (ph_mask & reg_mask);
-    if (!take && pend_const == cd(1.0)) return;
+    if (!take && !(fold && pend_const != cd(1.0))) return;
     ph_mask &= ~take;
-    cd K = pend_const;
     cd h[MAX_REG_BITS];
     for (auto& x : h) x = 1.0;
     std::vector<DTerm> fix;
     for (uint64_t rest = take; rest; rest &= rest - 1) {
       const int p = __builtin_ctzll(rest);
-      K *= ph0[p];
+      pend_const *= ph0[p];
       const cd r = ph1[p] / ph0[p];
       if (reg_index[p] >= 0) {
         h[reg_index[p]] *= r;
@@ -529,12 +535,19 @@ struct PassBuilder {
         fix.push_back(t);
       }
     }
-    pend_const = 1.0;
+    cd K = 1.0;
+    if (fold) {
+      K = pend_const;
+      pend_const = 1.0;
+    }
     const cd t0[4] = {K, K * h[0], K * h[1], K * h[0] * h[1]};
     const cd t1[4] = {1.0, h[2], h[3], h[2] * h[3]};
     const cd t2[4] = {h[4], h[2] * h[4], h[3] * h[4], h[2] * h[3] * h[4]};
     DTerm b{};
     b.kind = TERM_PBLOCK;
+    b.p0 = (uint8_t)((K != cd(1.0) ? 1 : 0) |
+                     (K != cd(1.0) || h[0] != cd(1.0) || h[1] != cd(1.0) ? 2 : 0) |
+                     (h[2] != cd(1.0) || h[3] != cd(1.0) || h[4] != cd(1.0) ? 4 : 0));
     b.tab = add_table(t0);
     add_table(t1);  // consecutive: the block's entries 4..11
     add_table(t2);

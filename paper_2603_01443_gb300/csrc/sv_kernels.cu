@@ -123,15 +123,22 @@ struct StageRegs {
 // Apply a phase block: slot j gets Phi lo[j & 3] hi[j >> 2] with the block's
 // precomputed products lo and hi (the host folds the block's constant K into
 // lo) and Phi the product of the ratios of the TERM_PFIX terms whose bit is
-// set in the thread's fixed index bits c (1 when there are none): two complex
-// products per amplitude however many phases the block holds.
+// set in the thread's fixed index bits c (1 when there are none): at most two
+// complex products per amplitude however many phases the block holds, and
+// none for the products the block's flags mark as 1.
 template <typename R, int RB>
 __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                             uint64_t c, const DTerm* __restrict__ terms,
                                             const R* __restrict__ tabs) {
   constexpr int L = RB < 2 ? RB : 2;
   constexpr int H = RB - L;
-  const R* tb = tabs + 8 * terms[op.term_sign_end()].tab;
+  const DTerm blk = terms[op.term_sign_end()];
+  const R* tb = tabs + 8 * blk.tab;
+  // bit 0: lo[0] != 1, bit 1: lo[1..3], bit 2: hi.  Skipping pays where the
+  // FP64 pipes bound the pass; the FP32 pass is bound by issue, where the
+  // branches cost more than the products they save (measured), so complex64
+  // applies every product.
+  const uint32_t flags = sizeof(R) == 8 ? blk.p0 : 7u;
   R pr = R(1), pi = R(0);
   const bool fixed = op.term_phase_end() > op.term_sign_end() + 1;
   for (int t = op.term_sign_end() + 1; t < op.term_phase_end(); ++t) {
@@ -143,16 +150,19 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
   }
 #pragma unroll
   for (int l = 0; l < (1 << L); ++l) {  // one lo product at a time: few live registers
+    if (!fixed && !(flags & (l == 0 ? 1u : 2u))) continue;  // a product equal to 1
     R lr = tb[2 * l], li = tb[2 * l + 1];
     if (fixed) cmul(lr, li, pr, pi);
 #pragma unroll
     for (int m = 0; m < (1 << H); ++m) cmul(a[(m << L) | l].x, a[(m << L) | l].y, lr, li);
   }
+  if (flags & 4u) {
 #pragma unroll
-  for (int m = 1; m < (1 << H); ++m) {  // one hi product at a time: few live registers
-    const R hr = tb[8 + 2 * m], hh = tb[9 + 2 * m];
+    for (int m = 1; m < (1 << H); ++m) {  // one hi product at a time: few live registers
+      const R hr = tb[8 + 2 * m], hh = tb[9 + 2 * m];
 #pragma unroll
-    for (int l = 0; l < (1 << L); ++l) cmul(a[(m << L) | l].x, a[(m << L) | l].y, hr, hh);
+      for (int l = 0; l < (1 << L); ++l) cmul(a[(m << L) | l].x, a[(m << L) | l].y, hr, hh);
+    }
   }
 }
 

@@ -12,7 +12,7 @@ import workload as w
 from oracle import cutting as ct
 from oracle import statevector as sv
 from paper_2603_01443_gb300 import api, capi
-from gpu_util import TOL, assert_parity, gpu_cut, gpu_uncut, rel_err
+from gpu_util import FID_TOL, TOL, assert_parity, fidelity, gpu_cut, gpu_uncut, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -281,3 +281,22 @@ def test_rotation_engine_on_and_off(cuda_lib, monkeypatch, rot, prec, kind):
     assert_parity(u.cpu().numpy(), ref, prec, "uncut")
     psi, _, _ = gpu_cut(gates, q, segs, "projector", prec)
     assert_parity(psi.cpu().numpy(), ref, prec, "cut")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_deep_single_pass(cuda_lib, prec):
+    # 12 qubits fit one tile, so a depth-1000 brickwork is one pass of ~12000
+    # rotations: the scalar factors the rotation engine defers (each
+    # rotation's cos or sin) are folded in early enough that the amplitudes,
+    # which carry their inverse, stay finite and accurate
+    q = 12
+    gates = w.brickwork(q, 1000, 4)
+    ref = sv.simulate(q, gates)
+    u, _ = gpu_uncut(gates, q, prec)
+    got = u.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    # rounding grows like sqrt(G) 2^-24 per amplitude over G ~ 12000 gate
+    # applications (~7e-6 in complex64); an overflow would give inf or nan
+    tol = 1e-4 if prec == "c64" else 1e-12
+    assert rel_err(got, ref) <= tol
+    assert 1 - fidelity(got, ref) <= FID_TOL
