@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -118,6 +119,48 @@ __device__ __forceinline__ void tile_c64(const float2* __restrict__ A, const flo
   for (int i = 0; i < RPT; ++i)
     __stcs(reinterpret_cast<float4*>(o + i * NA),
            make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y));
+}
+
+// Few terms (K <= 8): a pure store stream.  A CTA owns 8 rows x 512 columns
+// of the output (each row a 4 KB contiguous run), each thread 2 columns of
+// every row; the factors' values come straight from L2 (the lower factor's
+// two values per term with one 16-byte load, the upper factor's eight row
+// values with warp-uniform loads), so there is no shared-memory staging and
+// no barrier between tiles.
+constexpr int kWideRows = 8;
+constexpr int kWideCols = 512;
+__global__ void __launch_bounds__(256)
+    merge_wide_c64(const float2* __restrict__ A, const float2* __restrict__ B,
+                   float2* __restrict__ out, int qa, int qb, int K,
+                   const int32_t* __restrict__ aidx, const int32_t* __restrict__ bidx) {
+  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
+  const int64_t tiles_x = NA / kWideCols, n_tiles = tiles_x * (NB / kWideRows);
+  const int t = threadIdx.x;
+  for (int64_t w = blockIdx.x; w < n_tiles; w += gridDim.x) {
+    const int64_t y0 = (w / tiles_x) * kWideRows, x0 = (w % tiles_x) * kWideCols + 2 * t;
+    float2 acc[kWideRows][2];
+#pragma unroll
+    for (int r = 0; r < kWideRows; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)aidx[k] * NA + x0));
+      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+      const float4* brow = reinterpret_cast<const float4*>(B + (int64_t)bidx[k] * NB + y0);
+#pragma unroll
+      for (int r = 0; r < kWideRows; r += 2) {
+        const float4 b = __ldg(brow + r / 2);
+        const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+        cfma(acc[r][0], a0, b0);
+        cfma(acc[r][1], a1, b0);
+        cfma(acc[r + 1][0], a0, b1);
+        cfma(acc[r + 1][1], a1, b1);
+      }
+    }
+    float2* o = out + y0 * NA + x0;
+#pragma unroll
+    for (int r = 0; r < kWideRows; ++r)
+      __stcs(reinterpret_cast<float4*>(o + r * NA),
+             make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y));
+  }
 }
 
 template <bool COMP>
@@ -320,7 +363,19 @@ cc_status launch_merge_fma(const MergeStage& st, int precision, void* stream) {
   const int64_t NA = int64_t(1) << st.qa, NB = int64_t(1) << st.qb;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (precision == CC_C64) {
-    if (st.qa >= 7 && st.qb >= 5) {
+    const char* wide_env = std::getenv("CUTSIM_MERGE_WIDE");
+    const bool wide_ok = !(wide_env && wide_env[0] == '0');
+    // the wide form re-reads the lower factor once per 8 output rows (the
+    // tile form once per 32), so it is taken while the lower factor's K terms
+    // are small: q = 30 K = 4 1.81 -> 1.62 ms, K = 2 1.46 -> 1.26 ms; the
+    // last stage of an n = 3 chain with K * NA = 2^22 ran 1.86 -> 1.93 ms
+    if (wide_ok && st.Z == 1 && st.K <= 8 && st.qa >= 9 && st.qb >= 3 &&
+        st.K * NA <= (int64_t(1) << 21)) {
+      const int64_t tiles = (NA / kWideCols) * (NB / kWideRows);
+      merge_wide_c64<<<(unsigned)std::min(tiles, cap), 256, 0, s>>>(
+          (const float2*)st.A, (const float2*)st.B, (float2*)st.out, st.qa, st.qb, (int)st.K,
+          st.aidx, st.bidx);
+    } else if (st.qa >= 7 && st.qb >= 5) {
       const int64_t tiles = (NA >> 7) * (NB >> 5) * st.Z;
       auto kern = st.K > KC ? merge_tile_c64<true> : merge_tile_c64<false>;
       kern<<<(unsigned)std::min(tiles, cap), 256, 0, s>>>(

@@ -300,3 +300,21 @@ def test_deep_single_pass(cuda_lib, prec):
     tol = 1e-4 if prec == "c64" else 1e-12
     assert rel_err(got, ref) <= tol
     assert 1 - fidelity(got, ref) <= FID_TOL
+
+
+@pytest.mark.parametrize("segs", [[9, 5], [10, 8], [12, 3], [9, 9]])
+@pytest.mark.parametrize("c", [0, 1, 2, 3])
+def test_few_term_wide_merge(cuda_lib, monkeypatch, segs, c):
+    # complex64 merges of K <= 8 terms with a lower factor of >= 2^9
+    # amplitudes run as a direct store stream over 8 x 512 output tiles;
+    # CUTSIM_MERGE_WIDE=0 selects the shared-memory tile form, which sums the
+    # same terms in the same order
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 8, 71 + c, segs, c)
+    ref = sv.simulate(q, gates)
+    monkeypatch.setenv("CUTSIM_MERGE_WIDE", "1")
+    psi, _, _ = gpu_cut(gates, q, segs, "projector", "c64", "fma")
+    assert_parity(psi.cpu().numpy(), ref, "c64", "wide merge")
+    monkeypatch.setenv("CUTSIM_MERGE_WIDE", "0")
+    psi_t, _, _ = gpu_cut(gates, q, segs, "projector", "c64", "fma")
+    assert torch.equal(psi, psi_t)
