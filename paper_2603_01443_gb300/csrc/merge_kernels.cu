@@ -129,9 +129,10 @@ __device__ __forceinline__ void tile_c64(const float2* __restrict__ A, const flo
 // no barrier between tiles.
 constexpr int kWideRows = 8;
 constexpr int kWideCols = 512;
+template <int K>  // 1, 2, 4 or 8: the term loop unrolls and its loads issue together
 __global__ void __launch_bounds__(256)
     merge_wide_c64(const float2* __restrict__ A, const float2* __restrict__ B,
-                   float2* __restrict__ out, int qa, int qb, int K,
+                   float2* __restrict__ out, int qa, int qb,
                    const int32_t* __restrict__ aidx, const int32_t* __restrict__ bidx) {
   const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
   const int64_t tiles_x = NA / kWideCols, n_tiles = tiles_x * (NB / kWideRows);
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(256)
     float2 acc[kWideRows][2];
 #pragma unroll
     for (int r = 0; r < kWideRows; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+#pragma unroll
     for (int k = 0; k < K; ++k) {
       const float4 a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)aidx[k] * NA + x0));
       const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
@@ -369,12 +371,14 @@ cc_status launch_merge_fma(const MergeStage& st, int precision, void* stream) {
     // tile form once per 32), so it is taken while the lower factor's K terms
     // are small: q = 30 K = 4 1.81 -> 1.62 ms, K = 2 1.46 -> 1.26 ms; the
     // last stage of an n = 3 chain with K * NA = 2^22 ran 1.86 -> 1.93 ms
-    if (wide_ok && st.Z == 1 && st.K <= 8 && st.qa >= 9 && st.qb >= 3 &&
-        st.K * NA <= (int64_t(1) << 21)) {
+    if (wide_ok && st.Z == 1 && (st.K == 1 || st.K == 2 || st.K == 4 || st.K == 8) &&
+        st.qa >= 9 && st.qb >= 3 && st.K * NA <= (int64_t(1) << 21)) {
       const int64_t tiles = (NA / kWideCols) * (NB / kWideRows);
-      merge_wide_c64<<<(unsigned)std::min(tiles, cap), 256, 0, s>>>(
-          (const float2*)st.A, (const float2*)st.B, (float2*)st.out, st.qa, st.qb, (int)st.K,
-          st.aidx, st.bidx);
+      auto kern = st.K == 1 ? merge_wide_c64<1> : st.K == 2 ? merge_wide_c64<2>
+                : st.K == 4 ? merge_wide_c64<4> : merge_wide_c64<8>;
+      kern<<<(unsigned)std::min(tiles, cap), 256, 0, s>>>(
+          (const float2*)st.A, (const float2*)st.B, (float2*)st.out, st.qa, st.qb, st.aidx,
+          st.bidx);
     } else if (st.qa >= 7 && st.qb >= 5) {
       const int64_t tiles = (NA >> 7) * (NB >> 5) * st.Z;
       auto kern = st.K > KC ? merge_tile_c64<true> : merge_tile_c64<false>;
