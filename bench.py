@@ -920,8 +920,9 @@ def main(argv=None):
                "kernel": "stage_kernel (uncut passes)", "flops_per_launch": uncut_flops / n_pass,
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": alu_src}
+    # AUTO's rule (the library's kAutoTcMinTerms): 3xTF32 from K = 8 terms on
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        "tf32x3" if (a.prec == "c64" and (1 << cpb[-1]) >= 16) else "fma")
+        "tf32x3" if (a.prec == "c64" and (1 << cpb[-1]) >= 8) else "fma")
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
         # complex FMA merge: 8 flops per term per output amplitude on the ALU

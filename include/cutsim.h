@@ -76,7 +76,7 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  * CC_MERGE_BF16X3  : tcgen05 tensor cores, kind::f16 with bf16 operands, the
  *                    same three-product split, FP32 accumulation (CC_C64,
  *                    factors >= 2^7; max|dpsi|/max|psi| <= 5e-5).
- * CC_MERGE_AUTO    : TF32X3 where it applies and K >= 16, else FMA.
+ * CC_MERGE_AUTO    : TF32X3 where it applies and K >= 8, else FMA.
  * For n_seg >= 3 the form applies to the last (2^q-sized) stage of the chain;
  * the earlier, smaller stages always use FMA. */
 typedef enum {
@@ -265,7 +265,7 @@ cc_status cc_gather_static(const void* psi, int64_t n_amp, int32_t precision, co
  *   - then one merge launch per chain level (one for n_seg = 2, two for
  *     n_seg = 3, ...), each over the output tiles of every circuit's stage at
  *     that level, on CUDA cores (CC_MERGE_FMA arithmetic); a circuit's final
- *     stage with K >= 16 terms and both factors >= 2^7 amplitudes (complex64)
+ *     stage with K >= 8 terms and both factors >= 2^7 amplitudes (complex64)
  *     runs instead as its own 3xTF32 tensor-core merge after its level, as
  *     CC_MERGE_AUTO would run it (CUTSIM_BATCH_TC=0: all on CUDA cores).
  * The whole sequence can be captured once into a CUDA graph and replayed.

@@ -134,7 +134,7 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
         const cc_plan* p = c->plans[i].get();
         if (p->stages.empty()) continue;
         const auto& sg = p->stages.back();
-        if (sg.K >= 16 && sg.qa >= 7 && sg.qb >= 7 && sg.Z == 1)
+        if (sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7 && sg.Z == 1)
           tcb = std::max(tcb, merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_TF32X3));
       }
     b->tc_off = wo * ab;
@@ -232,7 +232,7 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
       const int32_t* tabs = static_cast<const int32_t*>(p->tables_dev);
       J.aidx = tabs + sg.aidx_off;
       J.bidx = tabs + sg.bidx_off;
-      if (last && b->tc_ok && b->precision == CC_C64 && sg.K >= 16 && sg.qa >= 7 && sg.qb >= 7 &&
+      if (last && b->tc_ok && b->precision == CC_C64 && sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7 &&
           sg.Z == 1) {
         J.circ = i;
         c->tc_jobs.push_back({L, i, J});

@@ -216,6 +216,12 @@ int batch_segments_occupancy(int precision, int block, size_t smem);
 // One merge stage of one circuit inside a batched merge launch; operands are
 // offsets (in amplitudes) into one of three caller buffers.
 enum : int32_t { BUF_SEG = 0, BUF_WORK = 1, BUF_PSI = 2 };
+
+// CC_MERGE_AUTO (and batches) merge on the tensor cores (3xTF32) from this
+// many terms on, where both factors have >= 2^7 amplitudes: at q = 30 the
+// CUDA-core form is store-bound through K = 4 and slower from K = 8 on
+// (K = 8: 2.03 ms FMA, 1.64 ms 3xTF32).
+constexpr int64_t kAutoTcMinTerms = 8;
 struct BMergeJob {
   int32_t a_buf, b_buf, out_buf, kind;  // kind: 0 tiled, 1 flat
   int64_t a_off, b_off, out_off;

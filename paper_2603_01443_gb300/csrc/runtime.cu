@@ -318,11 +318,12 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
       acc = out;
       continue;
     }
-    // AUTO: the CUDA-core form while the merge is store-bound (K < 16), else
-    // 3xTF32 (long K summed in groups of 64 terms, see merge_tc.cu).
+    // AUTO: the CUDA-core form while the merge is store-bound (K below
+    // kAutoTcMinTerms), else 3xTF32 (long K summed in groups of 64 terms, see
+    // merge_tc.cu).
     int f = form;
     if (f == CC_MERGE_AUTO)
-      f = (p->precision == CC_C64 && sg.K >= 16 && sg.qa >= 7 && sg.qb >= 7)
+      f = (p->precision == CC_C64 && sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7)
               ? CC_MERGE_TF32X3
               : CC_MERGE_FMA;
     if (f != CC_MERGE_FMA) {

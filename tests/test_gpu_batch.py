@@ -47,7 +47,7 @@ def test_batch_vs_oracle(cuda_lib, prec, decomp, tile_bits, rows):
 @pytest.mark.parametrize("batch_tc,form", [("1", "auto"), ("0", "fma")])
 def test_batch_equals_one_circuit_path_bitwise(cuda_lib, monkeypatch, batch_tc, form):
     # same programs, same tile arithmetic: the batched result is bit-identical
-    # (final stages with K >= 16 on the tensor cores, as AUTO does, by default)
+    # (final stages with K >= 8 on the tensor cores, as AUTO does, by default)
     monkeypatch.setenv("CUTSIM_BATCH_TC", batch_tc)
     items = w.uneven_batch(8, seed=11, q_range=(14, 20), depths=(8, 16), c_range=(1, 5))
     b = make_batch(items)
