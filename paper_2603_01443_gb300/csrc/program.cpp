@@ -289,23 +289,43 @@ inline uint64_t item_mask(const Item& it) {
   return m;
 }
 
+// What the planners read of an item, packed: its qubit mask and, for a dense
+// item, its qubit's bit (0 for diagonal items).
+struct ItemBits {
+  uint64_t mask, dense;
+};
+
+std::vector<ItemBits> item_bits(const std::vector<Item>& items) {
+  std::vector<ItemBits> b(items.size());
+  for (size_t i = 0; i < items.size(); ++i)
+    b[i] = {item_mask(items[i]), items[i].kind == IT_DENSE ? 1ull << items[i].a : 0ull};
+  return b;
+}
+
+// The entries of `order` not yet applied, in order.
+void drop_applied(std::vector<int>& order, const std::vector<char>& applied) {
+  size_t w = 0;
+  for (int i : order)
+    if (!applied[i]) order[w++] = i;
+  order.resize(w);
+}
+
 // Forward scan over the items listed in `order` that are not yet applied: an
 // item is taken when none of its qubits is blocked and it is diagonal or its
 // qubit is in `dense_ok`; otherwise its qubits become blocked, so no later item
 // on them can overtake it.  Returns the number of dense items taken.
-int scan(const std::vector<Item>& items, const std::vector<int>& order,
+int scan(const std::vector<ItemBits>& bits, const std::vector<int>& order,
          const std::vector<char>& applied, uint64_t dense_ok, std::vector<int>* take) {
   uint64_t blocked = 0;
   int dense = 0;
   for (int i : order) {
     if (applied[i]) continue;
-    const Item& it = items[i];
-    const uint64_t m = item_mask(it);
-    if ((m & blocked) || (it.kind == IT_DENSE && !(dense_ok & (1ull << it.a)))) {
-      blocked |= m;
+    const ItemBits b = bits[i];
+    if ((b.mask & blocked) || (b.dense & ~dense_ok)) {
+      blocked |= b.mask;
       continue;
     }
-    if (it.kind == IT_DENSE) ++dense;
+    if (b.dense) ++dense;
     if (take) take->push_back(i);
   }
   return dense;
@@ -315,7 +335,7 @@ int scan(const std::vector<Item>& items, const std::vector<int>& order,
 // on, plus the always-included `fixed` mask: the candidates are the qubits of
 // the earliest pending dense items and every window of `width` consecutive
 // pool entries; the one that admits the most dense items wins.
-uint64_t choose_set(const std::vector<Item>& items, const std::vector<int>& order,
+uint64_t choose_set(const std::vector<ItemBits>& bits, const std::vector<int>& order,
                     const std::vector<char>& applied, const std::vector<int>& pool, int width,
                     uint64_t fixed) {
   if (width >= (int)pool.size()) {
@@ -329,11 +349,11 @@ uint64_t choose_set(const std::vector<Item>& items, const std::vector<int>& orde
     uint64_t seen = 0, in_pool = 0;
     for (int j : pool) in_pool |= 1ull << j;
     for (int i : order) {
-      if (applied[i] || items[i].kind != IT_DENSE) continue;
-      const uint64_t b = 1ull << items[i].a;
+      const uint64_t b = bits[i].dense;
+      if (applied[i] || !b) continue;
       if ((b & in_pool) && !(b & seen)) {
         seen |= b;
-        picked.push_back(items[i].a);
+        picked.push_back(__builtin_ctzll(b));
         if ((int)picked.size() == width) break;
       }
     }
@@ -356,7 +376,7 @@ uint64_t choose_set(const std::vector<Item>& items, const std::vector<int>& orde
   uint64_t best = cands[0];
   int best_d = -1;
   for (uint64_t m : cands) {
-    const int d = scan(items, order, applied, m, nullptr);
+    const int d = scan(bits, order, applied, m, nullptr);
     if (d > best_d) {
       best_d = d;
       best = m;
@@ -686,8 +706,9 @@ struct PassBuilder {
   }
 };
 
-void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector<int>& take,
-              const std::vector<int>& tile_bits, bool first, int rb_max) {
+void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector<ItemBits>& bits,
+              const std::vector<int>& take, const std::vector<int>& tile_bits, bool first,
+              int rb_max) {
   DPass P{};
   P.nq = hp.nq;
   P.k = (int)tile_bits.size();
@@ -717,14 +738,15 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
   PassBuilder pb(hp, hp.nq, tile_bits);
   std::vector<char> done(items.size(), 1);
   for (int i : take) done[i] = 0;
+  std::vector<int> rest(take);  // the pass's items not yet in a stage
   size_t left = take.size();
   do {
-    const uint64_t regs = choose_set(items, take, done, tile_bits, P.rbits, 0);
+    const uint64_t regs = choose_set(bits, rest, done, tile_bits, P.rbits, 0);
     std::vector<int> qubits;
     for (int j : tile_bits)
       if (regs & (1ull << j)) qubits.push_back(j);
     std::vector<int> st_items;
-    scan(items, take, done, regs, &st_items);
+    scan(bits, rest, done, regs, &st_items);
     DStage st{};
     pb.begin_stage(qubits, st);
     for (int i : st_items) {
@@ -736,6 +758,7 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
       hp.nq = -1;
       return;
     }
+    drop_applied(rest, done);
     pb.end_stage(st, left == 0);
     if (pb.overflow) {
       hp.nq = -1;
@@ -754,13 +777,14 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
   HostProgram hp;
   hp.nq = nq;
   hp.n_state = n_state;
+  const std::vector<ItemBits> bits = item_bits(items);
   std::vector<char> applied(items.size(), 0);
-  std::vector<int> order(items.size());
+  std::vector<int> order(items.size());  // the items not yet in a pass, in order
   for (size_t i = 0; i < items.size(); ++i) order[i] = (int)i;
   std::vector<int> all_bits(nq);
   for (int j = 0; j < nq; ++j) all_bits[j] = j;
   if (nq <= kmax) {
-    add_pass(hp, items, order, all_bits, true, rb_max);
+    add_pass(hp, items, bits, order, all_bits, true, rb_max);
     return hp;
   }
   low = std::min(low, kmax);
@@ -770,19 +794,20 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
   size_t left = items.size();
   bool first = true;
   while (left > 0 || first) {
-    const uint64_t tile = choose_set(items, order, applied, pool, kmax - low, fixed);
+    const uint64_t tile = choose_set(bits, order, applied, pool, kmax - low, fixed);
     std::vector<int> tile_bits;
     for (int j = 0; j < nq; ++j)
       if (tile & (1ull << j)) tile_bits.push_back(j);
     std::vector<int> take;
-    scan(items, order, applied, tile, &take);
+    scan(bits, order, applied, tile, &take);
     if (take.empty() && left > 0) {  // cannot happen: the first pending item always fits
       hp.nq = -1;
       return hp;
     }
     for (int i : take) applied[i] = 1;
+    drop_applied(order, applied);
     left -= take.size();
-    add_pass(hp, items, take, tile_bits, first, rb_max);
+    add_pass(hp, items, bits, take, tile_bits, first, rb_max);
     if (hp.nq < 0) return hp;
     first = false;
   }
