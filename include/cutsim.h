@@ -202,6 +202,27 @@ cc_status cc_merge(const cc_plan* plan, const void* seg_buf, uint64_t seg_buf_by
 cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int32_t q, int32_t precision,
                           cc_uncut** out);
 
+/* cc_program_image -- the gate program the uncut simulation of C would run,
+ * as a host-side image for inspection and host tests; host work only (no
+ * device needed).  Gates as for cc_uncut_create; tile_bits = 0 takes the
+ * uncut default, else 2^tile_bits amplitudes per tile (more than the
+ * precision's contiguous low tile bits, 4 for CC_C64 and 3 for CC_C128, and
+ * at most 14 / 13), which forces more passes on small circuits.
+ * words (int64, HOST): version 1, nq, n_state, passes, stages, ops, terms,
+ *   mats, tabs; per pass nq, k, low, init_zero, stage_begin, stage_end,
+ *   rbits, n_rest, zero_tile, zero_rest, 16 tile bits, 48 rest bits; per
+ *   stage op_begin, op_end, 8 register tile bits; per op type, t,
+ *   term_begin, n_sign, n_phase, n_table, mat, sign_adj; per term kind, p0,
+ *   p1, tab.  reals (double, HOST): the 2x2 matrices (4 complex each, the
+ *   rotations' t in the first) then the tables (4 complex each), re/im
+ *   interleaved.  The meaning of each field is that of the device program
+ *   the gate-pass kernels execute.
+ * With words or reals NULL it only stores the sizes in *n_words, *n_reals;
+ * CC_EBUFSIZE when the given capacities are too small. */
+cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int32_t q, int32_t precision,
+                           int32_t tile_bits, int64_t* words, int64_t* n_words, double* reals,
+                           int64_t* n_reals);
+
 /* cc_uncut_info -- number of gate passes over the 2^q vector and of fused ops. */
 cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops, int32_t* tile_bits);
 

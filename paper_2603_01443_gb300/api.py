@@ -8,7 +8,7 @@ handle passed to each call.
 from __future__ import annotations
 
 import ctypes
-from ctypes import byref, c_double, c_int32, c_int64, c_void_p
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
 from typing import Optional, Sequence
 
 import numpy as np
@@ -122,6 +122,23 @@ class CutPlan:
         capi.check(capi.lib().cc_merge(self._h, _ptr(seg_buf), _nbytes(seg_buf), _ptr(psi),
                                        _nbytes(psi), _ptr(workspace), _nbytes(workspace),
                                        capi.MERGE_FORM[form], _stream(stream)), "cc_merge")
+
+
+def program_image(gates: Sequence, q: int, precision: str = "c64", tile_bits: int = 0):
+    """The uncut gate program of a circuit as (int64 words, float64 reals), as
+    cc_program_image lays it out; host work, no device needed."""
+    L = capi.lib()
+    arr = gates if isinstance(gates, capi.GateArray) else capi.GateArray(gates)
+    nw, nr = c_int64(0), c_int64(0)
+    capi.check(L.cc_program_image(arr.data, arr.n, q, capi.PRECISION[precision], tile_bits,
+                                  None, byref(nw), None, byref(nr)), "cc_program_image")
+    words = np.zeros(max(nw.value, 1), dtype=np.int64)
+    reals = np.zeros(max(nr.value, 1), dtype=np.float64)
+    capi.check(L.cc_program_image(arr.data, arr.n, q, capi.PRECISION[precision], tile_bits,
+                                  words.ctypes.data_as(POINTER(c_int64)), byref(nw),
+                                  reals.ctypes.data_as(POINTER(c_double)), byref(nr)),
+               "cc_program_image")
+    return words[:nw.value], reals[:nr.value]
 
 
 class UncutPlan:

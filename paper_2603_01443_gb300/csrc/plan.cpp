@@ -460,6 +460,78 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
   }
 }
 
+extern "C" cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int32_t q,
+                                      int32_t precision, int32_t tile_bits, int64_t* words,
+                                      int64_t* n_words, double* reals, int64_t* n_reals) {
+  try {
+    if (!n_words || !n_reals) return fail(CC_EINVAL, "n_words / n_reals is NULL");
+    if (q < 1 || q > CC_MAX_QUBITS) return fail(CC_ERANGE, "q must be in 1..34");
+    if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+    const int low = low_tile_bits(precision);
+    if (tile_bits == 0) tile_bits = uncut_tile_bits(precision);
+    if (tile_bits <= low || tile_bits > max_tile_bits(precision))
+      return fail(CC_ERANGE, "tile_bits must exceed the contiguous low tile bits and fit shared memory");
+    cc_status st = check_gates(gates, n_gates, q);
+    if (st != CC_OK) return st;
+    std::vector<Item> items;
+    for (int g = 0; g < n_gates; ++g) {
+      st = gate_items(gates[g], 0, items);
+      if (st != CC_OK) return st;
+    }
+    const HostProgram hp = compile_program(items, q, q, tile_bits, low, reg_bits_max(precision));
+    if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
+    std::vector<int64_t> w = {1, hp.nq, hp.n_state, (int64_t)hp.passes.size(),
+                              (int64_t)hp.stages.size(), (int64_t)hp.ops.size(),
+                              (int64_t)hp.terms.size(), (int64_t)hp.mats.size(),
+                              (int64_t)hp.tabs.size()};
+    for (const DPass& P : hp.passes) {
+      const int64_t f[10] = {P.nq, P.k, P.low, P.init_zero, P.stage_begin, P.stage_end,
+                             P.rbits, P.n_rest, (int64_t)P.zero_tile, (int64_t)P.zero_rest};
+      w.insert(w.end(), f, f + 10);
+      for (int t = 0; t < MAX_TILE_BITS; ++t) w.push_back(P.tile_bit[t]);
+      for (int r = 0; r < MAX_REST_BITS; ++r) w.push_back(P.rest_bit[r]);
+    }
+    for (const DStage& S : hp.stages) {
+      w.push_back(S.op_begin);
+      w.push_back(S.op_end);
+      for (int i = 0; i < 8; ++i) w.push_back(S.rb[i]);
+    }
+    for (const DOp& o : hp.ops) {
+      const int64_t f[8] = {o.type, o.t, o.term_begin, o.n_sign, o.n_phase, o.n_table, o.mat,
+                            (int64_t)o.sign_adj};
+      w.insert(w.end(), f, f + 8);
+    }
+    for (const DTerm& t : hp.terms) {
+      w.push_back(t.kind);
+      w.push_back(t.p0);
+      w.push_back(t.p1);
+      w.push_back(t.tab);
+    }
+    const int64_t nr = 2 * (int64_t)(hp.mats.size() + hp.tabs.size());
+    const bool query = !words || !reals;
+    const bool fits = !query && *n_words >= (int64_t)w.size() && *n_reals >= nr;
+    *n_words = (int64_t)w.size();
+    *n_reals = nr;
+    if (query) return CC_OK;
+    if (!fits) return fail(CC_EBUFSIZE, "words or reals too small for the program image");
+    std::memcpy(words, w.data(), w.size() * sizeof(int64_t));
+    int64_t k = 0;
+    for (const cd& z : hp.mats) {
+      reals[k++] = z.real();
+      reals[k++] = z.imag();
+    }
+    for (const cd& z : hp.tabs) {
+      reals[k++] = z.real();
+      reals[k++] = z.imag();
+    }
+    return CC_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(CC_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CC_EINVAL, "internal error in cc_program_image");
+  }
+}
+
 extern "C" cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops,
                                    int32_t* tile_bits) {
   if (!u) return fail(CC_EINVAL, "NULL argument");

@@ -26,3 +26,15 @@ def cuda_lib():
     from paper_2603_01443_gb300 import capi
 
     return capi.lib()
+
+
+@pytest.fixture(scope="session")
+def host_lib():
+    """The loaded C-ABI library for host-only calls (built here if missing)."""
+    from paper_2603_01443_gb300 import capi
+
+    if not os.path.exists(capi.LIB_PATH):
+        from paper_2603_01443_gb300 import build
+
+        build.build()
+    return capi.lib()

@@ -1,0 +1,92 @@
+"""The host program compiler pinned on the CPU: the gate program the pass
+kernels would execute (cc_program_image), run by a plain numpy interpreter of
+the device program's definition (tests/program_interp.py), equals the FP64
+oracle's state vector.  Small tiles force many passes and stages and narrow
+register widths; both rotation-engine settings and both precisions' layouts
+are covered.  No GPU is used."""
+
+import numpy as np
+import pytest
+
+import workload as w
+from oracle import statevector as sv
+from paper_2603_01443_gb300 import api, capi
+from program_interp import parse, run
+
+ALL_KINDS = ["U3", "H", "X", "Z", "S", "SDG", "T", "TDG", "CZ", "CX", "SWAP", "ISWAP", "CAN"]
+
+
+def interp(gates, q, prec, tile_bits):
+    words, reals = api.program_image(gates, q, prec, tile_bits)
+    return parse(words, reals)
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
+@pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c64", 7), ("c64", 14), ("c128", 4),
+                                            ("c128", 6), ("c128", 13)])
+@pytest.mark.parametrize("q,n_gates,seed", [(6, 120, 1), (9, 200, 2), (10, 160, 3)])
+def test_program_matches_oracle(host_lib, monkeypatch, rot, prec, tile_bits, q, n_gates,
+                                seed):
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    gates = w.random_circuit(q, n_gates, seed, kinds=ALL_KINDS)
+    prog = interp(gates, q, prec, tile_bits)
+    if tile_bits < q:
+        assert len(prog.passes) > 1
+    got = run(prog)
+    ref = sv.simulate(q, gates)
+    assert rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
+def test_brickwork_program_and_rotation_ops(host_lib, monkeypatch, rot):
+    # a brickwork's fused one-qubit matrices become tangent-form rotations
+    # (OP_ROT / OP_ROTC) with the engine on and complex 2x2 ops with it off
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    q = 11
+    gates = w.brickwork(q, 12, 5)
+    prog = interp(gates, q, "c64", 6)
+    types = {op[0] for op in prog.ops}
+    if rot == "1":
+        assert types <= {1, 2, 3} and types & {2, 3}
+        assert any(op[4] for op in prog.ops)  # phase blocks
+    else:
+        assert types <= {0, 1}
+    assert rel(run(prog), sv.simulate(q, gates)) <= 1e-12
+
+
+def test_deep_single_pass_program(host_lib):
+    # one tile holds every qubit: one pass of thousands of rotations, whose
+    # deferred scalar factors are folded in before the amplitudes grow large
+    q = 8
+    gates = w.brickwork(q, 400, 6)
+    prog = interp(gates, q, "c64", 0)
+    assert len(prog.passes) == 1
+    got = run(prog)
+    assert np.all(np.isfinite(got))
+    assert rel(got, sv.simulate(q, gates)) <= 1e-11
+
+
+def test_program_image_arguments(host_lib):
+    gates = w.brickwork(6, 2, 0)
+    arr = capi.GateArray(gates)
+    L = capi.lib()
+    from ctypes import byref, c_int64
+    nw, nr = c_int64(0), c_int64(0)
+    assert L.cc_program_image(arr.data, arr.n, 6, capi.PRECISION["c64"], 0, None, byref(nw),
+                              None, byref(nr)) == 0
+    assert nw.value > 9 and nr.value > 0
+    small = np.zeros(4, dtype=np.int64)
+    reals = np.zeros(nr.value)
+    from ctypes import POINTER, c_double
+    st = L.cc_program_image(arr.data, arr.n, 6, capi.PRECISION["c64"], 0,
+                            small.ctypes.data_as(POINTER(c_int64)), byref(c_int64(4)),
+                            reals.ctypes.data_as(POINTER(c_double)), byref(nr))
+    assert capi.STATUS[st] == "CC_EBUFSIZE"
+    with pytest.raises(capi.CutsimError):
+        api.program_image(gates, 6, "c64", 4)  # not above the 4 contiguous low bits
+    with pytest.raises(capi.CutsimError):
+        api.program_image(gates, 6, "c128", 14)  # complex128 tiles hold at most 2^13
