@@ -223,6 +223,23 @@ cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int32_t q, int
                            int32_t tile_bits, int64_t* words, int64_t* n_words, double* reals,
                            int64_t* n_reals);
 
+/* cc_plan_program_image -- segment `seg`'s gate program of the plan
+ * cc_plan_create would build for the same arguments (Algorithm 1's
+ * subcircuit generation: one program over the 2^(q_seg + c_seg) amplitudes of
+ * all its variants), as a host-side image for inspection and host tests;
+ * host work only (no device needed).  tile_bits = 0 takes the segment
+ * default, else the limits of cc_program_image.  words and reals as for
+ * cc_program_image, followed in words by the plan's number of global cut
+ * bits B, the segment's number of variant bits c_seg, and the global bit of
+ * each of its variant bits in order (variant bit t of the segment is global
+ * bit ids[t]; Algorithm 3 sums over all 2^B global combinations m, taking
+ * from segment i the variant whose bit t is bit ids[t] of m). */
+cc_status cc_plan_program_image(const cc_gate* gates, int32_t n_gates, int32_t q,
+                                const int32_t* seg_sizes, int32_t n_seg, int32_t decomp,
+                                int32_t precision, int32_t tile_bits, int32_t seg,
+                                int64_t* words, int64_t* n_words, double* reals,
+                                int64_t* n_reals);
+
 /* cc_uncut_info -- number of gate passes over the 2^q vector and of fused ops. */
 cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops, int32_t* tile_bits);
 

@@ -141,6 +141,27 @@ def program_image(gates: Sequence, q: int, precision: str = "c64", tile_bits: in
     return words[:nw.value], reals[:nr.value]
 
 
+def plan_program_image(gates: Sequence, q: int, seg_sizes: Sequence[int], seg: int,
+                       decomp: str = "projector", precision: str = "c64", tile_bits: int = 0):
+    """Segment `seg`'s gate program of the plan for these arguments, as
+    (int64 words, float64 reals) laid out by cc_plan_program_image; host work,
+    no device needed."""
+    L = capi.lib()
+    arr = gates if isinstance(gates, capi.GateArray) else capi.GateArray(gates)
+    sizes = (c_int32 * len(seg_sizes))(*seg_sizes)
+    args = (arr.data, arr.n, q, sizes, len(seg_sizes), capi.DECOMP[decomp],
+            capi.PRECISION[precision], tile_bits, seg)
+    nw, nr = c_int64(0), c_int64(0)
+    capi.check(L.cc_plan_program_image(*args, None, byref(nw), None, byref(nr)),
+               "cc_plan_program_image")
+    words = np.zeros(max(nw.value, 1), dtype=np.int64)
+    reals = np.zeros(max(nr.value, 1), dtype=np.float64)
+    capi.check(L.cc_plan_program_image(*args, words.ctypes.data_as(POINTER(c_int64)), byref(nw),
+                                       reals.ctypes.data_as(POINTER(c_double)), byref(nr)),
+               "cc_plan_program_image")
+    return words[:nw.value], reals[:nr.value]
+
+
 class UncutPlan:
     """Pass plan of the uncut simulation (T_orig)."""
 

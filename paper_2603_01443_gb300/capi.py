@@ -83,6 +83,10 @@ _SIGNATURES = {
     "cc_program_image": (c_int32, [POINTER(CGate), c_int32, c_int32, c_int32, c_int32,
                                    POINTER(c_int64), POINTER(c_int64), POINTER(c_double),
                                    POINTER(c_int64)]),
+    "cc_plan_program_image": (c_int32, [POINTER(CGate), c_int32, c_int32, POINTER(c_int32),
+                                        c_int32, c_int32, c_int32, c_int32, c_int32,
+                                        POINTER(c_int64), POINTER(c_int64), POINTER(c_double),
+                                        POINTER(c_int64)]),
     "cc_simulate_uncut": (c_int32, [c_void_p, c_void_p, c_uint64, c_void_p]),
     "cc_uncut_destroy": (None, [c_void_p]),
     "cc_compare": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, POINTER(c_double), c_void_p]),

@@ -99,7 +99,8 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
 }
 
 cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* seg_sizes,
-                          int n_seg, int decomp, int precision, int seg_kmax, cc_plan** out) {
+                          int n_seg, int decomp, int precision, int seg_kmax, cc_plan** out,
+                          bool host_only) {
   try {
     if (!out) return fail(CC_EINVAL, "out is NULL");
     *out = nullptr;
@@ -298,6 +299,10 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     // All device tables of the plan (gate programs, merge index tables) go up
     // in one allocation and one copy.  Everything above is host work; the
     // device is needed from here on.
+    if (host_only) {
+      *out = p.release();
+      return CC_OK;
+    }
     st = check_device();
     if (st != CC_OK) return st;
     std::vector<unsigned char> img;
@@ -460,6 +465,65 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
   }
 }
 
+namespace {
+
+// A host program as int64 words and doubles (the layout cc_program_image
+// documents).
+void serialize_program(const cc::HostProgram& hp, std::vector<int64_t>& w, std::vector<double>& r) {
+  using namespace cc;
+  w = {1, hp.nq, hp.n_state, (int64_t)hp.passes.size(), (int64_t)hp.stages.size(),
+       (int64_t)hp.ops.size(), (int64_t)hp.terms.size(), (int64_t)hp.mats.size(),
+       (int64_t)hp.tabs.size()};
+  for (const DPass& P : hp.passes) {
+    const int64_t f[10] = {P.nq, P.k, P.low, P.init_zero, P.stage_begin, P.stage_end,
+                           P.rbits, P.n_rest, (int64_t)P.zero_tile, (int64_t)P.zero_rest};
+    w.insert(w.end(), f, f + 10);
+    for (int t = 0; t < MAX_TILE_BITS; ++t) w.push_back(P.tile_bit[t]);
+    for (int q = 0; q < MAX_REST_BITS; ++q) w.push_back(P.rest_bit[q]);
+  }
+  for (const DStage& S : hp.stages) {
+    w.push_back(S.op_begin);
+    w.push_back(S.op_end);
+    for (int i = 0; i < 8; ++i) w.push_back(S.rb[i]);
+  }
+  for (const DOp& o : hp.ops) {
+    const int64_t f[8] = {o.type, o.t, o.term_begin, o.n_sign, o.n_phase, o.n_table, o.mat,
+                          (int64_t)o.sign_adj};
+    w.insert(w.end(), f, f + 8);
+  }
+  for (const DTerm& t : hp.terms) {
+    w.push_back(t.kind);
+    w.push_back(t.p0);
+    w.push_back(t.p1);
+    w.push_back(t.tab);
+  }
+  r.clear();
+  for (const cd& z : hp.mats) {
+    r.push_back(z.real());
+    r.push_back(z.imag());
+  }
+  for (const cd& z : hp.tabs) {
+    r.push_back(z.real());
+    r.push_back(z.imag());
+  }
+}
+
+// Copy an image out (or only report its sizes when words or reals is NULL).
+cc_status export_image(const std::vector<int64_t>& w, const std::vector<double>& r, int64_t* words,
+                       int64_t* n_words, double* reals, int64_t* n_reals) {
+  const bool query = !words || !reals;
+  const bool fits = !query && *n_words >= (int64_t)w.size() && *n_reals >= (int64_t)r.size();
+  *n_words = (int64_t)w.size();
+  *n_reals = (int64_t)r.size();
+  if (query) return CC_OK;
+  if (!fits) return cc::fail(CC_EBUFSIZE, "words or reals too small for the program image");
+  std::memcpy(words, w.data(), w.size() * sizeof(int64_t));
+  std::memcpy(reals, r.data(), r.size() * sizeof(double));
+  return CC_OK;
+}
+
+}  // namespace
+
 extern "C" cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int32_t q,
                                       int32_t precision, int32_t tile_bits, int64_t* words,
                                       int64_t* n_words, double* reals, int64_t* n_reals) {
@@ -480,55 +544,45 @@ extern "C" cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int
     }
     const HostProgram hp = compile_program(items, q, q, tile_bits, low, reg_bits_max(precision));
     if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
-    std::vector<int64_t> w = {1, hp.nq, hp.n_state, (int64_t)hp.passes.size(),
-                              (int64_t)hp.stages.size(), (int64_t)hp.ops.size(),
-                              (int64_t)hp.terms.size(), (int64_t)hp.mats.size(),
-                              (int64_t)hp.tabs.size()};
-    for (const DPass& P : hp.passes) {
-      const int64_t f[10] = {P.nq, P.k, P.low, P.init_zero, P.stage_begin, P.stage_end,
-                             P.rbits, P.n_rest, (int64_t)P.zero_tile, (int64_t)P.zero_rest};
-      w.insert(w.end(), f, f + 10);
-      for (int t = 0; t < MAX_TILE_BITS; ++t) w.push_back(P.tile_bit[t]);
-      for (int r = 0; r < MAX_REST_BITS; ++r) w.push_back(P.rest_bit[r]);
-    }
-    for (const DStage& S : hp.stages) {
-      w.push_back(S.op_begin);
-      w.push_back(S.op_end);
-      for (int i = 0; i < 8; ++i) w.push_back(S.rb[i]);
-    }
-    for (const DOp& o : hp.ops) {
-      const int64_t f[8] = {o.type, o.t, o.term_begin, o.n_sign, o.n_phase, o.n_table, o.mat,
-                            (int64_t)o.sign_adj};
-      w.insert(w.end(), f, f + 8);
-    }
-    for (const DTerm& t : hp.terms) {
-      w.push_back(t.kind);
-      w.push_back(t.p0);
-      w.push_back(t.p1);
-      w.push_back(t.tab);
-    }
-    const int64_t nr = 2 * (int64_t)(hp.mats.size() + hp.tabs.size());
-    const bool query = !words || !reals;
-    const bool fits = !query && *n_words >= (int64_t)w.size() && *n_reals >= nr;
-    *n_words = (int64_t)w.size();
-    *n_reals = nr;
-    if (query) return CC_OK;
-    if (!fits) return fail(CC_EBUFSIZE, "words or reals too small for the program image");
-    std::memcpy(words, w.data(), w.size() * sizeof(int64_t));
-    int64_t k = 0;
-    for (const cd& z : hp.mats) {
-      reals[k++] = z.real();
-      reals[k++] = z.imag();
-    }
-    for (const cd& z : hp.tabs) {
-      reals[k++] = z.real();
-      reals[k++] = z.imag();
-    }
-    return CC_OK;
+    std::vector<int64_t> w;
+    std::vector<double> r;
+    serialize_program(hp, w, r);
+    return export_image(w, r, words, n_words, reals, n_reals);
   } catch (const std::bad_alloc&) {
     return fail(CC_ENOMEM, "host allocation failed");
   } catch (...) {
     return fail(CC_EINVAL, "internal error in cc_program_image");
+  }
+}
+
+extern "C" cc_status cc_plan_program_image(const cc_gate* gates, int32_t n_gates, int32_t q,
+                                           const int32_t* seg_sizes, int32_t n_seg,
+                                           int32_t decomp, int32_t precision, int32_t tile_bits,
+                                           int32_t seg, int64_t* words, int64_t* n_words,
+                                           double* reals, int64_t* n_reals) {
+  try {
+    if (!n_words || !n_reals) return fail(CC_EINVAL, "n_words / n_reals is NULL");
+    if (precision != CC_C64 && precision != CC_C128) return fail(CC_EINVAL, "unknown precision");
+    if (tile_bits == 0) tile_bits = seg_tile_bits(precision);
+    if (tile_bits <= low_tile_bits(precision) || tile_bits > max_tile_bits(precision))
+      return fail(CC_ERANGE, "tile_bits must exceed the contiguous low tile bits and fit shared memory");
+    cc_plan* raw = nullptr;
+    const cc_status st = create_plan(gates, n_gates, q, seg_sizes, n_seg, decomp, precision,
+                                     tile_bits, &raw, true);
+    if (st != CC_OK) return st;
+    std::unique_ptr<cc_plan> p(raw);
+    if (seg < 0 || seg >= p->n_seg) return fail(CC_ERANGE, "segment index out of range");
+    std::vector<int64_t> w;
+    std::vector<double> r;
+    serialize_program(p->hprog[seg], w, r);
+    w.push_back((int64_t)p->bits.size());
+    w.push_back((int64_t)p->seg_cut_ids[seg].size());
+    for (int b : p->seg_cut_ids[seg]) w.push_back(b);
+    return export_image(w, r, words, n_words, reals, n_reals);
+  } catch (const std::bad_alloc&) {
+    return fail(CC_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(CC_EINVAL, "internal error in cc_plan_program_image");
   }
 }
 

@@ -18,9 +18,11 @@ bool seg_launch_per_pass();  // CUTSIM_SEG_LAUNCH=passes: one launch per segment
 struct cc_plan;
 namespace cc {
 // cc_plan_create with an explicit largest segment tile (bits, in
-// low_tile_bits + 1 .. max_tile_bits).
+// low_tile_bits + 1 .. max_tile_bits).  host_only: stop after the host work
+// (the segment programs and cut bits; no device tables, no device needed).
 cc_status create_plan(const cc_gate* gates, int n_gates, int q, const int* seg_sizes, int n_seg,
-                      int decomp, int precision, int seg_kmax, cc_plan** out);
+                      int decomp, int precision, int seg_kmax, cc_plan** out,
+                      bool host_only = false);
 }  // namespace cc
 
 struct cc_plan {

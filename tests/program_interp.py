@@ -49,7 +49,9 @@ class Program:
     tabs: np.ndarray     # complex, 4 per table
 
 
-def parse(words: np.ndarray, reals: np.ndarray) -> Program:
+def parse(words: np.ndarray, reals: np.ndarray, trailing: bool = False):
+    """The program of an image; with trailing=True also the words after it
+    (a segment image's cut bits)."""
     w = [int(x) for x in words]
     assert w[0] == 1, "image version"
     nq, n_state, n_pass, n_stage, n_op, n_term, n_mat, n_tab = w[1:9]
@@ -74,9 +76,10 @@ def parse(words: np.ndarray, reals: np.ndarray) -> Program:
     for _ in range(n_term):
         terms.append(tuple(w[i:i + 4]))
         i += 4
-    assert i == len(w)
+    assert trailing or i == len(w)
     z = reals[0::2] + 1j * reals[1::2]
-    return Program(nq, n_state, passes, stages, ops, terms, z[:n_mat], z[n_mat:n_mat + n_tab])
+    prog = Program(nq, n_state, passes, stages, ops, terms, z[:n_mat], z[n_mat:n_mat + n_tab])
+    return (prog, w[i:]) if trailing else prog
 
 
 def _bit(v: np.ndarray, p: int) -> np.ndarray:
