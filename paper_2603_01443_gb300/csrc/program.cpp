@@ -447,7 +447,7 @@ struct PassBuilder {
       add_sign(vpos[j], vpos[j]);
       return;
     }
-    if (rot && std::abs(d0) > 1e-150 && std::isfinite(std::abs(d1 / d0))) {
+    if (rot && std::norm(d0) > 1e-300) {  // ph1 / ph0 exists (the entries are finite)
       const int p = vpos[j];
       if ((ph_mask >> p) & 1ull) {
         ph0[p] *= d0;
@@ -746,6 +746,7 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
     for (int j : tile_bits)
       if (regs & (1ull << j)) qubits.push_back(j);
     std::vector<int> st_items;
+    st_items.reserve(rest.size());
     scan(bits, rest, done, regs, &st_items);
     DStage st{};
     pb.begin_stage(qubits, st);
@@ -799,6 +800,7 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
     for (int j = 0; j < nq; ++j)
       if (tile & (1ull << j)) tile_bits.push_back(j);
     std::vector<int> take;
+    take.reserve(order.size());
     scan(bits, order, applied, tile, &take);
     if (take.empty() && left > 0) {  // cannot happen: the first pending item always fits
       hp.nq = -1;
