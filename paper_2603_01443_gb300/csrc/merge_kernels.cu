@@ -10,9 +10,11 @@
 // of the output, stages chunks of the factors' rows in shared memory and keeps
 // an 8 x 2 (8 x 1) register block of accumulators per thread; stores are
 // 16-byte streaming stores, each warp writing 512 contiguous bytes per row.
-// The flat form (one output per thread) covers factors too short for a tile.
-// Both take per-term row tables so that one kernel also serves the batched
-// stages of the chained merge for three or more segments.
+// The wide form (complex64, K <= 8, a small lower factor) drops the staging:
+// 8 x 512 tiles read straight from L2 and written with no barrier.  The flat
+// form (one output per thread) covers factors too short for a tile.  The
+// tiled and flat forms take per-term row tables so that one kernel also
+// serves the batched stages of the chained merge for three or more segments.
 //
 // Accumulation (complex64): terms are summed in FP32 chunks of KC; when there
 // is more than one chunk, each chunk total is added to a running (hi, lo)

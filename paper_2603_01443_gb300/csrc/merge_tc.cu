@@ -21,6 +21,12 @@
 //               blocks, staged through shared memory and written by bulk
 //               tensor stores (TMA), then release of the accumulator, so the
 //               store of tile i overlaps the MMAs of tile i+1.
+// Forms: merge_tc_kernel (the structure above); merge_tc_pair_kernel, the
+// default, where two CTAs of a cluster share each column tile by TMA
+// multicast and stream K in 128-, 64- or 32-byte blocks (2, 4 or 8 stages);
+// merge_tc_rs_kernel (row operand resident in shared memory) and
+// merge_tc_2sm_kernel (one cta_group::2 MMA of M = 256 per pair), both
+// opt-in and slower on GB300.
 // Every mbarrier wait is bounded: on expiry the kernel raises a device error
 // flag (reported as CC_ETIMEOUT by cc_sync), waits a bounded time for its own
 // copies and MMAs in flight, frees its TMEM and returns.
