@@ -90,3 +90,30 @@ def test_program_image_arguments(host_lib):
         api.program_image(gates, 6, "c64", 4)  # not above the 4 contiguous low bits
     with pytest.raises(capi.CutsimError):
         api.program_image(gates, 6, "c128", 14)  # complex128 tiles hold at most 2^13
+
+
+@pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c128", 4), ("c128", 13)])
+def test_phase_block_skip_flags(host_lib, prec, tile_bits):
+    # the complex128 kernel skips the products a phase block's flags mark as
+    # 1 (bit 0: lo[0], bit 1: lo[1..3], bit 2: hi[1..7]); every product so
+    # marked must be exactly 1
+    q = 10
+    gates = w.random_circuit(q, 200, 9, kinds=ALL_KINDS)
+    prog = interp(gates, q, prec, tile_bits)
+    blocks = 0
+    for op in prog.ops:
+        n_sign, n_phase = op[3], op[4]
+        if not n_phase:
+            continue
+        kind, flags, _, tab = prog.terms[op[2] + n_sign]
+        assert kind == 2  # TERM_PBLOCK
+        blk = prog.tabs[4 * tab:4 * tab + 12]
+        blocks += 1
+        if not flags & 1:
+            assert blk[0] == 1
+        if not flags & 2:
+            assert np.all(blk[1:4] == 1)
+        if not flags & 4:
+            assert np.all(blk[5:12] == 1)
+        assert blk[4] == 1  # hi[0], the empty product
+    assert blocks > 0
