@@ -233,7 +233,12 @@ cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int32_t q, int
  * bits B, the segment's number of variant bits c_seg, and the global bit of
  * each of its variant bits in order (variant bit t of the segment is global
  * bit ids[t]; Algorithm 3 sums over all 2^B global combinations m, taking
- * from segment i the variant whose bit t is bit ids[t] of m). */
+ * from segment i the variant whose bit t is bit ids[t] of m), then the merge
+ * stages the plan runs: their number and per stage seg, qa, qb, K, Z,
+ * aidx_off, bidx_off (stage s: U_s[z][x_s 2^qa + x] = sum_{k < K}
+ * U_{s-1}[tab[aidx_off + z K + k]][x] * seg_s[tab[bidx_off + z K + k]][x_s],
+ * with U_0 the variants of segment 0), then the length of the index table
+ * and its entries. */
 cc_status cc_plan_program_image(const cc_gate* gates, int32_t n_gates, int32_t q,
                                 const int32_t* seg_sizes, int32_t n_seg, int32_t decomp,
                                 int32_t precision, int32_t tile_bits, int32_t seg,

@@ -300,6 +300,7 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     // in one allocation and one copy.  Everything above is host work; the
     // device is needed from here on.
     if (host_only) {
+      p->host_tables = std::move(tab);
       *out = p.release();
       return CC_OK;
     }
@@ -578,6 +579,14 @@ extern "C" cc_status cc_plan_program_image(const cc_gate* gates, int32_t n_gates
     w.push_back((int64_t)p->bits.size());
     w.push_back((int64_t)p->seg_cut_ids[seg].size());
     for (int b : p->seg_cut_ids[seg]) w.push_back(b);
+    // the merge stages and their index tables
+    w.push_back((int64_t)p->stages.size());
+    for (const auto& sg : p->stages) {
+      const int64_t f[7] = {sg.seg, sg.qa, sg.qb, sg.K, sg.Z, sg.aidx_off, sg.bidx_off};
+      w.insert(w.end(), f, f + 7);
+    }
+    w.push_back((int64_t)p->host_tables.size());
+    for (int32_t v : p->host_tables) w.push_back(v);
     return export_image(w, r, words, n_words, reals, n_reals);
   } catch (const std::bad_alloc&) {
     return fail(CC_ENOMEM, "host allocation failed");

@@ -51,6 +51,7 @@ struct cc_plan {
   std::vector<Stage> stages;
   void* arena = nullptr;       // the one device allocation holding every table below
   void* tables_dev = nullptr;  // merge index tables (inside arena)
+  std::vector<int32_t> host_tables;  // the same tables, kept by host-only plans
   int64_t n_sub = 0;
   uint64_t seg_buf_bytes = 0, psi_bytes = 0, workspace_bytes = 0, table_bytes = 0;
   uint64_t chain_ws_amps = 0;  // amplitudes of one chained-merge intermediate buffer

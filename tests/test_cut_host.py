@@ -5,7 +5,8 @@ with each segment's variant taken by its cut bits (Algorithm 3 written out),
 equals the FP64 oracle's uncut state.  This covers the cut items and their
 coefficients for both rank-2 splits, CX cuts, rank-4 (SWAP/ISWAP/CAN) cuts by
 Pauli products, chains of three segments, small tiles and both rotation
-engine settings.  No GPU is used."""
+engine settings.  The plan's merge stages and index tables, applied as the
+chained merge the merge kernels run, give the same state.  No GPU is used."""
 
 import numpy as np
 import pytest
@@ -16,13 +17,52 @@ from paper_2603_01443_gb300 import api
 from program_interp import parse, run
 
 
+def parse_stages(tail, c_i):
+    """The merge stages (seg, qa, qb, K, Z, aidx_off, bidx_off) and the index
+    table that follow a segment's cut ids in its image."""
+    i = 2 + c_i
+    n_st = int(tail[i])
+    stages = [tuple(int(v) for v in tail[i + 1 + 7 * j:i + 8 + 7 * j]) for j in range(n_st)]
+    i += 1 + 7 * n_st
+    n_tab = int(tail[i])
+    tab = np.asarray(tail[i + 1:i + 1 + n_tab], dtype=np.int64)
+    assert len(tab) == n_tab and i + 1 + n_tab == len(tail)
+    return stages, tab
+
+
+def chained_merge(vecs, stages, tab):
+    """Algorithm 3 as the plan stages it: stage s absorbs segment s into the
+    product of the segments before it, U_s[z][x_s 2^qa + x] = sum_k
+    U_{s-1}[aidx(z, k)][x] seg_s[bidx(z, k)][x_s], U_0 the variants of
+    segment 0; the result is U_{n-1}[0]."""
+    u = vecs[0]
+    for seg, qa, qb, K, Z, ao, bo in stages:
+        assert u.shape[1] == 1 << qa and vecs[seg].shape[1] == 1 << qb
+        nxt = np.zeros((Z, 1 << (qa + qb)), dtype=complex)
+        for z in range(Z):
+            for k in range(K):
+                a = u[tab[ao + z * K + k]]
+                b = vecs[seg][tab[bo + z * K + k]]
+                nxt[z] += np.kron(b, a)
+        u = nxt
+    assert u.shape[0] == 1
+    return u[0]
+
+
 def cut_state(gates, q, segs, decomp, prec, tile_bits):
-    vecs, ids, n_bits = [], [], None
+    """The exhaustive sum over all global cut combinations, checked against
+    the plan's chained merge of the same segment states."""
+    vecs, ids, n_bits, staged = [], [], None, None
     for i, qi in enumerate(segs):
         words, reals = api.plan_program_image(gates, q, segs, i, decomp, prec, tile_bits)
         prog, tail = parse(words, reals, trailing=True)
         n_bits, c_i = tail[0], tail[1]
         ids.append(tail[2:2 + c_i])
+        st = parse_stages(tail, c_i)
+        if staged is None:
+            staged = st
+        else:  # every segment's image carries the same plan-wide stages
+            assert st[0] == staged[0] and np.array_equal(st[1], staged[1])
         assert prog.nq == qi + c_i and prog.n_state == qi
         vecs.append(run(prog).reshape(1 << c_i, 1 << qi))  # variant r at rows, x_i at columns
     assert n_bits <= 10, "too many cut bits for the exhaustive term sum"
@@ -33,6 +73,9 @@ def cut_state(gates, q, segs, decomp, prec, tile_bits):
             r = sum(((m >> b) & 1) << t for t, b in enumerate(ids[i]))
             phi = vecs[i][r] if phi is None else np.kron(vecs[i][r], phi)
         psi = psi + phi
+    if len(segs) >= 2:
+        chain = chained_merge(vecs, *staged)
+        assert rel(chain, psi) <= 1e-13
     return psi
 
 
@@ -80,3 +123,36 @@ def test_random_circuit_two_segments(host_lib, monkeypatch, rot, n_gates, seed):
                              kinds=["U3", "H", "T", "S", "CZ", "CX", "SWAP", "CAN"])
     got = cut_state(gates, q, segs, "projector", "c64", 5)
     assert rel(got, sv.simulate(q, gates)) <= 1e-12
+
+
+@pytest.mark.parametrize("segs", [[3, 3, 3], [2, 3, 2, 2], [4, 5]])
+def test_merge_stage_shapes(host_lib, segs):
+    # stage s absorbs segment s: qa is the width of the segments before it,
+    # K counts the combinations of the cut bits on boundary (s-1, s), Z those
+    # on (s, s+1); the next stage sums over this stage's Z, the last has
+    # Z = 1, every index stays inside the rows it indexes, and the two
+    # boundaries' bits together are all the plan's bits
+    q = sum(segs)
+    gates = w.staircase(q, 2)
+    tails = []
+    for i in range(len(segs)):
+        words, reals = api.plan_program_image(gates, q, segs, i, "projector", "c64", 0)
+        tails.append(parse(words, reals, trailing=True)[1])
+    n_bits = int(tails[0][0])
+    c = [int(tl[1]) for tl in tails]
+    stages, tab = parse_stages(tails[0], c[0])
+    assert [st[0] for st in stages] == list(range(1, len(segs)))
+    log_k = 0
+    rows = 1 << c[0]
+    for j, (seg, qa, qb, K, Z, ao, bo) in enumerate(stages):
+        assert qa == sum(segs[:seg]) and qb == segs[seg]
+        assert K == (stages[j - 1][4] if j else K) and K >= 2
+        assert (Z == 1) == (j == len(stages) - 1)
+        a = tab[ao:ao + Z * K]
+        b = tab[bo:bo + Z * K]
+        assert a.min() >= 0 and a.max() < rows
+        assert b.min() >= 0 and b.max() < (1 << c[seg])
+        assert len(set(zip(a.tolist(), b.tolist()))) == Z * K  # no term twice
+        log_k += K.bit_length() - 1
+        rows = Z
+    assert log_k == n_bits
