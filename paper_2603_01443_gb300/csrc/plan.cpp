@@ -135,6 +135,12 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     // adds one or two global bits; seg_cut_ids[i] lists segment i's bits in
     // order, and bit t of its variant number is its t-th entry.
     std::vector<std::vector<Item>> items(n_seg);
+    {
+      // most gates give one item: size each segment's list once
+      std::vector<size_t> n_in(n_seg, 8);
+      for (int g = 0; g < n_gates; ++g) ++n_in[seg_of_qubit(p.get(), gates[g].q0)];
+      for (int i = 0; i < n_seg; ++i) items[i].reserve(n_in[i]);
+    }
     p->seg_cut_ids.assign(n_seg, {});
     for (int g = 0; g < n_gates; ++g) {
       const cc_gate& gt = gates[g];
@@ -446,6 +452,7 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
     u->q = q;
     u->precision = precision;
     std::vector<Item> items;
+    items.reserve((size_t)n_gates);
     for (int g = 0; g < n_gates; ++g) {
       st = gate_items(gates[g], 0, items);
       if (st != CC_OK) return st;
@@ -539,6 +546,7 @@ extern "C" cc_status cc_program_image(const cc_gate* gates, int32_t n_gates, int
     cc_status st = check_gates(gates, n_gates, q);
     if (st != CC_OK) return st;
     std::vector<Item> items;
+    items.reserve((size_t)n_gates);
     for (int g = 0; g < n_gates; ++g) {
       st = gate_items(gates[g], 0, items);
       if (st != CC_OK) return st;
