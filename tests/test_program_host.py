@@ -42,6 +42,23 @@ def test_program_matches_oracle(host_lib, monkeypatch, rot, prec, tile_bits, q, 
 
 
 @pytest.mark.parametrize("rot", ["1", "0"])
+@pytest.mark.parametrize("prec,reg_bits,tile_bits", [("c64", 2, 7), ("c64", 3, 9), ("c64", 4, 13),
+                                                     ("c128", 2, 6), ("c128", 3, 10)])
+def test_fewer_register_bits(host_lib, monkeypatch, rot, prec, reg_bits, tile_bits):
+    # CUTSIM_REG_BITS narrows every stage's register set (the kernels'
+    # thread count per tile grows to match): more stages, each over fewer
+    # bits, and phase blocks over fewer factors; the program still computes
+    # the circuit
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    monkeypatch.setenv("CUTSIM_REG_BITS", str(reg_bits))
+    q = 10
+    gates = w.random_circuit(q, 180, 5, kinds=ALL_KINDS)
+    prog = interp(gates, q, prec, tile_bits)
+    assert all(P.rbits <= reg_bits for P in prog.passes)
+    assert rel(run(prog), sv.simulate(q, gates)) <= 1e-12
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
 def test_brickwork_program_and_rotation_ops(host_lib, monkeypatch, rot):
     # a brickwork's fused one-qubit matrices become tangent-form rotations
     # (OP_ROT / OP_ROTC) with the engine on and complex 2x2 ops with it off
