@@ -5,13 +5,15 @@ oracle's state vector.  Small tiles force many passes and stages and narrow
 register widths; both rotation-engine settings and both precisions' layouts
 are covered.  No GPU is used."""
 
+import copy
+
 import numpy as np
 import pytest
 
 import workload as w
 from oracle import statevector as sv
 from paper_2603_01443_gb300 import api, capi
-from program_interp import parse, run
+from program_interp import OP_DENSE, OP_ROT, OP_ROTC, TERM_PBLOCK, TERM_SIGN, parse, run
 
 ALL_KINDS = ["U3", "H", "X", "Z", "S", "SDG", "T", "TDG", "CZ", "CX", "SWAP", "ISWAP", "CAN"]
 
@@ -134,3 +136,72 @@ def test_phase_block_skip_flags(host_lib, prec, tile_bits):
             assert np.all(blk[5:12] == 1)
         assert blk[4] == 1  # hi[0], the empty product
     assert blocks > 0
+
+
+def _mutations(prog):
+    """One copy of the program per mutation, each changing one field the
+    interpreter reads: a rotation's tangent, a dense matrix entry, a sign
+    term's second bit, an adjacent-sign mask, a phase-block entry, two tile
+    bits of a pass.  Each takes the last such field in the program, where the
+    state is spread over every basis state (early in the first pass many
+    amplitudes are still zero, and a changed factor on them changes
+    nothing)."""
+    out = {}
+
+    def ops_of(pred):
+        return [o for o, op in enumerate(prog.ops) if pred(op)]
+
+    rot = ops_of(lambda op: op[0] in (OP_ROT, OP_ROTC) and abs(prog.mats[4 * op[6]].real) > 0.1)
+    if rot:
+        m = copy.deepcopy(prog)
+        m.mats[4 * m.ops[rot[-1]][6]] *= -1
+        out["rotation tangent"] = m
+    dense = ops_of(lambda op: op[0] == OP_DENSE)
+    if dense:
+        m = copy.deepcopy(prog)
+        m.mats[4 * m.ops[dense[-1]][6] + 1] *= 1j
+        out["dense entry"] = m
+    sign = [k for k, t in enumerate(prog.terms) if t[0] == TERM_SIGN and t[1] != t[2]]
+    if sign:
+        m = copy.deepcopy(prog)
+        kind, p0, p1, tab = m.terms[sign[-1]]
+        m.terms[sign[-1]] = (kind, p0, (p1 + 1) % m.nq if (p1 + 1) % m.nq != p0 else (p1 + 2) % m.nq, tab)
+        out["sign term bit"] = m
+    adj = ops_of(lambda op: op[7] != 0)
+    if adj:
+        m = copy.deepcopy(prog)
+        op = list(m.ops[adj[-1]])
+        op[7] &= op[7] - 1  # drop its lowest adjacent pair
+        m.ops[adj[-1]] = tuple(op)
+        out["adjacent sign mask"] = m
+    blk = [t for t in prog.terms if t[0] == TERM_PBLOCK]
+    if blk:
+        m = copy.deepcopy(prog)
+        m.tabs[4 * blk[-1][3]] *= np.exp(0.3j)  # the entry every amplitude with lo = 0 takes
+        out["phase block entry"] = m
+    multi = [i for i, P in enumerate(prog.passes) if P.k >= 6]
+    if multi:
+        m = copy.deepcopy(prog)
+        P = m.passes[multi[-1]]
+        P.tile_bit = list(P.tile_bit)
+        P.tile_bit[P.k - 1], P.tile_bit[P.k - 2] = P.tile_bit[P.k - 2], P.tile_bit[P.k - 1]
+        out["tile bit order"] = m
+    return out
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
+def test_interpreter_rejects_mutated_programs(host_lib, monkeypatch, rot):
+    # the host compiler's pins are only as strong as the interpreter: a
+    # program with any one field changed must miss the oracle's state
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    q = 9
+    gates = w.random_circuit(q, 160, 7, kinds=ALL_KINDS)
+    ref = sv.simulate(q, gates)
+    prog = interp(gates, q, "c64", 6)
+    assert rel(run(prog), ref) <= 1e-12
+    muts = _mutations(prog)
+    expect = {"rotation tangent", "sign term bit", "phase block entry", "tile bit order"} \
+        if rot == "1" else {"dense entry", "sign term bit", "tile bit order"}
+    assert expect <= set(muts), sorted(muts)
+    for name, m in muts.items():
+        assert rel(run(m), ref) > 1e-3, name
