@@ -156,3 +156,26 @@ def test_merge_stage_shapes(host_lib, segs):
         log_k += K.bit_length() - 1
         rows = Z
     assert log_k == n_bits
+
+
+@pytest.mark.parametrize("which", ["aidx", "bidx"])
+def test_chained_merge_rejects_wrong_tables(host_lib, which):
+    # the staged merge check depends on every table entry: exchanging two
+    # entries of one stage's row or segment indices moves the merged state
+    segs, q = [3, 3, 3], 9
+    gates = w.staircase(q, 2)
+    vecs, staged = [], None
+    for i, qi in enumerate(segs):
+        words, reals = api.plan_program_image(gates, q, segs, i, "projector", "c64", 0)
+        prog, tail = parse(words, reals, trailing=True)
+        staged = parse_stages(tail, tail[1])
+        vecs.append(run(prog).reshape(1 << tail[1], 1 << qi))
+    stages, tab = staged
+    good = chained_merge(vecs, stages, tab)
+    assert rel(good, sv.simulate(q, gates)) <= 1e-12
+    for seg, qa, qb, K, Z, ao, bo in stages:
+        off = ao if which == "aidx" else bo
+        bad = tab.copy()
+        j = next(j for j in range(1, Z * K) if bad[off + j] != bad[off])
+        bad[off], bad[off + j] = bad[off + j], bad[off]
+        assert rel(chained_merge(vecs, stages, bad), good) > 1e-3, (seg, which)
