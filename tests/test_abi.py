@@ -10,7 +10,7 @@ from ctypes import byref, c_double, c_int32, c_int64, c_void_p
 
 import pytest
 
-from paper_2603_01443_gb300 import capi
+from paper_2603_01443_gb300 import api, capi
 
 import workload as w
 
@@ -199,3 +199,15 @@ def test_cut_bits_limit_is_checked_on_the_host(L):
     assert st != 2
     if h.value:
         L.cc_plan_destroy(h)
+
+
+def test_plan_image_rejects_bad_segment_arguments(L):
+    # host-only checks, no device: a segment index outside the plan, and a
+    # segment whose qubits plus variant bits exceed the 34-bit vector limit
+    g = w.brickwork_cut(8, 4, 0, [4, 4], 2)
+    for seg in (-1, 2):
+        with pytest.raises(capi.CutsimError, match="segment index out of range"):
+            api.plan_program_image(g, 8, [4, 4], seg)
+    g = [w.Gate("H", 32), w.Gate("CZ", 32, 33), w.Gate("CZ", 32, 33), w.Gate("CZ", 32, 33)]
+    with pytest.raises(capi.CutsimError, match="needs 2"):
+        api.plan_program_image(g, 34, [33, 1], 0)
