@@ -11,6 +11,7 @@ import torch
 import workload as w
 from oracle import cutting as ct
 from oracle import statevector as sv
+from oracle import reductions as rd
 from paper_2603_01443_gb300 import api, capi
 from gpu_util import FID_TOL, TOL, assert_parity, fidelity, gpu_cut, gpu_uncut, rel_err
 
@@ -154,6 +155,18 @@ def test_single_segment_and_no_gates(cuda_lib):
     assert np.array_equal(psi.cpu().numpy(), ref.astype(np.complex64))
 
 
+def check_compare(got, ref, mtol):
+    """The device's verification quantities against the FP64 oracle's: the
+    maxima within mtol (relative), the inner product and norms within 1e-11."""
+    for k in ("max_abs_diff", "max_abs_b"):
+        assert abs(got[k] - ref[k]) <= mtol * ref[k], k
+    inner = abs(complex(ref["inner_re"], ref["inner_im"]))
+    for k in ("inner_re", "inner_im"):
+        assert abs(got[k] - ref[k]) <= 1e-11 * inner, k
+    for k in ("norm2_a", "norm2_b"):
+        assert abs(got[k] - ref[k]) <= 1e-11 * ref[k], k
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_compare_and_gather(cuda_lib, prec):
     rng = np.random.default_rng(3)
@@ -162,23 +175,14 @@ def test_compare_and_gather(cuda_lib, prec):
     b = a + (1e-3 * rng.standard_normal(n)).astype(api.NUMPY_DTYPE[prec])
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
     got = api.compare(ta, tb, prec)
-    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
-    inner = np.vdot(a64, b64)
     # complex64: the maxima are taken in FP32 (2^-24 relative on the squares),
     # the sums in exact products + double-float runs + FP64, as accurate as FP64
-    mtol = 1e-12 if prec == "c128" else 1e-7
-    assert abs(got["max_abs_diff"] - np.max(np.abs(a64 - b64))) <= mtol * np.max(np.abs(a64 - b64))
-    assert abs(got["max_abs_b"] - np.max(np.abs(b64))) <= mtol * np.max(np.abs(b64))
-    assert abs(got["inner_re"] - inner.real) <= 1e-11 * abs(inner)
-    assert abs(got["inner_im"] - inner.imag) <= 1e-11 * abs(inner)
-    assert abs(got["norm2_a"] - np.vdot(a64, a64).real) <= 1e-11 * np.vdot(a64, a64).real
-    assert abs(got["norm2_b"] - np.vdot(b64, b64).real) <= 1e-11 * np.vdot(b64, b64).real
+    check_compare(got, rd.compare(a, b), 1e-12 if prec == "c128" else 1e-7)
     # a nearly equal pair: 1 - fidelity resolved far below the complex64 rounding level
     c = (a + (1e-6 * rng.standard_normal(n)).astype(a.dtype)).astype(a.dtype)
     tc = torch.from_numpy(c).cuda()
     f = api.compare(ta, tc, prec)["fidelity"]
-    c64 = c.astype(np.complex128)
-    f_ref = abs(np.vdot(a64, c64)) ** 2 / (np.vdot(a64, a64).real * np.vdot(c64, c64).real)
+    f_ref = rd.compare(a, c)["fidelity"]
     assert abs(f - f_ref) <= 1e-13, (f, f_ref)
     idx = w.sample_indices(20, 4096, 5) + [n - 1, 0]
     assert np.array_equal(api.gather(ta, idx, prec), a[np.array(idx)])
@@ -195,14 +199,7 @@ def test_compare_lengths(cuda_lib, n):
     a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
     b = (a + 1e-3 * rng.standard_normal(n)).astype(np.complex64)
     got = api.compare(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), "c64")
-    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
-    inner = np.vdot(a64, b64)
-    assert abs(got["max_abs_diff"] - np.max(np.abs(a64 - b64))) <= 1e-7 * np.max(np.abs(a64 - b64))
-    assert abs(got["max_abs_b"] - np.max(np.abs(b64))) <= 1e-7 * np.max(np.abs(b64))
-    assert abs(got["inner_re"] - inner.real) <= 1e-11 * abs(inner)
-    assert abs(got["inner_im"] - inner.imag) <= 1e-11 * abs(inner)
-    assert abs(got["norm2_a"] - np.vdot(a64, a64).real) <= 1e-11 * np.vdot(a64, a64).real
-    assert abs(got["norm2_b"] - np.vdot(b64, b64).real) <= 1e-11 * np.vdot(b64, b64).real
+    check_compare(got, rd.compare(a, b), 1e-7)
 
 
 def test_error_paths_on_device(cuda_lib):
