@@ -3,6 +3,7 @@
 import numpy as np
 import torch
 
+from oracle import reductions as rd
 from paper_2603_01443_gb300 import api
 
 # Tolerances on max |d psi| / max |psi| and on 1 - fidelity.
@@ -11,13 +12,14 @@ FID_TOL = 1e-6
 
 
 def rel_err(got, ref):
-    return float(np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref)))
+    """max |got - ref| / max |ref|, from the oracle's verification quantities."""
+    r = rd.compare(np.asarray(got), np.asarray(ref))
+    return r["max_abs_diff"] / r["max_abs_b"]
 
 
 def fidelity(a, b):
-    a = np.asarray(a, dtype=np.complex128)
-    b = np.asarray(b, dtype=np.complex128)
-    return float(abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+    """|<a|b>|^2 / (|a|^2 |b|^2), from the oracle's verification quantities."""
+    return rd.compare(np.asarray(a), np.asarray(b))["fidelity"]
 
 
 def gpu_cut(gates, q, segs, decomp="projector", prec="c64", form="fma"):
