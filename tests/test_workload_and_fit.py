@@ -70,3 +70,15 @@ def test_planner_threshold_matches_the_oracle():
             assert planner.threshold(q, n) == pytest.approx(th.threshold(q, n), abs=1e-12)
     with pytest.raises(ValueError):
         planner.threshold(10, 1)
+
+
+def test_splitmix64_reference_sequence():
+    # the first outputs of SplitMix64 from state 0 (Steele, Lea, Flood 2014;
+    # the widely used reference sequence), and the derived doubles and angles
+    r = w.SplitMix64(0)
+    assert [r.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                0x06C45D188009454F]
+    r = w.SplitMix64(0)
+    assert r.next_double() == (0xE220A8397B1DCDAF >> 11) / 2.0 ** 53
+    a = r.next_angle()
+    assert a == 2.0 * math.pi * ((0x6E789E6AA1B965F4 >> 11) / 2.0 ** 53) and 0.0 <= a < 2 * math.pi
