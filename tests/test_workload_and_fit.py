@@ -82,3 +82,30 @@ def test_splitmix64_reference_sequence():
     assert r.next_double() == (0xE220A8397B1DCDAF >> 11) / 2.0 ** 53
     a = r.next_angle()
     assert a == 2.0 * math.pi * ((0x6E789E6AA1B965F4 >> 11) / 2.0 ** 53) and 0.0 <= a < 2 * math.pi
+
+
+def test_traffic_records_follow_the_kernel_source(monkeypatch, tmp_path):
+    # a DRAM-traffic record is used only for its own workload and only while
+    # the kernel source it was taken on is unchanged
+    import json
+
+    csrc = tmp_path / "paper_2603_01443_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("// kernel v1\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    a = bench.parse_args([])
+    rec = {"sources": ["k.cu"], "source_hash": bench.kernel_source_hash(["k.cu"]),
+           "dram_bytes_per_launch": 123.0}
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        json.dumps({bench.traffic_key("kern", a): rec}))
+    assert bench.recorded_traffic("kern", a) == 123.0
+    assert bench.recorded_traffic("kern", bench.parse_args(["--q", "28"])) is None
+    assert bench.recorded_traffic("other", a) is None
+    (csrc / "k.cu").write_text("// kernel v1 with a changed comment\n")
+    assert bench.recorded_traffic("kern", a) is None
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz
+    assert abs(bench.fp32_peak_tflops() - 80.55) < 0.01
