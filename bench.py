@@ -152,6 +152,12 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.summarize(out)
+
+    @staticmethod
+    def summarize(out):
+        """Median SM clock, the maximum clock and every throttle reason seen
+        Active, from nvidia-smi's CSV lines in FIELDS order (None if none)."""
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():

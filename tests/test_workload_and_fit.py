@@ -109,3 +109,21 @@ def test_traffic_records_follow_the_kernel_source(monkeypatch, tmp_path):
 def test_fp32_peak_from_unit_counts():
     # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz
     assert abs(bench.fp32_peak_tflops() - 80.55) < 0.01
+
+
+def test_clock_samples_summary():
+    # nvidia-smi CSV lines (FIELDS order): the median SM clock under load, the
+    # maximum clock and each throttle reason that was Active at least once
+    out = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1398.7, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+    s = bench.ClockSampler.summarize(out)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3,
+                 "reasons": ["sw_power_cap"]}
+    hot = out + "\n0, 1500, 2070, 1400, 0x48, Not Active, Active, Not Active, Active"
+    assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler.summarize("") is None
