@@ -114,3 +114,19 @@ def test_variant_bits_reversed_in_one_segment(monkeypatch):
 
     monkeypatch.setattr(ct, "preprocess", bad)
     assert caught(pins.pin_cut_equals_uncut(10, GATES, [4, 6], "projector"))
+
+
+def test_sampled_amplitudes_with_segment_bits_from_the_wrong_offset(monkeypatch):
+    # the per-amplitude form of Algorithm 3 (used at sizes where the full
+    # merge cannot be formed) must take each segment's bits from its own
+    # offset; reading segment i at the offset of segment n-1-i is caught by
+    # the comparison with the full merge
+    q, segs = 12, [5, 7]
+    gates = w.brickwork_cut(q, 6, 5, segs, 3)
+    psi, pre, states = ct.cut_simulate(q, gates, segs, "projector")
+    xs = np.array(w.sample_indices(q, 300, 17))
+    good = ct.amplitudes(pre, states, xs)
+    assert np.max(np.abs(good - psi[xs])) < 1e-15
+    pre.seg_starts = list(reversed(pre.seg_starts))
+    bad = ct.amplitudes(pre, states, xs)
+    assert caught(float(np.max(np.abs(bad - psi[xs]))))
