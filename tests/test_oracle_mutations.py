@@ -130,3 +130,28 @@ def test_sampled_amplitudes_with_segment_bits_from_the_wrong_offset(monkeypatch)
     pre.seg_starts = list(reversed(pre.seg_starts))
     bad = ct.amplitudes(pre, states, xs)
     assert caught(float(np.max(np.abs(bad - psi[xs]))))
+
+
+@pytest.mark.parametrize("mistake", ["no realignment", "dropped smallest term"])
+def test_schmidt_terms_mistakes(monkeypatch, mistake):
+    # the operator-Schmidt terms of a rank-4 cut (Eq. 1, k = 4): an SVD of the
+    # matrix itself instead of its realignment, or a dropped term, no longer
+    # rebuilds the gate, and the cut simulation no longer equals the uncut one
+    orig = ct.schmidt_terms
+
+    def bad(u, rtol=1e-12):
+        if mistake == "no realignment":
+            w_, sig, vh = np.linalg.svd(u)
+            return (tuple(complex(x) for x in sig), tuple(w_[:, l].reshape(2, 2) for l in range(4)),
+                    tuple(vh[l, :].reshape(2, 2) for l in range(4)))
+        coef, a, b = orig(u, rtol)
+        return coef[:-1], a[:-1], b[:-1]
+
+    monkeypatch.setattr(ct, "schmidt_terms", bad)
+    g = w.Gate("CAN", 0, 1, 0.3, 1.1, 2.9)
+    coef, a, b = ct.local_terms("CAN", "projector", g)
+    u = sum(c * np.kron(x, y) for c, x, y in zip(coef, a, b))
+    q, segs = 8, [4, 4]
+    gates = w.brickwork_cut(q, 4, 7, segs, 1, boundary_kind="CAN")
+    assert caught(float(np.max(np.abs(u - sv.gate_matrix(g)))),
+                  pins.pin_cut_equals_uncut(q, gates, segs, "projector"))
