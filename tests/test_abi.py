@@ -211,3 +211,25 @@ def test_plan_image_rejects_bad_segment_arguments(L):
     g = [w.Gate("H", 32), w.Gate("CZ", 32, 33), w.Gate("CZ", 32, 33), w.Gate("CZ", 32, 33)]
     with pytest.raises(capi.CutsimError, match="needs 2"):
         api.plan_program_image(g, 34, [33, 1], 0)
+
+
+def test_last_error_is_per_thread(L):
+    # each thread sees the message of its own last failed call
+    import threading
+
+    g = w.brickwork(8, 2, 0)
+    msgs = {}
+    ready = threading.Barrier(2)
+
+    def fail_with(name, args):
+        ready.wait()
+        for _ in range(200):
+            with pytest.raises(capi.CutsimError):
+                api.plan_program_image(*args)
+            msgs.setdefault(name, set()).add(L.cc_last_error())
+
+    t1 = threading.Thread(target=fail_with, args=("seg", (g, 8, [4, 4], 5)))
+    t2 = threading.Thread(target=fail_with, args=("sum", (g, 8, [4, 3], 0)))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert msgs["seg"] == {b"segment index out of range"}
+    assert msgs["sum"] == {b"segment sizes do not sum to q"}
