@@ -179,3 +179,16 @@ def test_chained_merge_rejects_wrong_tables(host_lib, which):
         j = next(j for j in range(1, Z * K) if bad[off + j] != bad[off])
         bad[off], bad[off + j] = bad[off + j], bad[off]
         assert rel(chained_merge(vecs, stages, bad), good) > 1e-3, (seg, which)
+
+
+@pytest.mark.parametrize("gates", [
+    [],                                                    # no gates, no cuts
+    [w.Gate("H", 0), w.Gate("H", 5), w.Gate("CZ", 2, 3)],  # one cut, boundary (1, 2) uncut
+    [w.Gate("H", 7), w.Gate("CX", 7, 4), w.Gate("T", 4)],  # one CX cut on boundary (1, 2) only
+])
+def test_degenerate_cut_plans(host_lib, gates):
+    # boundaries without cuts give stages with K = 1 or Z = 1; the staged and
+    # the exhaustive merges both still give the uncut state
+    q, segs = 8, [3, 3, 2]
+    got = cut_state(gates, q, segs, "projector", "c64", 5)
+    assert rel(got, sv.simulate(q, gates)) <= 1e-12

@@ -205,3 +205,15 @@ def test_interpreter_rejects_mutated_programs(host_lib, monkeypatch, rot):
     assert expect <= set(muts), sorted(muts)
     for name, m in muts.items():
         assert rel(run(m), ref) > 1e-3, name
+
+
+@pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c128", 4), ("c64", 14)])
+@pytest.mark.parametrize("gates", [[], [w.Gate("Z", 3)], [w.Gate("CZ", 0, 7)], [w.Gate("H", 7)]])
+def test_degenerate_circuits(host_lib, prec, tile_bits, gates):
+    # no gates, one diagonal gate (which leaves |0...0> unchanged), one gate on
+    # the highest qubit: the program still starts from |0...0> and ends
+    # with every pending factor applied
+    q = 8
+    prog = interp(gates, q, prec, tile_bits)
+    assert len(prog.passes) >= 1
+    assert rel(run(prog), sv.simulate(q, gates)) <= 1e-15
