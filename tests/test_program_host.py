@@ -217,3 +217,66 @@ def test_degenerate_circuits(host_lib, prec, tile_bits, gates):
     prog = interp(gates, q, prec, tile_bits)
     assert len(prog.passes) >= 1
     assert rel(run(prog), sv.simulate(q, gates)) <= 1e-15
+
+
+def validate(prog):
+    """Structural checks of a program, the ones the kernels rely on: each pass
+    orders all nq bits (tile bits, then the rest) with its low tile bits
+    contiguous; stages partition the ops in order; register bits name
+    distinct tile positions; every op's terms lie in its own range with the
+    kinds of their section (signs, then one phase block and its per-bit
+    phases, then tables); matrices and tables exist; bits lie below nq."""
+    from program_interp import OP_DIAG, TERM_PFIX, TERM_TABLE
+
+    n_mat, n_tab = len(prog.mats) // 4, len(prog.tabs) // 4
+    next_stage, next_op = 0, 0
+    for pi, P in enumerate(prog.passes):
+        assert P.init_zero == (1 if pi == 0 else 0)
+        order = list(P.tile_bit[:P.k]) + list(P.rest_bit[:P.n_rest])
+        assert sorted(order) == list(range(prog.nq)) and P.k + P.n_rest == prog.nq
+        assert P.stage_begin == next_stage and P.stage_end > P.stage_begin
+        next_stage = P.stage_end
+        for si in range(P.stage_begin, P.stage_end):
+            op_begin, op_end, rb = prog.stages[si]
+            assert op_begin == next_op and op_end >= op_begin
+            next_op = op_end
+            regs = list(rb[:P.rbits])
+            assert len(set(regs)) == P.rbits and all(0 <= r < P.k for r in regs)
+            for o in range(op_begin, op_end):
+                typ, t, tb0, n_sign, n_phase, n_table, mat, sign_adj = prog.ops[o]
+                assert 0 <= tb0 and tb0 + n_sign + n_phase + n_table <= len(prog.terms)
+                assert sign_adj >> max(prog.nq - 1, 0) == 0
+                if typ == OP_DIAG:
+                    assert mat == -1
+                else:
+                    assert 0 <= t < P.rbits and 0 <= mat < n_mat
+                sec = ([TERM_SIGN] * n_sign + ([TERM_PBLOCK] if n_phase else [])
+                       + [TERM_PFIX] * max(n_phase - 1, 0) + [TERM_TABLE] * n_table)
+                for k, kind in zip(range(tb0, tb0 + len(sec)), sec):
+                    tk, p0, p1, tab = prog.terms[k]
+                    assert tk == kind
+                    assert 0 <= p0 < prog.nq and 0 <= p1 < prog.nq
+                    if kind == TERM_PBLOCK:
+                        assert 0 <= tab and tab + 3 <= n_tab
+                    elif kind != TERM_SIGN:
+                        assert 0 <= tab < n_tab
+    assert next_stage == len(prog.stages) and next_op == len(prog.ops)
+
+
+@pytest.mark.parametrize("rot", ["1", "0"])
+def test_programs_are_well_formed(host_lib, monkeypatch, rot):
+    monkeypatch.setenv("CUTSIM_ROT", rot)
+    for prec, tb in [("c64", 5), ("c64", 13), ("c128", 4), ("c128", 12)]:
+        for q, n_gates, seed in [(6, 120, 1), (10, 300, 2)]:
+            validate(interp(w.random_circuit(q, n_gates, seed, kinds=ALL_KINDS), q, prec, tb))
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_largest_programs_are_well_formed(host_lib, prec):
+    # q = 34, the library's largest vector: too large to interpret here, so
+    # the program is checked for the structure the kernels rely on
+    q = 34
+    gates = w.brickwork(q, 3, 5) + [w.Gate("SWAP", 0, 33), w.Gate("CX", 33, 1)]
+    prog = interp(gates, q, prec, 0)
+    validate(prog)
+    assert len(prog.passes) >= 3
