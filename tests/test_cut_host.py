@@ -192,3 +192,23 @@ def test_degenerate_cut_plans(host_lib, gates):
     q, segs = 8, [3, 3, 2]
     got = cut_state(gates, q, segs, "projector", "c64", 5)
     assert rel(got, sv.simulate(q, gates)) <= 1e-12
+
+
+@pytest.mark.parametrize("segs,c", [([17, 17], 6), ([12, 11, 11], [3, 4])])
+def test_largest_segment_programs_are_well_formed(host_lib, segs, c):
+    # q = 34 plans: each segment's program over its qubits and variant bits
+    # has the structure the kernels rely on, and its tables match the stages
+    from test_program_host import validate
+
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 8, 3, segs, c)
+    for i, qi in enumerate(segs):
+        words, reals = api.plan_program_image(gates, q, segs, i, "projector", "c64", 0)
+        prog, tail = parse(words, reals, trailing=True)
+        c_i = int(tail[1])
+        assert prog.nq == qi + c_i and prog.n_state == qi
+        validate(prog)
+        stages, tab = parse_stages(tail, c_i)
+        assert len(stages) == len(segs) - 1
+        # each stage has Z K row indices and Z K segment indices
+        assert sum(2 * K * Z for _, _, _, K, Z, _, _ in stages) == len(tab)
