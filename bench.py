@@ -60,6 +60,7 @@ def parse_args(argv=None):
                    help="largest c_total of the boundary sweep (capped by the depth)")
     p.add_argument("--sweep-both", action="store_true",
                    help="sweep complex64 and complex128")
+    p.add_argument("--oracle-timing", default=None, help=argparse.SUPPRESS)
     return p.parse_args(argv)
 
 
@@ -178,58 +179,188 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline_sample(a, n_sub_sample=96, n_amp=1 << 22):
-    """Time the FP64 oracle on a bounded sample of the workload, in a fresh
-    single-threaded interpreter, and extrapolate to T_cut seconds."""
-    code = r"""
-import json, os, sys, time
-sys.path.insert(0, %r)
-import numpy as np
-import workload as w
-from oracle import cutting as ct, statevector as sv
-q, depth, n, ctot, seed, decomp, n_sub_sample, n_amp = %d, %d, %d, %d, %d, %r, %d, %d
-segs = w.equal_partition(q, n)
-gates = w.brickwork_cut(q, depth, seed, segs, w.split_cuts(ctot, n))
-t0 = time.perf_counter(); pre = ct.preprocess(q, gates, segs, decomp); t_pre = time.perf_counter() - t0
-subs = [(i, r) for i in range(n) for r in range(len(pre.subcircuits[i]))]
-pick = subs[:: max(1, len(subs) // n_sub_sample)][:n_sub_sample]
-states = [[None] * len(pre.subcircuits[i]) for i in range(n)]
-t0 = time.perf_counter()
-for i, r in pick:
-    states[i][r] = sv.simulate_ops(segs[i], pre.subcircuits[i][r])
-t_sub_sample = time.perf_counter() - t0
-# unsampled subcircuits only feed the timing of the merge sum: any vector will do
-for i in range(n):
-    for r in range(len(states[i])):
-        if states[i][r] is None:
-            states[i][r] = sv.zero_state(segs[i])
-xs = w.sample_indices(q, n_amp, 7)
-t0 = time.perf_counter(); ct.amplitudes(pre, states, xs); t_merge_sample = time.perf_counter() - t0
-t_sub = t_sub_sample * len(subs) / len(pick)
-t_merge = t_merge_sample * (2 ** q) / n_amp
-print(json.dumps({"t_pre": t_pre, "t_sub": t_sub, "t_merge": t_merge,
-                  "sample_s": t_pre + t_sub_sample + t_merge_sample,
-                  "n_sub": len(subs), "n_sub_sample": len(pick), "n_amp": n_amp}))
-"""
-    src = code % (ROOT, a.q, a.depth, a.n, a.ctotal, a.seed, a.decomp, n_sub_sample, n_amp)
+# ---------------------------------------------------------------- CPU oracle
+# The FP64 oracle timed on the host cores, in a separate interpreter that
+# never touches the GPU, over a pool of spawned worker processes (one per
+# usable core, numpy single-threaded in each):
+#   Algorithm 1 in full (sequential, as written);
+#   Algorithm 2 in full: every subcircuit, spread over the pool, its state
+#     written into one shared-memory block;
+#   Algorithm 3 on a sample of contiguous slabs of the output, each slab one
+#     full row of the lowest segment (2^{q_0} amplitudes, the oracle's
+#     per-amplitude form of the sum), the slabs spread evenly over the 2^q
+#     output and over the pool; every slab is the same work, so the wall time
+#     scales to the whole output by the number of slabs.  The estimate is
+#     taken at S and at 2S slabs to show that it has converged.
+# The pool also evaluates the oracle's amplitudes at the 4096 seeded indices
+# of the GPU parity check (outside every timed region).
+
+_OW = {}
+
+
+def _ow_init(root, spec, shm_name, offsets, shapes):
+    import sys as _sys
+
+    if root not in _sys.path:
+        _sys.path.insert(0, root)
+    import numpy as np
+    from multiprocessing import shared_memory
+
+    import workload as w
+    from oracle import cutting as ct
+
+    segs = w.equal_partition(spec["q"], spec["n"])
+    gates = w.brickwork_cut(spec["q"], spec["depth"], spec["seed"], segs,
+                            w.split_cuts(spec["ctotal"], spec["n"]))
+    _OW["pre"] = ct.preprocess(spec["q"], gates, segs, spec["decomp"])
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _OW["shm"] = shm
+    buf = np.ndarray((sum(int(np.prod(s)) for s in shapes),), dtype=np.complex128, buffer=shm.buf)
+    _OW["states"] = [[buf[o:o + shapes[i][1]] for o in offs] for i, offs in enumerate(offsets)]
+
+
+def _ow_ping(_):
+    return os.getpid()
+
+
+def _ow_sub(job):
+    from oracle import statevector as sv
+
+    i, r = job
+    pre = _OW["pre"]
+    _OW["states"][i][r][:] = sv.simulate_ops(pre.seg_sizes[i], pre.subcircuits[i][r])
+    return job
+
+
+def _ow_slab(x0):
+    import numpy as np
+
+    from oracle import cutting as ct
+
+    pre = _OW["pre"]
+    L = 1 << pre.seg_sizes[0]
+    ct.amplitudes(pre, _OW["states"], np.arange(x0, x0 + L, dtype=np.int64))
+    return x0
+
+
+def _ow_sample(xs):
+    from oracle import cutting as ct
+
+    out = ct.amplitudes(_OW["pre"], _OW["states"], xs)
+    return [[float(v.real), float(v.imag)] for v in out]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_timing_main(spec):
+    """Entry of the CPU oracle timing interpreter (see above); prints one JSON line."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    import workload as w
+    from oracle import cutting as ct
+
+    q, n = spec["q"], spec["n"]
+    segs = w.equal_partition(q, n)
+    gates = w.brickwork_cut(q, spec["depth"], spec["seed"], segs, w.split_cuts(spec["ctotal"], n))
+    t0 = time.perf_counter()
+    pre = ct.preprocess(q, gates, segs, spec["decomp"])
+    t_pre = time.perf_counter() - t0
+
+    shapes = [(len(pre.subcircuits[i]), 1 << segs[i]) for i in range(n)]
+    offsets, off = [], 0
+    for nv, size in shapes:
+        offsets.append([off + r * size for r in range(nv)])
+        off += nv * size
+    shm = shared_memory.SharedMemory(create=True, size=max(16, off * 16))
+    cores = spec.get("cores") or host_cores()
+    ctx = mp.get_context("spawn")
+    res = {}
+    try:
+        with ctx.Pool(cores, initializer=_ow_init,
+                      initargs=(ROOT, spec, shm.name, offsets, shapes)) as pool:
+            pool.map(_ow_ping, range(4 * cores), chunksize=1)  # every worker up before timing
+            jobs = [(i, r) for i in range(n) for r in range(shapes[i][0])]
+            t0 = time.perf_counter()
+            pool.map(_ow_sub, jobs, chunksize=1)
+            t_sub = time.perf_counter() - t0
+            L = 1 << segs[0]
+            n_slabs_total = (1 << q) // L
+            est = []
+            for S in spec["slabs"]:
+                S = min(S, n_slabs_total)
+                stride = n_slabs_total // S
+                x0s = [(j * stride + (stride // 2 if len(est) else 0)) * L for j in range(S)]
+                t0 = time.perf_counter()
+                pool.map(_ow_slab, x0s, chunksize=max(1, S // (4 * cores)))
+                t_s = time.perf_counter() - t0
+                est.append({"slabs": S, "slab_amplitudes": L, "seconds": t_s,
+                            "t_merge": t_s * n_slabs_total / S})
+            if spec.get("sample_seed") is not None:
+                xs = w.sample_indices(q, 4096, spec["sample_seed"])
+                chunks = [xs[k:k + 256] for k in range(0, len(xs), 256)]
+                amps = [v for part in pool.map(_ow_sample, chunks) for v in part]
+                res["sample_amplitudes"] = amps
+                res["sample_seed"] = spec["sample_seed"]
+    finally:
+        shm.close()
+        shm.unlink()
+    res.update({"t_pre": t_pre, "t_sub": t_sub, "merge_estimates": est, "cores": cores,
+                "n_sub": sum(s[0] for s in shapes)})
+    print(json.dumps(res))
+    return 0
+
+
+def run_oracle_timing(a, slabs, sample_seed=None, timeout=900):
+    """The CPU oracle timing interpreter for workload a; its JSON result or {"error": ...}."""
+    spec = {"q": a.q, "depth": a.depth, "n": a.n, "ctotal": a.ctotal, "seed": a.seed,
+            "decomp": a.decomp, "slabs": list(slabs), "sample_seed": sample_seed}
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, env=env,
-                       timeout=600)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-timing",
+                        json.dumps(spec)], capture_output=True, text=True, env=env, timeout=timeout)
     if r.returncode != 0:
-        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    value = d["t_pre"] + d["t_sub"] + d["t_merge"]
-    return {
-        "value": value, "unit": "s", "cores": 1, "kind": "oracle",
-        "sample": (f"Algorithm 1 in full, Algorithm 2 on {d['n_sub_sample']} of {d['n_sub']} "
-                   f"subcircuits, the Algorithm 3 sum at {d['n_amp']} of 2^{a.q} amplitudes "
-                   f"(per-amplitude form); scaled to the whole workload"),
-        "sample_seconds": d["sample_s"],
-        "stages": {"pre_s": d["t_pre"], "sub_s": d["t_sub"], "merge_s": d["t_merge"]},
+        tail = r.stderr.strip().splitlines()
+        return {"error": tail[-1] if tail else "failed"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# Slabs of the Algorithm 3 sample: the estimate from BASE_SLABS is the value;
+# the cpu_baseline leg also measures 2 x BASE_SLABS as the convergence check.
+BASE_SLABS = 1024
+
+
+def cpu_value(d, a, which=0):
+    t_merge = d["merge_estimates"][which]["t_merge"]
+    return d["t_pre"] + d["t_sub"] + t_merge
+
+
+def cpu_record(d, a):
+    e0 = d["merge_estimates"][0]
+    rec = {
+        "value": cpu_value(d, a, 0), "unit": "s", "cores": d["cores"], "kind": "oracle",
+        "sample": (f"Algorithm 1 in full; Algorithm 2 in full ({d['n_sub']} subcircuits over "
+                   f"{d['cores']} worker processes); the Algorithm 3 sum (per-amplitude form) on "
+                   f"{e0['slabs']} contiguous slabs of {e0['slab_amplitudes']} amplitudes spread "
+                   f"evenly over the 2^{a.q} output, scaled by the slab count"),
+        "sample_seconds": d["t_pre"] + d["t_sub"] + e0["seconds"],
+        "stages": {"pre_s": d["t_pre"], "sub_s": d["t_sub"], "merge_s": e0["t_merge"]},
     }
+    if len(d["merge_estimates"]) > 1:
+        e1 = d["merge_estimates"][1]
+        rec["convergence"] = {"slabs": [e0["slabs"], e1["slabs"]],
+                              "t_merge_s": [e0["t_merge"], e1["t_merge"]],
+                              "ratio": e1["t_merge"] / e0["t_merge"]}
+    return rec
 
 
 def max_over_ranks(values, world, device=None):
@@ -253,16 +384,17 @@ def reference_arm(a):
     vals, secs = [], []
     last = None
     for i in range(a.warmup + a.steps):
-        r = cpu_baseline_sample(a, n_sub_sample=24, n_amp=1 << 20)
-        if "error" in r:
-            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + r["error"]}))
+        t0 = time.perf_counter()
+        d = run_oracle_timing(a, [BASE_SLABS])
+        if "error" in d:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + d["error"]}))
             return 0
         if i >= a.warmup:
-            vals.append(r["value"])
-            secs.append(r["sample_seconds"])
-            last = r
+            vals.append(cpu_value(d, a))
+            secs.append(time.perf_counter() - t0)
+            last = d
     value = statistics.mean(vals)
-    cpu = dict(last)
+    cpu = cpu_record(last, a)
     cpu["value"] = value
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
@@ -764,6 +896,8 @@ def sweep_batch(a, n_circ=64):
 
 def main(argv=None):
     a = parse_args(argv)
+    if a.oracle_timing is not None:
+        return oracle_timing_main(json.loads(a.oracle_timing))
     if a.impl == "reference":
         return reference_arm(a)
     if a.sweep == "boundary":
@@ -962,8 +1096,57 @@ def main(argv=None):
     # chain stages (FMA), the last stage (split + tensor-core kernel, or FMA),
     # the uncut passes, and the two verification kernels
     launches = 1 + (info["n_seg"] - 2) + (2 if tc_form != "fma" else 1) + n_pass + 2
+    # subcircuit stage (Algorithm 2): N_sub variants of 2^{q_i} amplitudes, 16
+    # flops per amplitude per dense one-qubit gate of the segment, 6 per
+    # diagonal factor (CZ inside the segment, the cut terms on its side)
+    seg_flops = 0.0
+    for i in range(info["n_seg"]):
+        lo, hi = info["seg_start"][i], info["seg_start"][i] + info["seg_qubits"][i]
+        inside = lambda x: lo <= x < hi
+        g_nd = g_diag = 0
+        for g in gates:
+            if g.q1 < 0:
+                if inside(g.q0):
+                    if g.kind in ("U3", "H", "X"):
+                        g_nd += 1
+                    else:
+                        g_diag += 1
+            elif inside(g.q0) and inside(g.q1):
+                g_nd += 2 if g.kind == "CX" else 0
+                g_diag += 1
+            elif inside(g.q0) or inside(g.q1):  # a cut: its term on this side
+                g_nd += 2 if (g.kind == "CX" and inside(g.q1)) else 0
+                g_diag += 1
+        seg_flops += (1 << (info["seg_cuts"][i] + info["seg_qubits"][i])) * (16.0 * g_nd + 6.0 * g_diag)
+    seg_tf = seg_flops / mean["sub"] / 1e12
+    seg_rf = {"bound": "alu", "achieved": seg_tf, "peak": alu_peak, "unit": "TFLOP/s",
+              "frac": seg_tf / alu_peak, "traffic": recorded_traffic("segments", a),
+              "kernel": "batch_kernel (all passes of all segments, one persistent launch)",
+              "flops_per_launch": seg_flops, "launch_s": mean["sub"],
+              "bytes_written": float(info["seg_buf_bytes"]), "peak_source": alu_src}
     cmp = rec["cmp"][-1]
-    cpu = None if a.no_cpu_baseline else cpu_baseline_sample(a)
+    orc = None
+    if not a.no_cpu_baseline:
+        orc = run_oracle_timing(a, [BASE_SLABS, 2 * BASE_SLABS], sample_seed=2024)
+    cpu = None
+    oracle_parity = None
+    if orc is not None and "error" in orc:
+        cpu = {"error": orc["error"]}
+    elif orc is not None:
+        cpu = cpu_record(orc, a)
+        import numpy as np
+
+        xs = w.sample_indices(a.q, 4096, orc["sample_seed"])
+        got = api.gather(psi, xs, a.prec).astype(np.complex128)
+        ref = np.array([complex(re, im) for re, im in orc["sample_amplitudes"]])
+        scale = api.compare(psi, psi, a.prec)["max_abs_b"]  # max |psi| of the whole cut state
+        dot = np.vdot(ref, got)
+        oracle_parity = {
+            "samples": len(xs), "seed": orc["sample_seed"],
+            "max_abs_diff_over_max": float(np.max(np.abs(got - ref)) / scale),
+            "fidelity_sampled": float(abs(dot) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)),
+            "tolerance": {"c64": 2e-6, "c128": 1e-12}[a.prec] if a.merge_form != "bf16x3" else 5e-5,
+        }
     out = {
         "metric": METRIC,
         "value": t_cut,
@@ -989,11 +1172,13 @@ def main(argv=None):
         "seg_passes": info["seg_passes"],
         "merge_terms": K,
         "threshold_n2": a.q / 2 if a.n == 2 else None,
-        "parity": {"max_abs_diff_over_max": cmp["max_abs_diff"] / cmp["max_abs_b"],
-                   "fidelity": cmp["fidelity"], "norm2_cut": cmp["norm2_a"],
-                   "norm2_uncut": cmp["norm2_b"]},
+        "parity": {"vs_uncut_gpu": {"max_abs_diff_over_max": cmp["max_abs_diff"] / cmp["max_abs_b"],
+                                    "fidelity": cmp["fidelity"], "norm2_cut": cmp["norm2_a"],
+                                    "norm2_uncut": cmp["norm2_b"]},
+                   "vs_oracle_sampled": oracle_parity},
         "roofline": dominant,
-        "rooflines": {"merge": merge_rf, "uncut_pass": pass_rf, "verify": verify_rf},
+        "rooflines": {"merge": merge_rf, "uncut_pass": pass_rf, "segments": seg_rf,
+                      "verify": verify_rf},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches * a.steps,

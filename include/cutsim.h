@@ -282,9 +282,9 @@ cc_status cc_gather(const void* psi, int64_t n_amp, int32_t precision, const int
  *     of the library image (CC_GATHER_STATIC_MAX entries, 1.5 MiB held on
  *     every GPU that loads the library until the process exits); n_idx above
  *     CC_GATHER_STATIC_MAX is rejected with CC_ERANGE before any device work;
- *   - the first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current, so make the first call
- *     on each device before any stream capture;
+ *   - every call looks up that array's device address (cudaGetSymbolAddress)
+ *     with the caller's device current; the call synchronizes `stream`, so
+ *     it cannot be recorded into a stream capture;
  *   - every call on a device shares the one array: calls whose device work
  *     overlaps (other threads, other streams) race and may return each
  *     other's amplitudes.  A call synchronizes `stream` before it returns, so

@@ -11,12 +11,12 @@
 //
 // The array (CC_GATHER_STATIC_MAX indices and amplitudes, 1.5 MiB) lives in
 // every GPU that loads the library until the process exits.  Host code cannot
-// use the array's name as a device address; the first call on each device
-// resolves the address with cudaGetSymbolAddress while that device is
-// current, and later calls reuse it.
+// use the array's name as a device address: every call resolves the address
+// with cudaGetSymbolAddress while the caller's device is current.  The lookup
+// is not cached, so a device reset that loads the library's module again (at
+// a new address) cannot leave a stale pointer behind.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -32,28 +32,22 @@ constexpr size_t kValBytes = kMax * 16;                 // 1 MiB of amplitudes (
 // the array has to start at zero.
 static __device__ __align__(256) unsigned char g_gather_scratch[kIdxBytes + kValBytes];
 
-std::mutex g_mu;
-void* g_addr[64] = {nullptr};
-
-// Device address of g_gather_scratch on the current device (set up once per device).
+// Device address of g_gather_scratch on the current device, looked up afresh
+// on every call.
 cc_status scratch_address(void** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     cudaGetLastError();
     return cc::fail(CC_ECUDA, "cc_gather_static: no current CUDA device");
   }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_gather_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return cc::fail(CC_ECUDA, std::string("cc_gather_static: cudaGetSymbolAddress failed: ") +
-                                    cudaGetErrorString(e));
-    }
-    g_addr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_gather_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return cc::fail(CC_ECUDA, std::string("cc_gather_static: cudaGetSymbolAddress failed: ") +
+                                  cudaGetErrorString(e));
   }
-  *out = g_addr[dev];
+  *out = p;
   return CC_OK;
 }
 

@@ -21,12 +21,11 @@
 //               blocks, staged through shared memory and written by bulk
 //               tensor stores (TMA), then release of the accumulator, so the
 //               store of tile i overlaps the MMAs of tile i+1.
-// Forms: merge_tc_kernel (the structure above); merge_tc_pair_kernel, the
-// default, where two CTAs of a cluster share each column tile by TMA
-// multicast and stream K in 128-, 64- or 32-byte blocks (2, 4 or 8 stages);
-// merge_tc_rs_kernel (row operand resident in shared memory) and
-// merge_tc_2sm_kernel (one cta_group::2 MMA of M = 256 per pair), both
-// opt-in and slower on GB300.
+// Forms: merge_tc_kernel (the structure above, streaming K in 128-, 64- or
+// 32-byte blocks through 2, 4 or 8 stages of the same 192 KB), the default;
+// merge_tc_rs_kernel (row operand resident in shared memory), opt-in and
+// slower on GB300.  No form shares a load between CTAs: each CTA fetches its
+// own operand tiles from L2.
 // Every mbarrier wait is bounded: on expiry the kernel raises a device error
 // flag (reported as CC_ETIMEOUT by cc_sync), waits a bounded time for its own
 // copies and MMAs in flight, frees its TMEM and returns.
@@ -239,30 +238,39 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // stores and adds every later group with tensor reduce-add stores (FP32 adds
 // in L2, after the warp's earlier stores of the tile have completed), so no
 // single tensor-core accumulation runs longer than group_kb K blocks.
-template <int KIND>
+//
+// KBB bytes of K per stage (the swizzle width) and NST stages: the operand
+// buffers hold NST * (2 * BM + 2 * BN) * KBB bytes (192 KB for 128 x 2 and
+// 64 x 4); narrower, more numerous stages keep more loads in flight while the
+// tensor cores read one.  Every CTA loads its own operand tiles: no load is
+// shared between CTAs.
+template <int KIND, int KBB, int NST>
 __global__ void __launch_bounds__(192, 1)
     merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
                     int kblocks, int group_kb, int* err) {
+  constexpr int RT = BM * KBB, CT = BN * KBB, STB = 2 * RT + 2 * CT;
+  static_assert(NST * STB == STAGES * STAGE_BYTES, "operand buffers of 192 KB");
+  static_assert((2 * NST + 8) * 8 <= 256, "barrier area");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stg_base = smem + STAGES * STAGE_BYTES;
+  unsigned char* stg_base = smem + NST * STB;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
-  uint64_t* full = bars;                 // [STAGES]
-  uint64_t* empty = bars + STAGES;       // [STAGES]
-  uint64_t* tfull = bars + 2 * STAGES;   // [2]
-  uint64_t* tempty = bars + 2 * STAGES + 2;  // [2]
-  uint64_t* drain = bars + 2 * STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * STAGES + 7);
+  uint64_t* full = bars;                  // [NST]
+  uint64_t* empty = bars + NST;           // [NST]
+  uint64_t* tfull = bars + 2 * NST;       // [2]
+  uint64_t* tempty = bars + 2 * NST + 2;  // [2]
+  uint64_t* drain = bars + 2 * NST + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NST + 7);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = n_rows / BM, tiles_n = n_cols / BN;
   const int n_tiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -293,10 +301,14 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c)) : "memory");
       int s = 0;
       uint32_t use = 0;  // how many times the stage ring wrapped
-      bool issued[STAGES] = {false, false};
-      uint32_t issued_parity[STAGES] = {0, 0};
+      bool issued[NST];
+      uint32_t issued_parity[NST];
+      for (int i = 0; i < NST; ++i) {
+        issued[i] = false;
+        issued_parity[i] = 0;
+      }
       bool ok = true;
-      const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+      const int kelem = KIND == CC_MERGE_BF16X3 ? KBB / 2 : KBB / 4;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int m0, n0;
         tile_coords(t, tiles_m, tiles_n, m0, n0);
@@ -305,23 +317,23 @@ __global__ void __launch_bounds__(192, 1)
             ok = false;
             break;
           }
-          unsigned char* st = smem + s * STAGE_BYTES;
+          unsigned char* st = smem + s * STB;
           const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(&full[s], STAGE_BYTES);
+          mbar_expect_tx(&full[s], STB);
           tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, m0);
-          tma_load_2d(smem_u32(st + R_TILE), &map_r, fb, kb * kelem, n_rows + m0);
-          tma_load_2d(smem_u32(st + 2 * R_TILE), &map_c, fb, kb * kelem, n0);
-          tma_load_2d(smem_u32(st + 2 * R_TILE + C_TILE), &map_c, fb, kb * kelem, n_cols + n0);
+          tma_load_2d(smem_u32(st + RT), &map_r, fb, kb * kelem, n_rows + m0);
+          tma_load_2d(smem_u32(st + 2 * RT), &map_c, fb, kb * kelem, n0);
+          tma_load_2d(smem_u32(st + 2 * RT + CT), &map_c, fb, kb * kelem, n_cols + n0);
           issued[s] = true;
           issued_parity[s] = use & 1;
-          if (++s == STAGES) {
+          if (++s == NST) {
             s = 0;
             ++use;
           }
         }
       }
       if (!ok) {  // let our own copies land before the CTA exits
-        for (int i = 0; i < STAGES; ++i)
+        for (int i = 0; i < NST; ++i)
           if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
       }
     }
@@ -349,11 +361,11 @@ __global__ void __launch_bounds__(192, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t rh = sdesc(st), rl = sdesc(st + R_TILE);
-            const uint64_t ch = sdesc(st + 2 * R_TILE), cl = sdesc(st + 2 * R_TILE + C_TILE);
+            const uint32_t st = smem_u32(smem + s * STB);
+            const uint64_t rh = sdesc_sw<KBB>(st), rl = sdesc_sw<KBB>(st + RT);
+            const uint64_t ch = sdesc_sw<KBB>(st + 2 * RT), cl = sdesc_sw<KBB>(st + 2 * RT + CT);
 #pragma unroll
-            for (int k = 0; k < KB_BYTES / 32; ++k) {
+            for (int k = 0; k < KBB / 32; ++k) {
               const uint64_t adv = (uint64_t)((k * 32) >> 4);
               umma<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
               umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
@@ -361,7 +373,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             any_mma = true;
             umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
-            if (++s == STAGES) {
+            if (++s == NST) {
               s = 0;
               ++use;
             }
@@ -386,6 +398,8 @@ __global__ void __launch_bounds__(192, 1)
     int iter = 0;
     bool ok_all = true;
     for (int t = blockIdx.x; t < n_tiles && ok_all; t += gridDim.x) {
+      int m0, n0;
+      tile_coords(t, tiles_m, tiles_n, m0, n0);
       for (int kb0 = 0; kb0 < kblocks; kb0 += group_kb, ++iter) {
         const int a = iter & 1;
         // one lane waits, the warp follows its verdict (tcgen05.ld needs the whole warp)
@@ -402,645 +416,6 @@ __global__ void __launch_bounds__(192, 1)
           if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
           __syncwarp();
         }
-        int m0, n0;
-        tile_coords(t, tiles_m, tiles_n, m0, n0);
-        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
-#pragma unroll 1
-        for (int c2 = 0; c2 < BN / 32; c2 += 2) {
-          uint32_t rr[2][32];
-          tmem_ld32x2(tbase + (uint32_t)(c2 * 32), rr[0], rr[1]);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-          const int c = c2 + h;
-          uint32_t (&r)[32] = rr[h];
-          unsigned char* sb = stg + buf * STG_BYTES;
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          __syncwarp();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
-            *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {
-            if (add)
-              asm volatile(
-                  "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group"
-                  " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(&map_out)),
-                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
-                  : "memory");
-            else
-              asm volatile(
-                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                      reinterpret_cast<uint64_t>(&map_out)),
-                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
-                  : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          }
-          buf ^= 1;
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[a]);
-      }
-    }
-    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    __syncwarp();
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(TMEM_COLS)
-                 : "memory");
-  }
-}
-
-// ----------------------------------------------------- paired (multicast) form
-// Two CTAs of a cluster compute the row tiles m and m + 1 of the same column
-// tile n.  Each loads its own row operand and HALF of the shared column
-// operand, multicasting that half into both CTAs' shared memory, so the pair
-// reads each column-operand byte from L2 once: two thirds of the operand L2
-// traffic of the single-CTA form, whose merge is bound by that traffic.
-// A stage is refilled only after both CTAs' MMAs have read it (each MMA warp
-// commits to the empty barrier of both CTAs).  The CTAs meet at a cluster
-// barrier at the start (barriers initialised) and at the end (no multicast
-// or remote arrive in flight toward an exiting CTA); every other wait is
-// bounded.
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                               int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-// KBB bytes of K per stage (the swizzle width) and NST stages: the operand
-// buffers hold NST * (2 * BM + 2 * BN) * KBB bytes (192 KB for 128 x 2,
-// 64 x 4 and 32 x 8); narrower, more numerous stages keep more of them in
-// flight while the tensor cores read one.
-template <int KIND, int KBB, int NST>
-__global__ void __launch_bounds__(192, 1)
-    merge_tc_pair_kernel(const __grid_constant__ CUtensorMap map_r,
-                         const __grid_constant__ CUtensorMap map_c_half,
-                         const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
-                         int kblocks, int group_kb, int* err) {
-  constexpr int RT = BM * KBB, CT = BN * KBB, STB = 2 * RT + 2 * CT;
-  static_assert(NST * STB == STAGES * STAGE_BYTES, "operand buffers as the single-CTA form");
-  static_assert((2 * NST + 8) * 8 <= 256, "barrier area");
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stg_base = smem + NST * STB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
-  uint64_t* full = bars;                  // [NST]
-  uint64_t* empty = bars + NST;           // [NST], two arrivals: both CTAs' MMAs
-  uint64_t* tfull = bars + 2 * NST;       // [2]
-  uint64_t* tempty = bars + 2 * NST + 2;  // [2]
-  uint64_t* drain = bars + 2 * NST + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NST + 7);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = (int)cluster_rank();
-  const int tiles_n = n_cols / BN;
-  const int pairs_m = n_rows / (2 * BM);
-  const int n_units = pairs_m * tiles_n;
-  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
-  constexpr uint16_t kBoth = 0x3;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);
-    }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
-    }
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync();  // the partner's barriers exist before anything targets them
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-
-  // unit u -> (row-tile pair, column tile) in bands of kBand row tiles
-  auto unit_coords = [&](int u, int& m0, int& n0) {
-    int pm, pn;
-    const int band_pairs = kBand / 2;
-    const int band = u / (band_pairs * tiles_n), r = u - band * band_pairs * tiles_n;
-    const int rows = min(band_pairs, pairs_m - band * band_pairs);
-    pm = band * band_pairs + r % rows;
-    pn = r / rows;
-    m0 = (2 * pm + rank) * BM;
-    n0 = pn * BN;
-  };
-
-  if (warp == 0) {
-    if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_r)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c_half)) : "memory");
-      int s = 0;
-      uint32_t use = 0;
-      bool issued[NST];
-      uint32_t issued_parity[NST];
-      for (int i = 0; i < NST; ++i) {
-        issued[i] = false;
-        issued_parity[i] = 0;
-      }
-      bool ok = true;
-      const int kelem = KIND == CC_MERGE_BF16X3 ? KBB / 2 : KBB / 4;
-      for (int u = cluster; u < n_units && ok; u += n_clusters) {
-        int m0, n0;
-        unit_coords(u, m0, n0);
-        for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          unsigned char* st = smem + s * STB;
-          const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(&full[s], STB);
-          tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, m0);
-          tma_load_2d(smem_u32(st + RT), &map_r, fb, kb * kelem, n_rows + m0);
-          // this CTA's half of the column tile, into both CTAs
-          const int half = rank * (BN / 2);
-          tma_load_2d_mc(smem_u32(st + 2 * RT + half * KBB), &map_c_half, fb, kb * kelem,
-                         n0 + half, kBoth);
-          tma_load_2d_mc(smem_u32(st + 2 * RT + CT + half * KBB), &map_c_half, fb,
-                         kb * kelem, n_cols + n0 + half, kBoth);
-          issued[s] = true;
-          issued_parity[s] = use & 1;
-          if (++s == NST) {
-            s = 0;
-            ++use;
-          }
-        }
-      }
-      if (!ok) {
-        for (int i = 0; i < NST; ++i)
-          if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_value<KIND>();
-      int s = 0;
-      uint32_t use = 0;
-      int iter = 0;
-      bool ok = true;
-      bool any_mma = false;
-      for (int u = cluster; u < n_units && ok; u += n_clusters) {
-        for (int kb0 = 0; kb0 < kblocks && ok; kb0 += group_kb, ++iter) {
-          const int a = iter & 1;
-          if (!mbar_wait(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
-          const int kb1 = min(kblocks, kb0 + group_kb);
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * STB);
-            const uint64_t rh = sdesc_sw<KBB>(st), rl = sdesc_sw<KBB>(st + RT);
-            const uint64_t ch = sdesc_sw<KBB>(st + 2 * RT), cl = sdesc_sw<KBB>(st + 2 * RT + CT);
-#pragma unroll
-            for (int k = 0; k < KBB / 32; ++k) {
-              const uint64_t adv = (uint64_t)((k * 32) >> 4);
-              umma<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
-              umma<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
-              umma<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
-            }
-            any_mma = true;
-            umma_commit_mc(&empty[s], kBoth);  // both CTAs may refill the stage once both read it
-            if (++s == NST) {
-              s = 0;
-              ++use;
-            }
-          }
-          if (!ok) break;
-          umma_commit(&tfull[a]);
-        }
-      }
-      if (!ok && any_mma) {
-        umma_commit(drain);
-        mbar_drain(drain, 0);
-      }
-    }
-  } else {
-    const int quarter = warp & 3;
-    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
-    int buf = 0;
-    int iter = 0;
-    bool ok_all = true;
-    for (int u = cluster; u < n_units && ok_all; u += n_clusters) {
-      int m0, n0;
-      unit_coords(u, m0, n0);
-      for (int kb0 = 0; kb0 < kblocks; kb0 += group_kb, ++iter) {
-        const int a = iter & 1;
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-          ok_all = false;
-          break;
-        }
-        tc_fence_after();
-        const bool add = kb0 > 0;
-        if (add) {
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-          __syncwarp();
-        }
-        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
-#pragma unroll 1
-        for (int c2 = 0; c2 < BN / 32; c2 += 2) {
-          uint32_t rr[2][32];
-          tmem_ld32x2(tbase + (uint32_t)(c2 * 32), rr[0], rr[1]);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-          const int c = c2 + h;
-          uint32_t (&r)[32] = rr[h];
-          unsigned char* sb = stg + buf * STG_BYTES;
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          __syncwarp();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float4* dst = reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4));
-            *dst = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {
-            if (add)
-              asm volatile(
-                  "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group"
-                  " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(&map_out)),
-                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
-                  : "memory");
-            else
-              asm volatile(
-                  "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                      reinterpret_cast<uint64_t>(&map_out)),
-                  "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
-                  : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          }
-          buf ^= 1;
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[a]);
-      }
-    }
-    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    __syncwarp();
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync();  // neither CTA exits while the other may still target it
-  tc_fence_after();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(TMEM_COLS)
-                 : "memory");
-  }
-}
-
-// ------------------------------------------------- two-SM form (cta_group::2)
-// A cluster of two CTAs computes a 256 x 256 output tile with one tcgen05.mma
-// of M = 256 per K step, issued by the even CTA (the leader): each CTA holds
-// its 128 rows of the row operand and its 128 rows of the column operand, so
-// per stage an SM receives two thirds of the bytes of the multicast pair form
-// (the column tile is split between the CTAs instead of copied into both),
-// and three 64 KB stages (or six of 32 KB) fit where two 96 KB ones did.
-// Each CTA's loads complete on its own full barrier; the odd CTA's MMA warp,
-// idle otherwise, relays that completion to the leader (a remote arrive on
-// peer_ready), whose MMA thread waits on both.  The MMA commits arrive on
-// the empty and tfull barriers of both CTAs (multicast); each CTA drains its
-// own 128 TMEM lanes and both CTAs' epilogue warps release the accumulator
-// on the leader's tempty barrier.  TMEM is allocated by one warp of each CTA
-// (cta_group::2).  Every wait is bounded as in the other forms.
-__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
-}
-
-// Wait with cluster-scope acquire, for barriers the other CTA arrives on
-// (bounded like mbar_wait).
-__device__ __forceinline__ bool mbar_test_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort_flag, int* err) {
-  const long long t0 = clock64();
-  while (!mbar_test_cluster(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
-      *abort_flag = 1;
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
-}
-
-template <int KIND>
-__device__ __forceinline__ void umma2(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                      uint32_t accumulate) {
-  if (KIND == CC_MERGE_BF16X3) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-  }
-}
-__device__ __forceinline__ void umma2_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void umma2_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// Instruction descriptor of the two-SM MMA: FP32 accumulator, K-major A and
-// B, M = 256 (128 rows per CTA), N = 256.
-template <int KIND>
-__host__ __device__ constexpr uint32_t idesc2_value() {
-  return (1u << 4) | ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 7) |
-         ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)((2 * BM) >> 4) << 24);
-}
-
-template <int KIND, int KBB, int NST>
-__global__ void __launch_bounds__(192, 1)
-    merge_tc_2sm_kernel(const __grid_constant__ CUtensorMap map_r,
-                        const __grid_constant__ CUtensorMap map_c_half,
-                        const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
-                        int kblocks, int group_kb, int* err) {
-  constexpr int RT = BM * KBB, CT = (BN / 2) * KBB, STB = 2 * RT + 2 * CT;
-  static_assert(NST * STB <= STAGES * STAGE_BYTES, "operand buffers within the pair form's");
-  static_assert((3 * NST + 8) * 8 <= 256, "barrier area");
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stg_base = smem + NST * STB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
-  uint64_t* full = bars;                  // [NST] this CTA's loads
-  uint64_t* ready = bars + NST;           // [NST] leader: the peer's loads (relayed)
-  uint64_t* empty = bars + 2 * NST;       // [NST] the leader's MMA commit, both CTAs
-  uint64_t* tfull = bars + 3 * NST;       // [2]
-  uint64_t* tempty = bars + 3 * NST + 2;  // [2] leader: 8 epilogue warps of both CTAs
-  uint64_t* drain = bars + 3 * NST + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * NST + 6);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * NST + 7);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_rank();
-  const bool leader = rank == 0;
-  const int tiles_n = n_cols / BN;
-  const int pairs_m = n_rows / (2 * BM);
-  const int n_units = pairs_m * tiles_n;
-  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
-  constexpr uint16_t kBoth = 0x3;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&ready[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 8);
-    }
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 1) {  // one warp of each CTA of the pair allocates, collectively
-    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync();  // the partner's barriers and TMEM exist before anything targets them
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-
-  auto unit_coords = [&](int u, int& m0, int& n0) {  // m0: the pair's first row
-    const int band_pairs = kBand / 2;
-    const int band = u / (band_pairs * tiles_n), r = u - band * band_pairs * tiles_n;
-    const int rows = min(band_pairs, pairs_m - band * band_pairs);
-    m0 = (band * band_pairs + r % rows) * 2 * BM;
-    n0 = (r / rows) * BN;
-  };
-
-  if (warp == 0) {
-    if (lane == 0) {  // producer: this CTA's half of both operands
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_r)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_c_half)) : "memory");
-      int s = 0;
-      uint32_t use = 0;
-      bool issued[NST];
-      uint32_t issued_parity[NST];
-      for (int i = 0; i < NST; ++i) {
-        issued[i] = false;
-        issued_parity[i] = 0;
-      }
-      bool ok = true;
-      const int kelem = KIND == CC_MERGE_BF16X3 ? KBB / 2 : KBB / 4;
-      const int half = (int)rank * (BN / 2);
-      for (int u = cluster; u < n_units && ok; u += n_clusters) {
-        int m0, n0;
-        unit_coords(u, m0, n0);
-        const int my_rows = m0 + (int)rank * BM;
-        for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          unsigned char* st = smem + s * STB;
-          const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(&full[s], STB);
-          tma_load_2d(smem_u32(st), &map_r, fb, kb * kelem, my_rows);
-          tma_load_2d(smem_u32(st + RT), &map_r, fb, kb * kelem, n_rows + my_rows);
-          tma_load_2d(smem_u32(st + 2 * RT), &map_c_half, fb, kb * kelem, n0 + half);
-          tma_load_2d(smem_u32(st + 2 * RT + CT), &map_c_half, fb, kb * kelem, n_cols + n0 + half);
-          issued[s] = true;
-          issued_parity[s] = use & 1;
-          if (++s == NST) {
-            s = 0;
-            ++use;
-          }
-        }
-      }
-      if (!ok) {
-        for (int i = 0; i < NST; ++i)
-          if (issued[i]) mbar_drain(&full[i], issued_parity[i]);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0 && !leader) {  // relay: this CTA's loads landed -> the leader may read them
-      int s = 0;
-      uint32_t use = 0;
-      for (int u = cluster; u < n_units; u += n_clusters) {
-        bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
-          if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_remote(mapa_rank(smem_u32(&ready[s]), 0));
-          if (++s == NST) {
-            s = 0;
-            ++use;
-          }
-        }
-        if (!ok) break;
-      }
-    } else if (lane == 0) {  // the leader's MMA issuer
-      constexpr uint32_t idesc = idesc2_value<KIND>();
-      int s = 0;
-      uint32_t use = 0;
-      int iter = 0;
-      bool ok = true;
-      bool any_mma = false;
-      for (int u = cluster; u < n_units && ok; u += n_clusters) {
-        for (int kb0 = 0; kb0 < kblocks && ok; kb0 += group_kb, ++iter) {
-          const int a = iter & 1;
-          if (!mbar_wait_cluster(&tempty[a], ((iter >> 1) & 1) ^ 1, abort_flag, err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t dtmem = tmem_base + (uint32_t)(a * BN);
-          const int kb1 = min(kblocks, kb0 + group_kb);
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(&full[s], use & 1, abort_flag, err) ||
-                !mbar_wait_cluster(&ready[s], use & 1, abort_flag, err)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * STB);
-            const uint64_t rh = sdesc_sw<KBB>(st), rl = sdesc_sw<KBB>(st + RT);
-            const uint64_t ch = sdesc_sw<KBB>(st + 2 * RT), cl = sdesc_sw<KBB>(st + 2 * RT + CT);
-#pragma unroll
-            for (int k = 0; k < KBB / 32; ++k) {
-              const uint64_t adv = (uint64_t)((k * 32) >> 4);
-              umma2<KIND>(dtmem, rh + adv, ch + adv, idesc, ((kb - kb0) | k) != 0);
-              umma2<KIND>(dtmem, rh + adv, cl + adv, idesc, 1);
-              umma2<KIND>(dtmem, rl + adv, ch + adv, idesc, 1);
-            }
-            any_mma = true;
-            umma2_commit_mc(&empty[s], kBoth);  // both CTAs may refill the stage
-            if (++s == NST) {
-              s = 0;
-              ++use;
-            }
-          }
-          if (!ok) break;
-          umma2_commit_mc(&tfull[a], kBoth);
-        }
-      }
-      if (!ok && any_mma) {
-        umma2_commit(drain);
-        mbar_drain(drain, 0);
-      }
-    }
-  } else {
-    const int quarter = warp & 3;
-    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
-    int buf = 0;
-    int iter = 0;
-    bool ok_all = true;
-    const uint32_t tempty_leader[2] = {mapa_rank(smem_u32(&tempty[0]), 0),
-                                       mapa_rank(smem_u32(&tempty[1]), 0)};
-    for (int u = cluster; u < n_units && ok_all; u += n_clusters) {
-      int m0, n0;
-      unit_coords(u, m0, n0);
-      const int my_rows = m0 + (int)rank * BM;
-      for (int kb0 = 0; kb0 < kblocks; kb0 += group_kb, ++iter) {
-        const int a = iter & 1;
-        int ok = 1;
-        if (lane == 0) ok = mbar_wait(&tfull[a], (iter >> 1) & 1, abort_flag, err) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-          ok_all = false;
-          break;
-        }
-        tc_fence_after();
-        const bool add = kb0 > 0;
-        if (add) {
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-          __syncwarp();
-        }
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
         for (int c2 = 0; c2 < BN / 32; c2 += 2) {
@@ -1049,7 +424,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int c = c2 + h;
-            uint32_t (&r)[32] = rr[h];
+            uint32_t(&r)[32] = rr[h];
             unsigned char* sb = stg + buf * STG_BYTES;
             if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
             __syncwarp();
@@ -1066,13 +441,13 @@ __global__ void __launch_bounds__(192, 1)
                 asm volatile(
                     "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group"
                     " [%0, {%2, %3}], [%1];" ::"l"(reinterpret_cast<uint64_t>(&map_out)),
-                    "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(my_rows + quarter * 32)
+                    "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
                     : "memory");
               else
                 asm volatile(
                     "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
                         reinterpret_cast<uint64_t>(&map_out)),
-                    "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(my_rows + quarter * 32)
+                    "r"(smem_u32(sb)), "r"(n0 + c * 32), "r"(m0 + quarter * 32)
                     : "memory");
               asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
@@ -1081,10 +456,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {  // release the accumulator on the leader
-          if (leader) mbar_arrive(&tempty[a]);
-          else mbar_arrive_remote(tempty_leader[a]);
-        }
+        if (lane == 0) mbar_arrive(&tempty[a]);
       }
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -1093,10 +465,9 @@ __global__ void __launch_bounds__(192, 1)
 
   tc_fence_before();
   __syncthreads();
-  cluster_sync();  // neither CTA exits while the other may still target it
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(TMEM_COLS)
                  : "memory");
   }
@@ -1437,22 +808,15 @@ bool tc_stationary_requested() {
   return e && e[0] == '1';
 }
 
-// The paired multicast form (two CTAs per column tile) is the default where
-// the row tiles pair up; CUTSIM_TC_PAIR=0 selects the single-CTA form.
-bool tc_pair_requested() {
-  const char* e = std::getenv("CUTSIM_TC_PAIR");
-  return !(e && e[0] == '0');
-}
-
-// Bytes of K per stage of the paired form (2, 4 or 8 stages for 128, 64 or
-// 32).  Measured at q = 30 (merge ms, 128-byte / 64-byte blocks): a K loop of
-// 4 to 8 128-byte blocks per tile runs faster in four 64-byte stages (3xTF32
-// K = 64: 2.64 / 2.41, K = 128: 4.67 / 4.64; split-BF16 K = 128: 2.72 /
-// 2.50); shorter and longer loops run faster in two 128-byte stages (3xTF32
-// K = 32: 1.55 / 1.62, K = 256: 8.76 / 9.36; split-BF16 K = 64: 1.59 /
-// 1.65).  32-byte blocks were slower everywhere.  CUTSIM_TC_KBLOCK = 128,
-// 64 or 32 overrides.
-int tc_pair_kblock(int kblocks128) {
+// Bytes of K per stage (2, 4 or 8 stages for 128, 64 or 32).  Measured at
+// q = 30 with the earlier two-CTA form of this kernel (merge ms, 128-byte /
+// 64-byte blocks): a K loop of 4 to 8 128-byte blocks per tile ran faster in
+// four 64-byte stages (3xTF32 K = 64: 2.64 / 2.41, K = 128: 4.67 / 4.64;
+// split-BF16 K = 128: 2.72 / 2.50); shorter and longer loops ran faster in two
+// 128-byte stages (3xTF32 K = 32: 1.55 / 1.62, K = 256: 8.76 / 9.36;
+// split-BF16 K = 64: 1.59 / 1.65).  32-byte blocks were slower everywhere.
+// CUTSIM_TC_KBLOCK = 128, 64 or 32 overrides.
+int tc_kblock(int kblocks128) {
   const char* e = std::getenv("CUTSIM_TC_KBLOCK");
   if (e) {
     const int v = std::atoi(e);
@@ -1466,24 +830,11 @@ CUtensorMapSwizzle swizzle_of(int kbb) {
                     : kbb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
 }
 
-// CUTSIM_TC_2SM=1 selects the two-SM (cta_group::2) form where the paired
-// form would run.
-bool tc_2sm_requested() {
-  const char* e = std::getenv("CUTSIM_TC_2SM");
-  return e && e[0] == '1';
-}
-
 template <int KIND>
-void* two_sm_kernel_ptr(int kbb) {
-  if (kbb == 128) return reinterpret_cast<void*>(merge_tc_2sm_kernel<KIND, 128, 3>);
-  return reinterpret_cast<void*>(merge_tc_2sm_kernel<KIND, 64, 6>);
-}
-
-template <int KIND>
-void* pair_kernel_ptr(int kbb) {
-  if (kbb == 128) return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 128, 2>);
-  if (kbb == 64) return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 64, 4>);
-  return reinterpret_cast<void*>(merge_tc_pair_kernel<KIND, 32, 8>);
+void* tc_kernel_ptr(int kbb) {
+  if (kbb == 128) return reinterpret_cast<void*>(merge_tc_kernel<KIND, 128, 2>);
+  if (kbb == 64) return reinterpret_cast<void*>(merge_tc_kernel<KIND, 64, 4>);
+  return reinterpret_cast<void*>(merge_tc_kernel<KIND, 32, 8>);
 }
 
 int kr_of(int64_t K, int form) {
@@ -1560,27 +911,26 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand) failed");
   }
 
-  // The paired form reads K blocks of pkb bytes (its own swizzle width) and
-  // half a column tile per CTA.
-  const int pkb = tc_pair_kblock(KR * eb / KB_BYTES);
-  CUtensorMap map_r_pair, map_c_half;
+  // The streaming form reads K blocks of kbb bytes (its own swizzle width).
+  const int kbb = tc_kblock(KR * eb / KB_BYTES);
+  CUtensorMap map_r_k, map_c_k;
   {
     const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(2 * NB)};
     const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
-    const cuuint32_t box[2] = {(cuuint32_t)(pkb / eb), (cuuint32_t)BM};
-    if (enc(&map_r_pair, dt, 2, r_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            swizzle_of(pkb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint32_t box[2] = {(cuuint32_t)(kbb / eb), (cuuint32_t)BM};
+    if (enc(&map_r_k, dt, 2, r_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle_of(kbb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (row operand, paired form) failed");
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (row operand, K blocks) failed");
   }
   {
     const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(4 * NA)};
     const cuuint64_t strides[1] = {(cuuint64_t)KR * eb};
-    const cuuint32_t box[2] = {(cuuint32_t)(pkb / eb), (cuuint32_t)(BN / 2)};
-    if (enc(&map_c_half, dt, 2, c_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            swizzle_of(pkb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint32_t box[2] = {(cuuint32_t)(kbb / eb), (cuuint32_t)BN};
+    if (enc(&map_c_k, dt, 2, c_ops, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle_of(kbb), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand half) failed");
+      return fail(CC_ECUDA, "cuTensorMapEncodeTiled (column operand, K blocks) failed");
   }
 
   {
@@ -1597,15 +947,11 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     cudaFuncSetAttribute(merge_tc_rs_kernel<CC_MERGE_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    for (int kbb = 32; kbb <= 128; kbb *= 2) {
-      cudaFuncSetAttribute(pair_kernel_ptr<CC_MERGE_BF16X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      cudaFuncSetAttribute(pair_kernel_ptr<CC_MERGE_TF32X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      cudaFuncSetAttribute(two_sm_kernel_ptr<CC_MERGE_BF16X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      cudaFuncSetAttribute(two_sm_kernel_ptr<CC_MERGE_TF32X3>(kbb), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    for (int b = 32; b <= 128; b *= 2) {
+      cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_BF16X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_TF32X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     }
     attr_done[dev] = 1;
   }
@@ -1627,44 +973,17 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_rs_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
     kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
-  } else if (tc_pair_requested() && (n_rows / BM) % 2 == 0 && num_sms() >= 2) {
-    const bool two_sm = tc_2sm_requested() && (n_cols / BN) > 0 && pkb != 32;
-    const void* kern = two_sm ? (form == CC_MERGE_BF16X3 ? two_sm_kernel_ptr<CC_MERGE_BF16X3>(pkb)
-                                                         : two_sm_kernel_ptr<CC_MERGE_TF32X3>(pkb))
-                              : (form == CC_MERGE_BF16X3 ? pair_kernel_ptr<CC_MERGE_BF16X3>(pkb)
-                                                         : pair_kernel_ptr<CC_MERGE_TF32X3>(pkb));
-    const int pkblocks = KR * eb / pkb;
-    const int pgroup_kb = form == CC_MERGE_TF32X3
-                              ? std::max(1, (int)(2 * kTf32GroupTerms * eb / pkb))
-                              : pkblocks;
-    const int n_units = (n_rows / (2 * BM)) * (n_cols / BN);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * std::min(n_units, num_sms() / 2)), 1, 1);
-    cfg.blockDim = dim3(192, 1, 1);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int a_rows = n_rows, a_cols = n_cols, a_kb = pkblocks, a_gkb = std::min(pgroup_kb, pkblocks);
-    void* args[] = {&map_r_pair, &map_c_half, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err};
-    const cudaError_t le = cudaLaunchKernelExC(&cfg, kern, args);
-    if (le != cudaSuccess) {  // no room for 2-CTA clusters here: the single-CTA form
-      cudaGetLastError();
-      auto k1 = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
-                                        : merge_tc_kernel<CC_MERGE_TF32X3>;
-      k1<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks,
-                                       std::min(group_kb, kblocks), err);
-    }
   } else {
-    auto kern = form == CC_MERGE_BF16X3 ? merge_tc_kernel<CC_MERGE_BF16X3>
-                                        : merge_tc_kernel<CC_MERGE_TF32X3>;
-    kern<<<grid, 192, SMEM_BYTES, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks,
-                                       std::min(group_kb, kblocks), err);
+    const void* kern = form == CC_MERGE_BF16X3 ? tc_kernel_ptr<CC_MERGE_BF16X3>(kbb)
+                                               : tc_kernel_ptr<CC_MERGE_TF32X3>(kbb);
+    const int kb_n = KR * eb / kbb;
+    const int gkb = form == CC_MERGE_TF32X3 ? std::max(1, (int)(2 * kTf32GroupTerms * eb / kbb))
+                                            : kb_n;
+    int a_rows = n_rows, a_cols = n_cols, a_kb = kb_n, a_gkb = std::min(gkb, kb_n);
+    void* args[] = {&map_r_k, &map_c_k, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err};
+    const cudaError_t le = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(192), args, SMEM_BYTES, s);
+    if (le != cudaSuccess)
+      return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(le));
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(e));

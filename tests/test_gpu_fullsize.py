@@ -68,6 +68,9 @@ def test_q30_n2_c6_bench_workload_sampled_and_vs_uncut(cuda_lib):
     (26, 2, 8, "projector", "c128", "fma"),
     (26, 3, 4, "s_sdg", "c128", "auto"),
     (30, 2, 8, "projector", "c64", "tf32x3"),   # K = 256: grouped 3xTF32
+    (28, 2, 6, "projector", "c128", "auto"),    # complex128 at the larger sizes
+    (28, 3, 4, "s_sdg", "c128", "auto"),
+    (30, 2, 6, "projector", "c128", "auto"),    # 16 GiB complex128 output
     (32, 2, 4, "projector", "c64", "auto"),     # 32 GiB output, the largest case here
 ])
 def test_sampled_parity_at_scale(cuda_lib, q, n, c, decomp, prec, form):

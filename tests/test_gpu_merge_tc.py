@@ -108,41 +108,22 @@ def test_tc_forms_stationary_and_streaming(cuda_lib, monkeypatch, stationary, fo
     assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
 
 
-@pytest.mark.parametrize("kblock", ["128", "64", "32"])
 @pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
 @pytest.mark.parametrize("segs,c", [([7, 8], 4), ([9, 10], 6), ([10, 9], 8), ([8, 11], 5),
                                     ([9, 9], 10)])
-def test_tc_pair_form(cuda_lib, monkeypatch, kblock, form, segs, c):
-    # two CTAs of a cluster share each column tile by TMA multicast (the
-    # default), streaming K in blocks of 128, 64 or 32 bytes (2, 4 or 8
-    # stages); CUTSIM_TC_PAIR=0 selects the single-CTA kernel
-    monkeypatch.delenv("CUTSIM_TC_PAIR", raising=False)
-    monkeypatch.setenv("CUTSIM_TC_KBLOCK", kblock)
+def test_tc_kblock_forms(cuda_lib, monkeypatch, form, segs, c):
+    # the streaming kernel with K in blocks of 128, 64 or 32 bytes (2, 4 or 8
+    # stages of the same 192 KB) against the oracle; every block width issues
+    # the same products in the same order per tile, so the bits agree
     q = sum(segs)
     gates = w.brickwork_cut(q, 12, 41 + c, segs, c)
-    psi, _ = run(gates, q, segs, form)
     ref = sv.simulate(q, gates)
-    assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
-    monkeypatch.setenv("CUTSIM_TC_PAIR", "0")
-    psi_single, _ = run(gates, q, segs, form)
-    # the same products in the same order per tile: identical bits
-    assert torch.equal(psi, psi_single)
-
-
-@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
-@pytest.mark.parametrize("segs,c", [([9, 10], 6), ([10, 9], 8), ([8, 11], 5), ([9, 9], 10),
-                                    ([8, 8], 7)])
-def test_tc_two_sm_form(cuda_lib, monkeypatch, form, segs, c):
-    # CUTSIM_TC_2SM=1: one M = 256 tcgen05.mma per K step over a CTA pair
-    # (cta_group::2), each CTA holding half of the column tile; against the
-    # oracle, and against the paired multicast form, which sums the same
-    # products in the same order
-    monkeypatch.setenv("CUTSIM_TC_2SM", "1")
-    q = sum(segs)
-    gates = w.brickwork_cut(q, 12, 61 + c, segs, c)
-    psi, _ = run(gates, q, segs, form)
-    ref = sv.simulate(q, gates)
-    assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
-    monkeypatch.setenv("CUTSIM_TC_2SM", "0")
-    psi_pair, _ = run(gates, q, segs, form)
-    assert rel_err(psi.cpu().numpy(), psi_pair.cpu().numpy()) <= 1e-6
+    first = None
+    for kblock in ("128", "64", "32"):
+        monkeypatch.setenv("CUTSIM_TC_KBLOCK", kblock)
+        psi, _ = run(gates, q, segs, form)
+        assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form], kblock
+        if first is None:
+            first = psi
+        else:
+            assert torch.equal(psi, first), kblock

@@ -62,3 +62,48 @@ def test_static_gather_rejects_oversized_requests(cuda_lib):
     assert b"maximum" in L.cc_last_error()
     st, _ = call(L.cc_gather_static, psi, [1 << 20], "c64")
     assert st == 2
+
+
+_FRESH = r"""
+import ctypes, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2603_01443_gb300 import capi
+L = capi.lib()
+psi = torch.randn(1 << 20, dtype=torch.complex64, device="cuda")
+torch.cuda.synchronize()
+idx = np.arange(0, 1 << 20, 17, dtype=np.int64)[:65536]
+out = np.empty(len(idx), dtype=np.complex64)
+def once():
+    st = L.cc_gather_static(ctypes.c_void_p(psi.data_ptr()), psi.numel(), 0,
+                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx),
+                            out.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, L.cc_last_error()
+once()  # the first library call in the process: loads the module (and its array)
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+for _ in range(8):
+    once()
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+assert np.array_equal(out, psi.cpu().numpy()[idx])
+print("FREE", free0, free1)
+"""
+
+
+def test_static_gather_allocates_nothing_in_fresh_process(cuda_lib):
+    # In a process where cc_gather_static is the first library call, repeated
+    # calls leave the device's free memory unchanged: no scratch area grows.
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    line = [x for x in r.stdout.splitlines() if x.startswith("FREE")][-1]
+    _, free0, free1 = line.split()
+    assert int(free0) == int(free1), line
