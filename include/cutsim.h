@@ -76,14 +76,25 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  * CC_MERGE_BF16X3  : tcgen05 tensor cores, kind::f16 with bf16 operands, the
  *                    same three-product split, FP32 accumulation (CC_C64,
  *                    factors >= 2^7; max|dpsi|/max|psi| <= 5e-5).
- * CC_MERGE_AUTO    : TF32X3 where it applies and K >= 8, else FMA.
+ * CC_MERGE_OZAKI   : complex128 on tcgen05 tensor cores (CC_C128 plans, both
+ *                    factors >= 2^7 amplitudes): every operand row scaled by a
+ *                    power of two and cut into 6 bf16 slices of 9 bits, the
+ *                    21 leading slice products accumulated in FP32 (the
+ *                    leading levels exactly) and summed exactly in 64-bit
+ *                    fixed point, then rounded once to FP64 (the Ozaki
+ *                    scheme: Ozaki, Ogita, Oishi, Rump 2012); long K adds its
+ *                    64-term groups exactly through the output buffer
+ *                    (max|dpsi|/max|psi| <= 1e-12).
+ * CC_MERGE_AUTO    : complex64: TF32X3 where it applies and K >= 8, else FMA;
+ *                    complex128: OZAKI where it applies, else FMA.
  * For n_seg >= 3 the form applies to the last (2^q-sized) stage of the chain;
  * the earlier, smaller stages always use FMA. */
 typedef enum {
   CC_MERGE_AUTO = 0,
   CC_MERGE_FMA = 1,
   CC_MERGE_TF32X3 = 2,
-  CC_MERGE_BF16X3 = 3
+  CC_MERGE_BF16X3 = 3,
+  CC_MERGE_OZAKI = 4
 } cc_merge_form;
 
 typedef enum {

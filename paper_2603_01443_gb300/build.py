@@ -21,7 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcutsim.so")
 
-CU_SOURCES = ["runtime.cu", "sv_kernels.cu", "merge_kernels.cu", "merge_tc.cu", "reduce_kernels.cu",
+CU_SOURCES = ["runtime.cu", "sv_kernels.cu", "merge_kernels.cu", "merge_tc.cu", "merge_ozaki.cu",
+              "reduce_kernels.cu",
               "batch.cu", "mlp.cu",
               "gather_static.cu"]
 CPP_SOURCES = ["program.cpp", "plan.cpp"]

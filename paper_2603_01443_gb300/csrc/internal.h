@@ -222,6 +222,9 @@ enum : int32_t { BUF_SEG = 0, BUF_WORK = 1, BUF_PSI = 2 };
 // CUDA-core form is store-bound through K = 4 and slower from K = 8 on
 // (K = 8: 2.03 ms FMA, 1.64 ms 3xTF32).
 constexpr int64_t kAutoTcMinTerms = 8;
+// CC_MERGE_AUTO merges complex128 plans with the Ozaki tensor-core form from
+// this many terms on (both factors >= 2^7 amplitudes).
+constexpr int64_t kAutoOzakiMinTerms = 2;
 struct BMergeJob {
   int32_t a_buf, b_buf, out_buf, kind;  // kind: 0 tiled, 1 flat
   int64_t a_off, b_off, out_off;
@@ -266,6 +269,12 @@ cc_status launch_merge_fma(const MergeStage& st, int precision, void* stream);
 uint64_t merge_tc_workspace_bytes(int qa, int qb, int64_t K, int form);
 cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint64_t ws_bytes,
                           void* stream);
+
+// Complex128 tensor-core merge (Ozaki scheme, merge_ozaki.cu): same shapes as
+// the tensor-core merge; returns 0 bytes / CC_EUNSUPPORTED where it does not apply.
+uint64_t merge_ozaki_workspace_bytes(int qa, int qb, int64_t K);
+cc_status launch_merge_ozaki(const MergeStage& st, void* workspace, uint64_t ws_bytes,
+                             void* stream);
 
 // ----------------------------------------------------------- reductions
 cc_status launch_compare(const void* a, const void* b, int64_t n, int precision, double* out_dev,

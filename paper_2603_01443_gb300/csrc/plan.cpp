@@ -300,7 +300,8 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
       const auto& last = p->stages.back();
       const uint64_t tc = std::max(merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_TF32X3),
                                    merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_BF16X3));
-      p->workspace_bytes = 2 * u_max * ab + (precision == CC_C64 ? tc : 0);
+      const uint64_t oz = merge_ozaki_workspace_bytes(last.qa, last.qb, last.K);
+      p->workspace_bytes = 2 * u_max * ab + (precision == CC_C64 ? tc : oz);
     }
     // All device tables of the plan (gate programs, merge index tables) go up
     // in one allocation and one copy.  Everything above is host work; the

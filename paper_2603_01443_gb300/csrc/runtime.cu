@@ -285,9 +285,11 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
     return fail(CC_EINVAL, "buffers must be 16-byte aligned");
   if (seg_bytes < p->seg_buf_bytes) return fail(CC_EBUFSIZE, "seg_buf too small");
   if (psi_bytes < p->psi_bytes) return fail(CC_EBUFSIZE, "psi too small");
-  if (form < CC_MERGE_AUTO || form > CC_MERGE_BF16X3) return fail(CC_EINVAL, "unknown merge form");
+  if (form < CC_MERGE_AUTO || form > CC_MERGE_OZAKI) return fail(CC_EINVAL, "unknown merge form");
   if ((form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3) && p->precision != CC_C64)
     return fail(CC_EINVAL, "tensor-core merge forms need a complex64 plan");
+  if (form == CC_MERGE_OZAKI && p->precision != CC_C128)
+    return fail(CC_EINVAL, "the Ozaki merge form needs a complex128 plan");
   cc_status st = check_device();
   if (st != CC_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -321,20 +323,27 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
     // AUTO: the CUDA-core form while the merge is store-bound (K below
     // kAutoTcMinTerms), else 3xTF32 (long K summed in groups of 64 terms, see
     // merge_tc.cu).
+    // complex128: the Ozaki tensor-core form wherever it applies.
     int f = form;
-    if (f == CC_MERGE_AUTO)
-      f = (p->precision == CC_C64 && sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7)
-              ? CC_MERGE_TF32X3
-              : CC_MERGE_FMA;
+    if (f == CC_MERGE_AUTO) {
+      if (p->precision == CC_C64)
+        f = (sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7) ? CC_MERGE_TF32X3 : CC_MERGE_FMA;
+      else
+        f = (sg.K >= kAutoOzakiMinTerms && sg.qa >= 7 && sg.qb >= 7) ? CC_MERGE_OZAKI
+                                                                       : CC_MERGE_FMA;
+    }
     if (f != CC_MERGE_FMA) {
       void* tc_ws = workspace ? static_cast<char*>(workspace) + 2 * half : nullptr;
       const uint64_t tc_bytes = ws_bytes > 2 * half ? ws_bytes - 2 * half : 0;
-      if (!tc_ws || tc_bytes < merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f)) {
+      const uint64_t need = f == CC_MERGE_OZAKI ? merge_ozaki_workspace_bytes(sg.qa, sg.qb, sg.K)
+                                                : merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, f);
+      if (!tc_ws || tc_bytes < need) {
         if (form != CC_MERGE_AUTO)
           return fail(CC_EBUFSIZE, "workspace too small for the tensor-core merge");
         f = CC_MERGE_FMA;
       } else {
-        st = launch_merge_tc(ms, f, tc_ws, tc_bytes, stream);
+        st = f == CC_MERGE_OZAKI ? launch_merge_ozaki(ms, tc_ws, tc_bytes, stream)
+                                 : launch_merge_tc(ms, f, tc_ws, tc_bytes, stream);
         if (st == CC_OK) return CC_OK;
         if (st != CC_EUNSUPPORTED || form != CC_MERGE_AUTO) return st;
         f = CC_MERGE_FMA;
