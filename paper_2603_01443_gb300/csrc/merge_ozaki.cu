@@ -17,34 +17,37 @@
 //
 // Products.  The tensor cores form the slice products (i, j) with
 // i + j <= 5 (21 products; the dropped ones are below 2^-50 of the row
-// scales' product) and accumulate them in FP32 in four TMEM accumulators:
-// level 0 (i + j = 0), level 1, level 2, and levels 3-5 together.  A level-L
-// product is an integer times 2^(-9 L), at most 2^16 in magnitude, so over an
-// accumulation group of at most 128 real K elements level 0 sums integers
-// below 2^23 and level 1 multiples of 2^-9 below 2^15: FP32 holds every
-// partial sum exactly.  Level 2 is exact while its partial sums stay below
-// 2^24 units (3 x 128 products of at most 2^16; balanced digits make that
-// sure in practice); the merged levels 3-5 carry an FP32 rounding error
-// below 2^-40 of the scales' product.
+// scales' product) and accumulate them in FP32 in TMEM, one accumulator per
+// level L = i + j for the leading levels and one for the remaining levels
+// together.  A level-L product is an integer times 2^(-9 L), at most 2^16 in
+// magnitude, so over an accumulation group of at most 128 real K elements
+// level 0 sums integers below 2^23 and level 1 multiples of 2^-9 below 2^15:
+// FP32 holds every partial sum exactly.  Levels 2 and 3 are exact while their
+// partial sums stay below 2^24 units ((L + 1) x 128 products of at most 2^16;
+// balanced digits keep them near 2^20 in practice).  Only the merged
+// accumulator rounds: with four accumulators (levels 0, 1, 2, then 3-5) its
+// rounding reaches a few 1e-13 of max |psi| by 256 terms; with five (levels
+// 0-3, then 4-5) it stays near 2e-14 at any K.
 //
-// Epilogue.  Per output element the four accumulators become one exact
-// 64-bit fixed-point integer with 30 fractional bits,
-//   I = a0 2^30 + a1 2^30 + a2 2^30 + round(a3 2^30),
+// Epilogue.  Per output element the accumulators become one exact 64-bit
+// fixed-point integer (30 or 33 fraction bits below the level-0 unit),
 // longer K adds the integers of its 128-element groups exactly (the partial
 // sum round-trips through the output buffer as int64), and the last group
-// converts I 2^(e_y + f_n - 46) to FP64 with one rounding, built from the
-// integer bits (no FP64 arithmetic anywhere in the kernel).
+// rounds I 2^(e_y + f_n - 16 - fraction bits) to FP64 once.
 //
-// Kernel structure (one CTA per SM, persistent over 128 x 128 output tiles,
+// Kernel structure (one CTA per SM, persistent over 128 x BN output tiles,
 // bands of 16 row tiles):
 //   warp 0      TMA producer: per K block one 3-D load of the 6 row-operand
 //               slices (128 rows) and one of the 6 column-operand slices
-//               (128 rows) into one of NST shared-memory stages;
-//   warp 1      allocates the 512 TMEM columns (4 accumulators of 128) and one
-//               lane issues the 21 x (K block / 16) tcgen05.mma of a stage;
-//   warps 2..5  epilogue: tcgen05.ld of the four accumulators in 16-column
-//               chunks, fixed-point sum, FP64 assembly, 128-byte-swizzled
-//               staging and bulk tensor stores.
+//               (BN rows) into one of NST shared-memory stages;
+//   warp 1      allocates TMEM (NACC accumulators of BN columns, one or two
+//               sets) and one lane issues the 21 x (K block / 16) tcgen05.mma
+//               of a stage;
+//   warps 2..   epilogue (4 or 8 warps): tcgen05.ld of the accumulators in
+//               16-column chunks, fixed-point sum, FP64 conversion,
+//               128-byte-swizzled staging and bulk tensor stores; with two
+//               accumulator sets the epilogue of one tile overlaps the MMAs
+//               of the next.
 // Every mbarrier wait is bounded as in merge_tc.cu: on expiry the kernel
 // raises the device error flag, drains its own copies and MMAs and frees TMEM.
 #include <cuda.h>
@@ -68,18 +71,10 @@ using namespace tcg;
 constexpr int OZ_S = 6;           // slices per operand
 constexpr int OZ_BETA = 9;        // bits per slice
 constexpr int OZ_LEVELS = 6;      // products (i, j) with i + j < OZ_LEVELS
-constexpr int OZ_NACC = 4;        // TMEM accumulators: levels 0, 1, 2, 3..5
 constexpr int OZ_BM = 128;        // output rows per tile
-constexpr int OZ_BN = 128;        // output real columns per tile
 constexpr int OZ_GROUP_K = 128;   // real K elements per accumulation group
-constexpr int OZ_FIX = 30;        // fraction bits of the epilogue's fixed point
 constexpr int OZ_STG_BYTES = 32 * 128;              // one store box: 32 rows x 16 FP64
-constexpr int OZ_STG_TOTAL = 4 * 2 * OZ_STG_BYTES;  // 4 epilogue warps x 2 buffers
-constexpr int OZ_OPERANDS = 2 * 96 * 1024;          // operand stages: 192 KB
-constexpr int OZ_SMEM = OZ_OPERANDS + OZ_STG_TOTAL + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int OZ_TMEM_COLS = 512;
 constexpr int OZ_BAND = 16;
-static_assert(OZ_NACC * OZ_BN <= OZ_TMEM_COLS, "accumulators fit in TMEM");
 
 // Row exponent of a zero row: every digit is 0 and so is every product.
 constexpr int32_t OZ_ZERO_EXP = -4000;
@@ -160,16 +155,44 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------ main kernel
-__device__ __forceinline__ void oz_tile_coords(int t, int tiles_m, int tiles_n, int& m0, int& n0) {
+// A kernel configuration: K bytes per stage KBB, NST stages, BN output
+// columns per tile, NACC TMEM accumulators (levels 0 .. NACC - 2 each in
+// its own, exact; the remaining levels merged in the last), NBUF sets of
+// them (2: the epilogue of one tile overlaps the MMAs of the next).
+template <int KBB, int NST, int BN, int NACC, int NBUF, int EW>
+struct OzCfg {
+  static constexpr int KEL = KBB / 2;                  // bf16 elements of K per stage
+  static constexpr int AS = OZ_BM * KBB;               // one row-operand slice per stage
+  static constexpr int BS = BN * KBB;                  // one column-operand slice per stage
+  static constexpr int STB = OZ_S * (AS + BS);         // one stage
+  static constexpr int STG = EW * 2 * OZ_STG_BYTES;     // epilogue staging: 2 boxes per warp
+  static constexpr int SMEM = NST * STB + STG + 1024 + 256;
+  static constexpr int THREADS = 64 + 32 * EW;
+  static constexpr int COLS_PER_WARP = BN / (EW / 4);  // each TMEM lane quarter split EW / 4 ways
+  static constexpr int COLS = NACC * BN * NBUF;
+  static constexpr int TMEM = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128
+                            : COLS <= 256 ? 256 : 512;
+  // fixed-point fraction bits: the exact levels' units down to 2^-(9 (NACC - 2)),
+  // plus a margin for the merged level's rounding
+  static constexpr int FIX = NACC == 4 ? 30 : 33;
+  static_assert(COLS <= 512, "accumulators fit in TMEM");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static_assert(NACC == 4 || NACC == 5, "4 or 5 accumulators");
+  static_assert((EW == 4 || EW == 8) && COLS_PER_WARP % 16 == 0, "epilogue warps");
+};
+
+__device__ __forceinline__ void oz_tile_coords(int t, int tiles_m, int tiles_n, int bn, int& m0,
+                                               int& n0) {
   const int band = t / (OZ_BAND * tiles_n), r = t - band * OZ_BAND * tiles_n;
   const int rows = min(OZ_BAND, tiles_m - band * OZ_BAND);
   m0 = (band * OZ_BAND + r % rows) * OZ_BM;
-  n0 = (r / rows) * OZ_BN;
+  n0 = (r / rows) * bn;
 }
 
-// Instruction descriptor: FP32 accumulator, bf16 A and B (K-major), M = 128, N = 128.
+// Instruction descriptor: FP32 accumulator, bf16 A and B (K-major), M = 128, N = BN.
+template <int BN>
 constexpr uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
          ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
@@ -183,26 +206,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
-// The exact fixed-point value of one output element, in units of 2^-OZ_FIX of
-// the level-0 unit: a0, a1, a2 are exact multiples of 1, 2^-9, 2^-18.
-__device__ __forceinline__ long long oz_fixed(float a0, float a1, float a2, float a3) {
-  const long long i0 = __float2ll_rn(a0);
-  const long long i1 = __float2ll_rn(a1 * 0x1p9f);
-  const long long i2 = __float2ll_rn(a2 * 0x1p18f);
-  const long long i3 = __float2ll_rn(a3 * 0x1p30f);
-  return (i0 << OZ_FIX) + (i1 << (OZ_FIX - OZ_BETA)) + (i2 << (OZ_FIX - 2 * OZ_BETA)) + i3;
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// The fixed-point value of one output element in units of 2^-FIX of the
+// level-0 unit.  Level L < NACC - 1 holds an integer times 2^(-9 L) below
+// 2^25 units; each converts to int32 exactly, the merged last level rounds.
+// The sum is formed with 32 x 32 -> 64-bit multiply-adds by powers of two.
+template <int NACC, int FIX>
+__device__ __forceinline__ long long oz_fixed(const float (&a)[NACC]) {
+  long long I = (long long)__float2int_rn(a[NACC - 1] * __int_as_float((127 + FIX) << 23));
+#pragma unroll
+  for (int L = NACC - 2; L >= 1; --L)
+    I = mad_wide(__float2int_rn(a[L] * __int_as_float((127 + OZ_BETA * L) << 23)),
+                 1 << (FIX - OZ_BETA * L), I);
+  // level 0: i0 2^FIX, FIX >= 30
+  const int i0 = __float2int_rn(a[0]);
+  return mad_wide(i0 << (FIX - 30), 1 << 30, I);
 }
 
 // FP64 bits of I 2^sc, rounded to nearest even, from the integer alone.
 __device__ __forceinline__ unsigned long long oz_to_f64(long long I, int sc) {
   if (I == 0) return 0ull;
-  const unsigned long long sign = I < 0 ? (1ull << 63) : 0ull;
-  const unsigned long long m = I < 0 ? (unsigned long long)(-I) : (unsigned long long)I;
+  const unsigned long long sign = (unsigned long long)I & (1ull << 63);
+  const unsigned long long m = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
   const int lz = __clzll((long long)m);
   const unsigned long long mn = m << lz;  // leading one at bit 63
   unsigned long long mant = mn >> 11;     // 53 bits, implicit one at bit 52
-  const unsigned long long rest = mn & 0x7FFull;
-  mant += (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+  const unsigned int rest = (unsigned int)mn & 0x7FFu;
+  mant += (rest > 0x400u || (rest == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
   const int E = 1023 + (63 - lz) + sc;  // biased exponent of the leading one
   if (E <= 0) return sign;              // below the normal range (never for state vectors)
   if (E >= 2047) return sign | 0x7FF0000000000000ull;
@@ -210,34 +245,43 @@ __device__ __forceinline__ unsigned long long oz_to_f64(long long I, int sc) {
   return sign | ((((unsigned long long)(E - 1)) << 52) + mant);
 }
 
-template <int KBB, int NST>
-__global__ void __launch_bounds__(192, 1)
+// The same value through the hardware conversion: I to FP64 (rounded to
+// nearest even), then 2^sc added to the exponent field (exact: the results
+// of a state-vector merge lie far inside the normal range).
+__device__ __forceinline__ unsigned long long oz_to_f64_cvt(long long I, int sc) {
+  if (I == 0) return 0ull;
+  double d;
+  asm("cvt.rn.f64.s64 %0, %1;" : "=d"(d) : "l"(I));
+  return (unsigned long long)__double_as_longlong(d) + ((unsigned long long)(long long)sc << 52);
+}
+
+template <int KBB, int NST, int BN, int NACC, int NBUF, int EW, int CVT>
+__global__ void __launch_bounds__(64 + 32 * EW, 1)
     merge_ozaki_kernel(const __grid_constant__ CUtensorMap map_r,
                        const __grid_constant__ CUtensorMap map_c,
                        const __grid_constant__ CUtensorMap map_out,
                        const int32_t* __restrict__ e_row, const int32_t* __restrict__ f_col,
                        const double* out, int n_rows, int n_cols, int kblocks, int group_kb,
                        int* err) {
-  constexpr int KEL = KBB / 2;                  // bf16 elements of K per stage
-  constexpr int AS = OZ_BM * KBB, BS = OZ_BN * KBB;  // one slice of each operand
-  constexpr int STB = OZ_S * (AS + BS);
-  static_assert(NST * STB == OZ_OPERANDS, "operand stages of 192 KB");
-  static_assert((2 * NST + 6) * 8 <= 256, "barrier area");
+  using Cfg = OzCfg<KBB, NST, BN, NACC, NBUF, EW>;
+  constexpr int KEL = Cfg::KEL, AS = Cfg::AS, BS = Cfg::BS, STB = Cfg::STB;
+  constexpr int FIX = Cfg::FIX;
+  static_assert((2 * NST + 2 * NBUF + 3) * 8 <= 256, "barrier area");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stg_base = smem + NST * STB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + OZ_STG_TOTAL);
-  uint64_t* full = bars;                // [NST]
-  uint64_t* empty = bars + NST;         // [NST]
-  uint64_t* tfull = bars + 2 * NST;     // the accumulators hold a finished group
-  uint64_t* tempty = bars + 2 * NST + 1;  // the epilogue has read them
-  uint64_t* drain = bars + 2 * NST + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 3);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NST + 4);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + Cfg::STG);
+  uint64_t* full = bars;                        // [NST]
+  uint64_t* empty = bars + NST;                 // [NST]
+  uint64_t* tfull = bars + 2 * NST;             // [NBUF] accumulator set holds a finished group
+  uint64_t* tempty = bars + 2 * NST + NBUF;     // [NBUF] the epilogue has read it
+  uint64_t* drain = bars + 2 * NST + 2 * NBUF;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_m = n_rows / OZ_BM, tiles_n = n_cols / OZ_BN;
+  const int tiles_m = n_rows / OZ_BM, tiles_n = n_cols / BN;
   const int n_tiles = tiles_m * tiles_n;
   const int n_groups = (kblocks + group_kb - 1) / group_kb;
 
@@ -246,8 +290,10 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, 4);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EW);
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -256,7 +302,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(OZ_TMEM_COLS)
+                 "r"(Cfg::TMEM)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -280,7 +326,7 @@ __global__ void __launch_bounds__(192, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int m0, n0;
-        oz_tile_coords(t, tiles_m, tiles_n, m0, n0);
+        oz_tile_coords(t, tiles_m, tiles_n, BN, m0, n0);
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[s], (use & 1) ^ 1, abort_flag, err)) {
             ok = false;
@@ -306,7 +352,7 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = oz_idesc();
+      constexpr uint32_t idesc = oz_idesc<BN>();
       int s = 0;
       uint32_t use = 0;
       int iter = 0;
@@ -314,12 +360,14 @@ __global__ void __launch_bounds__(192, 1)
       bool any_mma = false;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         for (int kb0 = 0; kb0 < kblocks && ok; kb0 += group_kb, ++iter) {
-          if (!mbar_wait(tempty, (iter & 1) ^ 1, abort_flag, err)) {
+          const int ab = iter % NBUF;
+          if (!mbar_wait(&tempty[ab], ((iter / NBUF) & 1) ^ 1, abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          uint32_t fresh = (1u << OZ_NACC) - 1;  // accumulators not yet written in this group
+          const uint32_t dbase = tmem_base + (uint32_t)(ab * NACC * BN);
+          uint32_t fresh = (1u << NACC) - 1;  // accumulators not yet written in this group
           const int kb1 = min(kblocks, kb0 + group_kb);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&full[s], use & 1, abort_flag, err)) {
@@ -336,12 +384,11 @@ __global__ void __launch_bounds__(192, 1)
                 const uint64_t a = sdesc_sw<KBB>(st + i * AS) + adv;
 #pragma unroll
                 for (int j = 0; j < OZ_LEVELS - i; ++j) {
-                  const int acc = min(i + j, OZ_NACC - 1);
+                  const int acc = min(i + j, NACC - 1);
                   const uint64_t b = sdesc_sw<KBB>(st + OZ_S * AS + j * BS) + adv;
                   const uint32_t accumulate = (fresh >> acc) & 1u ? 0u : 1u;
                   fresh &= ~(1u << acc);
-                  umma<CC_MERGE_BF16X3>(tmem_base + (uint32_t)(acc * OZ_BN), a, b, idesc,
-                                        accumulate);
+                  umma<CC_MERGE_BF16X3>(dbase + (uint32_t)(acc * BN), a, b, idesc, accumulate);
                 }
               }
             }
@@ -353,7 +400,7 @@ __global__ void __launch_bounds__(192, 1)
             }
           }
           if (!ok) break;
-          umma_commit(tfull);
+          umma_commit(&tfull[ab]);
         }
       }
       if (!ok && any_mma) {
@@ -362,21 +409,26 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4, one output row per lane
+    // epilogue warps 2 .. EW + 1: TMEM lane quarter = warp % 4, one output row
+    // per lane; the EW / 4 warps of a quarter split the tile's columns
     const int quarter = warp & 3;
-    unsigned char* stg = stg_base + quarter * 2 * OZ_STG_BYTES;
+    const int part = (warp - 2) >> 2;
+    const int c_begin = part * (Cfg::COLS_PER_WARP / 16);
+    const int c_end = c_begin + Cfg::COLS_PER_WARP / 16;
+    unsigned char* stg = stg_base + (warp - 2) * 2 * OZ_STG_BYTES;
     int buf = 0;
     int iter = 0;
     bool ok_all = true;
     for (int t = blockIdx.x; t < n_tiles && ok_all; t += gridDim.x) {
       int m0, n0;
-      oz_tile_coords(t, tiles_m, tiles_n, m0, n0);
+      oz_tile_coords(t, tiles_m, tiles_n, BN, m0, n0);
       const int y = m0 + quarter * 32 + lane;
-      const int ey = e_row[y] - 2 * (OZ_BETA - 1) - OZ_FIX;  // exponent of one fixed-point unit
+      const int ey = e_row[y] - 2 * (OZ_BETA - 1) - FIX;  // exponent of one fixed-point unit
       const long long* orow = reinterpret_cast<const long long*>(out) + (int64_t)y * n_cols + n0;
       for (int g = 0; g < n_groups; ++g, ++iter) {
+        const int ab = iter % NBUF;
         int ok = 1;
-        if (lane == 0) ok = mbar_wait(tfull, iter & 1, abort_flag, err) ? 1 : 0;
+        if (lane == 0) ok = mbar_wait(&tfull[ab], (iter / NBUF) & 1, abort_flag, err) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           ok_all = false;
@@ -391,20 +443,27 @@ __global__ void __launch_bounds__(192, 1)
           __syncwarp();
         }
         const bool last = g == n_groups - 1;
-        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t tbase =
+            tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * NACC * BN);
 #pragma unroll 1
-        for (int c = 0; c < OZ_BN / 16; ++c) {
-          uint32_t r0[16], r1[16], r2[16], r3[16];
-          tmem_ld16(tbase + 0 * OZ_BN + c * 16, r0);
-          tmem_ld16(tbase + 1 * OZ_BN + c * 16, r1);
-          tmem_ld16(tbase + 2 * OZ_BN + c * 16, r2);
-          tmem_ld16(tbase + 3 * OZ_BN + c * 16, r3);
+        for (int c = c_begin; c < c_end; ++c) {
+          uint32_t r[NACC][16];
+#pragma unroll
+          for (int L = 0; L < NACC; ++L) tmem_ld16(tbase + L * BN + c * 16, r[L]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c == c_end - 1) {  // every accumulator value is in registers: free the set
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[ab]);
+          }
           long long v[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            v[j] = oz_fixed(__uint_as_float(r0[j]), __uint_as_float(r1[j]),
-                            __uint_as_float(r2[j]), __uint_as_float(r3[j]));
+          for (int j = 0; j < 16; ++j) {
+            float a[NACC];
+#pragma unroll
+            for (int L = 0; L < NACC; ++L) a[L] = __uint_as_float(r[L][j]);
+            v[j] = oz_fixed<NACC, FIX>(a);
+          }
           if (g > 0) {  // add the earlier groups' exact sums, read through L2
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
@@ -422,10 +481,17 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {
               const int4 f = __ldg(fp + q4);
-              w[4 * q4 + 0] = oz_to_f64(v[4 * q4 + 0], ey + f.x);
-              w[4 * q4 + 1] = oz_to_f64(v[4 * q4 + 1], ey + f.y);
-              w[4 * q4 + 2] = oz_to_f64(v[4 * q4 + 2], ey + f.z);
-              w[4 * q4 + 3] = oz_to_f64(v[4 * q4 + 3], ey + f.w);
+              if (CVT) {
+                w[4 * q4 + 0] = oz_to_f64_cvt(v[4 * q4 + 0], ey + f.x);
+                w[4 * q4 + 1] = oz_to_f64_cvt(v[4 * q4 + 1], ey + f.y);
+                w[4 * q4 + 2] = oz_to_f64_cvt(v[4 * q4 + 2], ey + f.z);
+                w[4 * q4 + 3] = oz_to_f64_cvt(v[4 * q4 + 3], ey + f.w);
+              } else {
+                w[4 * q4 + 0] = oz_to_f64(v[4 * q4 + 0], ey + f.x);
+                w[4 * q4 + 1] = oz_to_f64(v[4 * q4 + 1], ey + f.y);
+                w[4 * q4 + 2] = oz_to_f64(v[4 * q4 + 2], ey + f.z);
+                w[4 * q4 + 3] = oz_to_f64(v[4 * q4 + 3], ey + f.w);
+              }
             }
           } else {
 #pragma unroll
@@ -452,9 +518,6 @@ __global__ void __launch_bounds__(192, 1)
           }
           buf ^= 1;
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty);
       }
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -466,7 +529,7 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(OZ_TMEM_COLS)
+                 "r"(Cfg::TMEM)
                  : "memory");
   }
 }
@@ -492,11 +555,51 @@ OzEncodeFn oz_encode_fn() {
   return fn;
 }
 
-// Bytes of K per stage: 64 (two 96 KB stages, the default) or 32 (four 48 KB
-// stages); CUTSIM_OZ_KBLOCK overrides.
-int oz_kblock() {
-  const char* e = std::getenv("CUTSIM_OZ_KBLOCK");
-  return e && std::atoi(e) == 32 ? 32 : 64;
+// Kernel configurations (K bytes per stage, stages, columns per tile,
+// accumulators, accumulator sets, epilogue warps, FP64 conversion).
+// Measured at q = 30 (merge ms for K = 4 / 64 / 256 terms):
+//   0  64-column tiles, 4 accumulators, 2 sets, 8 epilogue warps, hardware
+//      int64 -> FP64 conversion: 7.3 / 11.8 / 49.3 (max|dpsi|/max|psi| up to
+//      4.4e-13 at K = 256, 1.6e-12 at K = 4096: the merged levels' rounding
+//      grows with K);
+//   1  the same with 5 accumulators (levels 0-3 exact, 4-5 merged), 1 set:
+//      8.4 / 15.6 / 64.9, errors near 2e-14 at every K;
+//   2  128-column tiles, 4 accumulators, 1 set, 4 epilogue warps, integer
+//      conversion: 15.7 / 19.7 / 64.8;
+//   3  configuration 0 with the integer conversion: 9.9 / 13.0 / 50.1.
+// The default takes 0 while K <= 64 (one accumulation group) and 1 beyond;
+// CUTSIM_OZ_CFG selects one by index.
+struct OzChoice {
+  int kbb, nst, bn, nacc, nbuf, ew, cvt;
+  const void* fn;
+  int smem, threads;
+};
+template <int KBB, int NST, int BN, int NACC, int NBUF, int EW, int CVT>
+OzChoice oz_choice() {
+  using Cfg = OzCfg<KBB, NST, BN, NACC, NBUF, EW>;
+  return {KBB, NST, BN, NACC, NBUF, EW, CVT,
+          reinterpret_cast<const void*>(merge_ozaki_kernel<KBB, NST, BN, NACC, NBUF, EW, CVT>),
+          Cfg::SMEM, Cfg::THREADS};
+}
+const OzChoice* oz_choices(int* n) {
+  static const OzChoice c[] = {
+      oz_choice<64, 2, 64, 4, 2, 8, 1>(),   // 0
+      oz_choice<64, 2, 64, 5, 1, 8, 1>(),   // 1
+      oz_choice<64, 2, 128, 4, 1, 4, 0>(),  // 2
+      oz_choice<64, 2, 64, 4, 2, 8, 0>(),   // 3
+  };
+  *n = (int)(sizeof(c) / sizeof(c[0]));
+  return c;
+}
+int oz_choice_for(int64_t K) {
+  const char* e = std::getenv("CUTSIM_OZ_CFG");
+  int n = 0;
+  oz_choices(&n);
+  if (e) {
+    const int v = std::atoi(e);
+    if (v >= 0 && v < n) return v;
+  }
+  return K <= OZ_GROUP_K / 2 ? 0 : 1;
 }
 
 int oz_kr(int64_t K) { return (int)(((2 * K + 31) / 32) * 32); }
@@ -557,7 +660,9 @@ cc_status launch_merge_ozaki(const MergeStage& st, void* workspace, uint64_t ws_
       (const double2*)st.A, (const double2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
       r_sl, c_sl, e_row, f_col);
 
-  const int kbb = oz_kblock();
+  int n_choices = 0;
+  const OzChoice& cfg = oz_choices(&n_choices)[oz_choice_for(st.K)];
+  const int kbb = cfg.kbb;
   const int kel = kbb / 2;
   const CUtensorMapSwizzle sw = kbb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   CUtensorMap map_r, map_c, map_out;
@@ -574,7 +679,7 @@ cc_status launch_merge_ozaki(const MergeStage& st, void* workspace, uint64_t ws_
   {
     const cuuint64_t dims[3] = {(cuuint64_t)KR, (cuuint64_t)(2 * NA), (cuuint64_t)OZ_S};
     const cuuint64_t strides[2] = {(cuuint64_t)KR * 2, (cuuint64_t)(2 * NA) * KR * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kel, (cuuint32_t)OZ_BN, (cuuint32_t)OZ_S};
+    const cuuint32_t box[3] = {(cuuint32_t)kel, (cuuint32_t)cfg.bn, (cuuint32_t)OZ_S};
     if (enc(&map_c, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, c_sl, dims, strides, box, estr3,
             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -595,22 +700,23 @@ cc_status launch_merge_ozaki(const MergeStage& st, void* workspace, uint64_t ws_
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaFuncSetAttribute(merge_ozaki_kernel<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
-    cudaFuncSetAttribute(merge_ozaki_kernel<32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    const OzChoice* all = oz_choices(&n_choices);
+    for (int i = 0; i < n_choices; ++i)
+      cudaFuncSetAttribute(all[i].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, all[i].smem);
     attr_done[dev] = 1;
   }
   const int n_rows = (int)NB, n_cols = (int)(2 * NA);
-  const int n_tiles = (n_rows / OZ_BM) * (n_cols / OZ_BN);
+  const int n_tiles = (n_rows / OZ_BM) * (n_cols / cfg.bn);
   const int grid = std::min(n_tiles, num_sms());
-  const int kblocks = KR / kel;
-  const int group_kb = OZ_GROUP_K / kel;
+  int kblocks = KR / kel;
+  int group_kb = OZ_GROUP_K / kel;
   const double* outp = static_cast<const double*>(st.out);
-  if (kbb == 64)
-    merge_ozaki_kernel<64, 2><<<grid, 192, OZ_SMEM, s>>>(map_r, map_c, map_out, e_row, f_col, outp,
-                                                         n_rows, n_cols, kblocks, group_kb, err);
-  else
-    merge_ozaki_kernel<32, 4><<<grid, 192, OZ_SMEM, s>>>(map_r, map_c, map_out, e_row, f_col, outp,
-                                                         n_rows, n_cols, kblocks, group_kb, err);
+  void* args[] = {&map_r, &map_c, &map_out, &e_row, &f_col, &outp, (void*)&n_rows, (void*)&n_cols,
+                  &kblocks, &group_kb, &err};
+  const cudaError_t le = cudaLaunchKernel(cfg.fn, dim3((unsigned)grid), dim3((unsigned)cfg.threads), args,
+                                          (size_t)cfg.smem, s);
+  if (le != cudaSuccess)
+    return fail(CC_ECUDA, std::string("Ozaki merge launch: ") + cudaGetErrorString(le));
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("Ozaki merge launch: ") + cudaGetErrorString(e));
   return CC_OK;

@@ -76,3 +76,17 @@ def test_ozaki_zero_rows_and_columns(cuda_lib):
     psi, _, _ = gpu_cut(gates, q, segs, "projector", "c128", "ozaki")
     ref = sv.simulate(q, gates)
     assert_parity(psi.cpu().numpy(), ref, "c128", "ozaki zero rows")
+
+
+@pytest.mark.parametrize("cfg", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("segs,c", [([8, 9], 5), ([9, 8], 8)])
+def test_ozaki_kernel_configurations(cuda_lib, monkeypatch, cfg, segs, c):
+    # every kernel configuration (tile width, accumulator count and sets,
+    # epilogue width, FP64 conversion) against the oracle; the default picks
+    # by K
+    monkeypatch.setenv("CUTSIM_OZ_CFG", cfg)
+    q = sum(segs)
+    gates = w.brickwork_cut(q, 12, 90 + c, segs, c)
+    psi, _, _ = gpu_cut(gates, q, segs, "projector", "c128", "ozaki")
+    ref = sv.simulate(q, gates)
+    assert_parity(psi.cpu().numpy(), ref, "c128", f"ozaki cfg {cfg}")
