@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--ctotal", type=int, default=6)
     p.add_argument("--prec", choices=["c64", "c128"], default="c64")
     p.add_argument("--decomp", choices=["projector", "s_sdg"], default="projector")
-    p.add_argument("--merge-form", default="auto", choices=["auto", "fma", "tf32x3", "bf16x3"])
+    p.add_argument("--merge-form", default="auto", choices=["auto", "fma", "tf32x3", "bf16x3", "ozaki"])
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -1061,8 +1061,12 @@ def main(argv=None):
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": alu_src}
     # AUTO's rule (the library's kAutoTcMinTerms): 3xTF32 from K = 8 terms on
+    # AUTO's rule (the library's kAutoTcMinTerms / kAutoOzakiMinTerms): 3xTF32
+    # from K = 8 terms on for complex64, the Ozaki form from K = 2 on for complex128
+    k_last = 1 << cpb[-1]
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        "tf32x3" if (a.prec == "c64" and (1 << cpb[-1]) >= 8) else "fma")
+        ("tf32x3" if k_last >= 8 else "fma") if a.prec == "c64" else
+        ("ozaki" if k_last >= 2 else "fma"))
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
         # complex FMA merge: 8 flops per term per output amplitude on the ALU
@@ -1084,6 +1088,16 @@ def main(argv=None):
                               "frac": tc_flops / mean["merge"] / 1e12 / tc_peak,
                               "peak_source": peak_src + " bf16 burst" +
                               (" x 0.5 (nominal TF32/BF16)" if tc_form == "tf32x3" else "")}
+    if tc_form == "ozaki":
+        # 21 bf16 slice products of the real GEMM of the last merge stage, each
+        # 4 KR flops per output amplitude (KR = 2 K_last rounded up to 32)
+        kr = ((2 * k_last + 31) // 32) * 32
+        tc_flops = 21.0 * 4 * kr * n_amp
+        merge_rf["tensor"] = {"achieved": tc_flops / mean["merge"] / 1e12, "peak": bf16,
+                              "unit": "TFLOP/s", "form": "ozaki",
+                              "frac": tc_flops / mean["merge"] / 1e12 / bf16,
+                              "peak_source": peak_src + " bf16 burst",
+                              "method_flops": 8.0 * k_last * n_amp}
     # verification: both 2^q vectors read once (complex64: FP32 exact products
     # in double-float, HBM-bound; complex128: FP64 arithmetic bounds it)
     verify_bytes = 2.0 * amp * n_amp

@@ -46,10 +46,9 @@ enum : uint8_t { TERM_SIGN = 0, TERM_TABLE = 1, TERM_PBLOCK = 2, TERM_PFIX = 3 }
 //   TERM_SIGN  : multiply by -1 when bit p0 and bit p1 of v are both set
 //   TERM_TABLE : multiply by tab[4*tab + (bit p0) + 2*(bit p1)]
 //   TERM_PBLOCK: opens a phase block, a product of one-bit phases: with the
-//                12 entries at tab[4*tab] = (lo[4], hi[8]), lo[l] = K times
-//                the product of h_i over the bits i of l (i < 2) and hi[m]
-//                the product of h_{2+i} over the bits i of m, it multiplies
-//                the amplitude in register slot j by lo[j & 3] hi[j >> 2]
+//                32 entries T[j] at tab[4*tab], T[j] = K times the product of
+//                h_i over the register bits i set in j, it multiplies the
+//                amplitude in register slot j by T[j]
 //   TERM_PFIX  : inside a phase block, multiply by tab[4*tab] when bit p0 of
 //                v (a bit that is not a register bit of the stage) is set
 struct DTerm {

@@ -525,10 +525,10 @@ struct PassBuilder {
   // ph0 of every phase is a constant factor: it joins the pending scalar,
   // which only the final OP_DIAG applies (in its K), so each factor is
   // ph1 / ph0 on a set bit (a block folds the scalar in early once it falls
-  // below 2^-24 in magnitude).  The block's 12 entries are precomputed products
-  // -- K {1, h0, h1, h0 h1} and the 8 products of h2, h3, h4 -- and its p0
-  // holds flags for the kernel to skip products equal to 1: bit 0 lo[0],
-  // bit 1 lo[1..3], bit 2 hi.
+  // below 2^-24 in magnitude).  The block's 32 entries are the factors of the
+  // 32 register slots, T[j] = K prod_{i: bit i of j set} h_i, so each
+  // amplitude takes one complex product; its p0 has bit 0 set unless
+  // T[0] = 1 (a product the complex128 kernel skips).
   void attach_phase_block(bool all) {
     // the deferred scalar is folded in early once it is small, so the
     // amplitudes (which carry its inverse) stay far from FP32 overflow
@@ -560,17 +560,18 @@ struct PassBuilder {
       K = pend_const;
       pend_const = 1.0;
     }
-    const cd t0[4] = {K, K * h[0], K * h[1], K * h[0] * h[1]};
-    const cd t1[4] = {1.0, h[2], h[3], h[2] * h[3]};
-    const cd t2[4] = {h[4], h[2] * h[4], h[3] * h[4], h[2] * h[3] * h[4]};
+    cd T[32];
+    for (int j = 0; j < 32; ++j) {
+      cd f = K;
+      for (int i = 0; i < MAX_REG_BITS; ++i)
+        if ((j >> i) & 1) f *= h[i];
+      T[j] = f;
+    }
     DTerm b{};
     b.kind = TERM_PBLOCK;
-    b.p0 = (uint8_t)((K != cd(1.0) ? 1 : 0) |
-                     (K != cd(1.0) || h[0] != cd(1.0) || h[1] != cd(1.0) ? 2 : 0) |
-                     (h[2] != cd(1.0) || h[3] != cd(1.0) || h[4] != cd(1.0) ? 4 : 0));
-    b.tab = add_table(t0);
-    add_table(t1);  // consecutive: the block's entries 4..11
-    add_table(t2);
+    b.p0 = (uint8_t)(K != cd(1.0) ? 1 : 0);
+    b.tab = add_table(T);
+    for (int q4 = 1; q4 < 8; ++q4) add_table(T + 4 * q4);  // consecutive: entries 4..31
     hp.terms.push_back(b);
     for (auto& d : fix) hp.terms.push_back(d);
   }

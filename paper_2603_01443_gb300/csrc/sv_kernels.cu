@@ -120,50 +120,57 @@ struct StageRegs {
   }
 };
 
-// Apply a phase block: slot j gets Phi lo[j & 3] hi[j >> 2] with the block's
-// precomputed products lo and hi (the host folds the block's constant K into
-// lo) and Phi the product of the ratios of the TERM_PFIX terms whose bit is
-// set in the thread's fixed index bits c (1 when there are none): at most two
-// complex products per amplitude however many phases the block holds, and
-// none for the products the block's flags mark as 1.
+// Apply a phase block: slot j gets Phi T[j], with T the block's 32
+// precomputed products (the host folds the block's constant K into them) and
+// Phi the product of the ratios of the TERM_PFIX terms whose bit is set in
+// the thread's fixed index bits c (1 when there are none): one complex
+// product per amplitude however many phases the block holds (two with Phi).
+// The complex128 kernel skips slot 0 where T[0] = 1.
 template <typename R, int RB>
 __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                             uint64_t c, const DTerm* __restrict__ terms,
                                             const R* __restrict__ tabs) {
-  constexpr int L = RB < 2 ? RB : 2;
-  constexpr int H = RB - L;
+  constexpr int N = 1 << RB;
   const DTerm blk = terms[op.term_sign_end()];
   const R* tb = tabs + 8 * blk.tab;
-  // bit 0: lo[0] != 1, bit 1: lo[1..3], bit 2: hi.  Skipping pays where the
-  // FP64 pipes bound the pass; the FP32 pass is bound by issue, where the
-  // branches cost more than the products they save (measured), so complex64
-  // applies every product.
-  const uint32_t flags = sizeof(R) == 8 ? blk.p0 : 7u;
+  const bool skip0 = sizeof(R) == 8 && !(blk.p0 & 1u);
   R pr = R(1), pi = R(0);
   const bool fixed = op.term_phase_end() > op.term_sign_end() + 1;
-  for (int t = op.term_sign_end() + 1; t < op.term_phase_end(); ++t) {
-    const DTerm d = terms[t];
-    if ((c >> d.p0) & 1u) {
-      const R* f = tabs + 8 * d.tab;
-      cmul(pr, pi, f[0], f[1]);
+  if (fixed) {
+    for (int t = op.term_sign_end() + 1; t < op.term_phase_end(); ++t) {
+      const DTerm d = terms[t];
+      if ((c >> d.p0) & 1u) {
+        const R* f = tabs + 8 * d.tab;
+        cmul(pr, pi, f[0], f[1]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) cmul(a[j].x, a[j].y, pr, pi);
+  }
+  if constexpr (sizeof(R) == 4) {
+    const float4* t4 = reinterpret_cast<const float4*>(tb);
+#pragma unroll
+    for (int j2 = 0; j2 < N / 2; ++j2) {
+      const float4 f = __ldg(t4 + j2);
+      cmul(a[2 * j2].x, a[2 * j2].y, f.x, f.y);
+      cmul(a[2 * j2 + 1].x, a[2 * j2 + 1].y, f.z, f.w);
+    }
+  } else {
+    const double2* t2 = reinterpret_cast<const double2*>(tb);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (j == 0 && skip0) continue;
+      const double2 f = __ldg(t2 + j);
+      cmul(a[j].x, a[j].y, f.x, f.y);
     }
   }
-#pragma unroll
-  for (int l = 0; l < (1 << L); ++l) {  // one lo product at a time: few live registers
-    if (!fixed && !(flags & (l == 0 ? 1u : 2u))) continue;  // a product equal to 1
-    R lr = tb[2 * l], li = tb[2 * l + 1];
-    if (fixed) cmul(lr, li, pr, pi);
-#pragma unroll
-    for (int m = 0; m < (1 << H); ++m) cmul(a[(m << L) | l].x, a[(m << L) | l].y, lr, li);
-  }
-  if (flags & 4u) {
-#pragma unroll
-    for (int m = 1; m < (1 << H); ++m) {  // one hi product at a time: few live registers
-      const R hr = tb[8 + 2 * m], hh = tb[9 + 2 * m];
-#pragma unroll
-      for (int l = 0; l < (1 << L); ++l) cmul(a[(m << L) | l].x, a[(m << L) | l].y, hr, hh);
-    }
-  }
+}
+
+// x with its sign bit flipped where bit 31 of m is set: x ^ (m & 0x80000000).
+__device__ __forceinline__ uint32_t xor_sign(uint32_t x, uint32_t m) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0x78;" : "=r"(d) : "r"(x), "r"(m), "r"(0x80000000u));
+  return d;
 }
 
 // Multiply the thread's 2^RB amplitudes by an op's diagonal factors.  With
@@ -206,15 +213,19 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
   }
   smask &= ALL;
   if (smask) {
+    // slot j's sign is bit j of smask moved to bit 31: one shift per slot and
+    // one three-input logic op (x ^ (m & 0x80000000)) per float
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      const uint32_t sb = (smask << (31 - j)) & 0x80000000u;
+      const uint32_t m = smask << (31 - j);
       if (sizeof(R) == 4) {
-        a[j].x = __int_as_float(__float_as_int((float)a[j].x) ^ (int)sb);
-        a[j].y = __int_as_float(__float_as_int((float)a[j].y) ^ (int)sb);
+        a[j].x = __uint_as_float(xor_sign(__float_as_uint((float)a[j].x), m));
+        a[j].y = __uint_as_float(xor_sign(__float_as_uint((float)a[j].y), m));
       } else {
-        a[j].x = __longlong_as_double(__double_as_longlong((double)a[j].x) ^ ((long long)sb << 32));
-        a[j].y = __longlong_as_double(__double_as_longlong((double)a[j].y) ^ ((long long)sb << 32));
+        const long long hx = __double_as_longlong((double)a[j].x);
+        const long long hy = __double_as_longlong((double)a[j].y);
+        a[j].x = __hiloint2double((int)xor_sign((uint32_t)(hx >> 32), m), (int)(uint32_t)hx);
+        a[j].y = __hiloint2double((int)xor_sign((uint32_t)(hy >> 32), m), (int)(uint32_t)hy);
       }
     }
   }

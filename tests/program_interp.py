@@ -6,7 +6,8 @@ state vector with numpy, following the device program's definition: passes in
 order; in a pass, every amplitude's virtual index v puts its tile bits first
 and the other bits above them; in each stage, every op first multiplies each
 amplitude by its diagonal factors (adjacent-bit signs, sign terms, the phase
-block over the stage's register bits and its TERM_PFIX factors, table terms)
+block's factor of the amplitude's register slot and its TERM_PFIX factors,
+table terms)
 and then applies its 2x2 matrix or rotation to the pairs differing in one
 register bit.  It shares nothing with the CUDA path beyond that image, so a
 match with the oracle pins the host compiler (pass and stage planning,
@@ -115,15 +116,11 @@ def run(prog: Program) -> np.ndarray:
                     f[(_bit(v, p0) & _bit(v, p1)) == 1] *= -1
                 if n_phase:
                     _, _, _, tab = prog.terms[tb0 + n_sign]
-                    blk = prog.tabs[4 * tab:4 * tab + 12]
-                    L = min(P.rbits, 2)
-                    lo = np.zeros(N, dtype=np.int64)
-                    hi = np.zeros(N, dtype=np.int64)
-                    for i2 in range(L):
-                        lo |= _bit(v, rb[i2]) << i2
-                    for i2 in range(P.rbits - L):
-                        hi |= _bit(v, rb[L + i2]) << i2
-                    f *= blk[lo] * blk[4 + hi]
+                    blk = prog.tabs[4 * tab:4 * tab + 32]
+                    slot = np.zeros(N, dtype=np.int64)
+                    for i2 in range(P.rbits):
+                        slot |= _bit(v, rb[i2]) << i2
+                    f *= blk[slot]
                     for k in range(tb0 + n_sign + 1, tb0 + n_sign + n_phase):
                         kind, p0, _, tab2 = prog.terms[k]
                         assert kind == TERM_PFIX

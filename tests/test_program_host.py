@@ -112,10 +112,12 @@ def test_program_image_arguments(host_lib):
 
 
 @pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c128", 4), ("c128", 13)])
-def test_phase_block_skip_flags(host_lib, prec, tile_bits):
-    # the complex128 kernel skips the products a phase block's flags mark as
-    # 1 (bit 0: lo[0], bit 1: lo[1..3], bit 2: hi[1..7]); every product so
-    # marked must be exactly 1
+def test_phase_block_entries(host_lib, prec, tile_bits):
+    # a phase block's 32 entries are the products K prod_i h_i^(bit i of j)
+    # over the register bits, so T[j] T[0] = T[j & 1] T[j & ~1] and every
+    # entry is a unit complex number up to the common K; the complex128
+    # kernel skips slot 0 where the flag (bit 0) is clear, which needs
+    # T[0] = 1 exactly
     q = 10
     gates = w.random_circuit(q, 200, 9, kinds=ALL_KINDS)
     prog = interp(gates, q, prec, tile_bits)
@@ -126,15 +128,14 @@ def test_phase_block_skip_flags(host_lib, prec, tile_bits):
             continue
         kind, flags, _, tab = prog.terms[op[2] + n_sign]
         assert kind == 2  # TERM_PBLOCK
-        blk = prog.tabs[4 * tab:4 * tab + 12]
+        blk = prog.tabs[4 * tab:4 * tab + 32]
         blocks += 1
         if not flags & 1:
             assert blk[0] == 1
-        if not flags & 2:
-            assert np.all(blk[1:4] == 1)
-        if not flags & 4:
-            assert np.all(blk[5:12] == 1)
-        assert blk[4] == 1  # hi[0], the empty product
+        k = abs(blk[0])
+        assert np.allclose(np.abs(blk), k, rtol=1e-12)
+        for j in range(32):
+            assert abs(blk[j] * blk[0] - blk[j & 1] * blk[j & ~1]) <= 1e-12 * k * k
     assert blocks > 0
 
 
@@ -177,7 +178,7 @@ def _mutations(prog):
     blk = [t for t in prog.terms if t[0] == TERM_PBLOCK]
     if blk:
         m = copy.deepcopy(prog)
-        m.tabs[4 * blk[-1][3]] *= np.exp(0.3j)  # the entry every amplitude with lo = 0 takes
+        m.tabs[4 * blk[-1][3]] *= np.exp(0.3j)  # the entry of the slot with no register bit set
         out["phase block entry"] = m
     multi = [i for i, P in enumerate(prog.passes) if P.k >= 6]
     if multi:
@@ -257,7 +258,7 @@ def validate(prog):
                     assert tk == kind
                     assert 0 <= p0 < prog.nq and 0 <= p1 < prog.nq
                     if kind == TERM_PBLOCK:
-                        assert 0 <= tab and tab + 3 <= n_tab
+                        assert 0 <= tab and tab + 8 <= n_tab
                     elif kind != TERM_SIGN:
                         assert 0 <= tab < n_tab
     assert next_stage == len(prog.stages) and next_op == len(prog.ops)
