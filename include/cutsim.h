@@ -257,6 +257,27 @@ cc_status cc_plan_program_image(const cc_gate* gates, int32_t n_gates, int32_t q
                                 int64_t* words, int64_t* n_words, double* reals,
                                 int64_t* n_reals);
 
+/* cc_kak_gates -- any two-qubit unitary as gates the library takes (host
+ * work, no device).  Eq. 1 makes a general two-qubit gate a Schmidt-rank-4
+ * cut; the canonical (Cartan, KAK) factorisation
+ *   U = e^{i g} (A1 (x) B1) CAN(tx, ty, tz) (A0 (x) B0)
+ * (Khaneja and Glaser 2001; Kraus and Cirac 2001) turns it into one-qubit
+ * gates around a CC_GATE_CAN, which the cutter and the simulators take.
+ *   u       host array of 32 doubles: the 4x4 unitary on (q0, q1), row-major,
+ *           interleaved re/im, basis |x_q0 x_q1> (index 2 x_q0 + x_q1);
+ *           read during the call only.
+ *   q0, q1  distinct qubits in [0, CC_MAX_QUBITS).
+ *   out     host array of at least 9 gates, written: U3 on q0, U3 on q1, CAN on
+ *           (q0, q1), U3 on q0, U3 on q1, and (when the global phase is not
+ *           0) U3 / X / U3 / X on q0 that multiply by e^{i g}; their product
+ *           is u exactly up to rounding (global phase included).
+ *   n_out   the number of gates written.
+ * Errors: CC_EINVAL for NULL arguments, bad qubits, non-finite entries or a
+ * matrix that is not unitary to 1e-10; CC_EUNSUPPORTED if the factorisation
+ * fails its own checks (not seen for unitary input). */
+#define CC_KAK_MAX_GATES 9
+cc_status cc_kak_gates(const double* u, int32_t q0, int32_t q1, cc_gate* out, int32_t* n_out);
+
 /* cc_uncut_info -- number of gate passes over the 2^q vector and of fused ops. */
 cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops, int32_t* tile_bits);
 

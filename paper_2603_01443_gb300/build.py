@@ -25,7 +25,7 @@ CU_SOURCES = ["runtime.cu", "sv_kernels.cu", "merge_kernels.cu", "merge_tc.cu", 
               "reduce_kernels.cu",
               "batch.cu", "mlp.cu",
               "gather_static.cu"]
-CPP_SOURCES = ["program.cpp", "plan.cpp"]
+CPP_SOURCES = ["program.cpp", "plan.cpp", "kak.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -94,6 +94,8 @@ _SIGNATURES = {
                             c_void_p]),
     "cc_gather_static": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), c_int64,
                                    c_void_p, c_void_p]),
+    "cc_kak_gates": (c_int32, [POINTER(c_double), c_int32, c_int32, POINTER(CGate),
+                               POINTER(c_int32)]),
     "cc_batch_create": (c_int32, [POINTER(CGate), POINTER(c_int64), c_int32, POINTER(c_int32),
                                   POINTER(c_int32), POINTER(c_int32), c_int32, c_int32, c_int32,
                                   c_int32, POINTER(c_void_p)]),

@@ -1,6 +1,6 @@
-"""The two-qubit KAK factorisation (host helper): every gate list it returns
-multiplies back, with the oracle's own gate matrices, to the input unitary
-exactly (global phase included)."""
+"""The two-qubit KAK factorisation (cc_kak_gates, host code behind the C
+ABI): every gate list it returns multiplies back, with the oracle's own gate
+matrices, to the input unitary exactly (global phase included)."""
 
 import math
 
@@ -9,7 +9,7 @@ import pytest
 from scipy.stats import unitary_group
 
 from oracle import statevector as sv
-from paper_2603_01443_gb300 import kak
+from paper_2603_01443_gb300 import capi, kak
 
 
 def product(gates):
@@ -33,32 +33,46 @@ SPECIAL = {
     "can": sv.can(0.4, 1.3, -0.7),
     "sqrt_swap": sv.can(-math.pi / 4, -math.pi / 4, -math.pi / 4),
     "cx_reversed": np.kron(sv.H, sv.H) @ sv.CX @ np.kron(sv.H, sv.H),
+    "phased_local": np.exp(0.7j) * np.kron(sv.H, sv.u3(1.1, 0.2, -2.4)),
 }
 
 
 @pytest.mark.parametrize("name", sorted(SPECIAL))
-def test_special_gates(name):
+def test_special_gates(host_lib, name):
     u = np.asarray(SPECIAL[name], dtype=complex)
     gates = kak.kak_gates(u, 0, 1)
+    assert len(gates) <= kak.MAX_GATES
     assert np.max(np.abs(product(gates) - u)) < 1e-10
 
 
-@pytest.mark.parametrize("seed", range(20))
-def test_random_unitaries(seed):
+@pytest.mark.parametrize("seed", range(40))
+def test_random_unitaries(host_lib, seed):
     u = unitary_group.rvs(4, random_state=seed)
     gates = kak.kak_gates(u, 0, 1)
     assert sum(1 for g in gates if g.kind == "CAN") == 1
+    assert [g.kind for g in gates[:5]] == ["U3", "U3", "CAN", "U3", "U3"]
     assert np.max(np.abs(product(gates) - u)) < 1e-10
 
 
-def test_u3_params_roundtrip():
-    rng = np.random.default_rng(1)
-    for _ in range(50):
-        u = unitary_group.rvs(2, random_state=rng)
-        th, ph, la, g = kak.u3_params(u)
-        assert np.allclose(np.exp(1j * g) * sv.u3(th, ph, la), u, atol=1e-12)
+def test_canonical_parameters_of_a_can_gate(host_lib):
+    # CAN itself: the factorisation's middle gate reproduces it with local
+    # factors that are identities up to phases and Pauli frame changes
+    u = sv.can(0.4, 1.3, -0.7)
+    gates = kak.kak_gates(u, 0, 1)
+    can = [g for g in gates if g.kind == "CAN"][0]
+    # CAN parameters are fixed up to sign and the Weyl-chamber symmetries:
+    # the sorted magnitudes of the three angles modulo pi agree
+    got = sorted(abs(math.remainder(x, math.pi)) for x in (can.theta, can.phi, can.lam))
+    want = sorted(abs(math.remainder(x, math.pi)) for x in (0.4, 1.3, -0.7))
+    assert np.allclose(got, want, atol=1e-9)
 
 
-def test_rejects_non_unitary():
+def test_rejects_bad_input(host_lib):
+    with pytest.raises(capi.CutsimError):
+        kak.kak_gates(np.ones((4, 4)), 0, 1)  # not unitary
+    with pytest.raises(capi.CutsimError):
+        kak.kak_gates(np.eye(4), 3, 3)  # one qubit twice
+    with pytest.raises(capi.CutsimError):
+        kak.kak_gates(np.full((4, 4), np.nan), 0, 1)
     with pytest.raises(ValueError):
-        kak.kak(np.ones((4, 4)))
+        kak.kak_gates(np.eye(2), 0, 1)
