@@ -486,7 +486,7 @@ def sweep_boundary(a):
     return 0
 
 
-def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True):
+def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True, form="auto", tile_bits=None):
     """Mean (T_pre, T_sub, T_merge, T_orig) of one circuit over `reps` runs
     after one warm-up (unless warmup=False); buffers allocated outside the
     timing."""
@@ -497,6 +497,9 @@ def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True):
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     packed = capi.GateArray(gates)
+    saved_tile = os.environ.get("CUTSIM_SEG_TILE_BITS")
+    if tile_bits is not None:  # the library reads the segment tile width per plan
+        os.environ["CUTSIM_SEG_TILE_BITS"] = str(tile_bits)
     probe = api.CutPlan(packed, q, segs, decomp, prec)
     seg, psi, ws = probe.alloc_seg_buf(), probe.alloc_psi(), probe.alloc_workspace()
     probe.close()
@@ -511,7 +514,7 @@ def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True):
         ev[0].record(stream)
         plan.simulate_segments(seg, stream)
         ev[1].record(stream)
-        plan.merge(seg, psi, ws, "auto", stream)
+        plan.merge(seg, psi, ws, form, stream)
         ev[2].record(stream)
         ev[2].synchronize()
         t1 = time.perf_counter()
@@ -527,6 +530,11 @@ def measure_point(gates, q, segs, prec, decomp, reps=3, warmup=True):
         plan.close()
         up.close()
     capi.check(capi.lib().cc_sync(stream.cuda_stream), "cc_sync")
+    if tile_bits is not None:
+        if saved_tile is None:
+            os.environ.pop("CUTSIM_SEG_TILE_BITS", None)
+        else:
+            os.environ["CUTSIM_SEG_TILE_BITS"] = saved_tile
     return tuple(statistics.mean(x) for x in zip(*rec))
 
 
@@ -644,7 +652,7 @@ def sweep_paper(a):
     return 0
 
 
-def planner_instance_features(q, depth, segs, cpb, gates):
+def planner_instance_features(q, depth, segs, cpb, gates, tile_bits=13, form="fma"):
     from paper_2603_01443_gb300 import planner as pl
 
     n = len(segs)
@@ -653,21 +661,38 @@ def planner_instance_features(q, depth, segs, cpb, gates):
     max_seg_bits = max(s + c for s, c in zip(segs, seg_c))
     dense = sum(1 for g in gates if g.kind in ("U3", "H", "X"))
     two = sum(1 for g in gates if g.q1 >= 0)
-    return pl.features(q, depth, n, sum(cpb), n_sub, max_seg_bits, dense, two), seg_c
+    return pl.features(q, depth, n, sum(cpb), n_sub, max_seg_bits, dense, two, tile_bits,
+                       form), seg_c
+
+
+def merge_forms(prec):
+    """The merge forms a plan of this precision can run (AUTO aside)."""
+    return ("fma", "tf32x3", "bf16x3") if prec == "c64" else ("fma", "ozaki")
+
+
+def resolved_form(form, prec, k_last, qa, qb):
+    """The form a merge request runs: a tensor-core form needs both factors
+    of >= 2^7 amplitudes (the library then merges on CUDA cores)."""
+    if form in ("tf32x3", "bf16x3", "ozaki") and (qa < 7 or qb < 7):
+        return "fma"
+    return form
 
 
 def sweep_planner(a, n_inst=4000):
     """Learned planner: time n_inst random brickwork instances (q 14..30,
-    depth 4..64, n in {2, 3, 4} equal segments, c_total 0..16) stage by
-    stage on this GPU, train an ensemble of FP32 networks (3 hidden layers of
-    64, hand-written CUDA kernels) on an 80/20 split to predict log10 stage
-    seconds, and report the prediction error on the held-out 20 %, the
-    cut/no-cut decisions of the model, of the closed-form threshold and of the
-    model with its fallback (ensemble spread > 20 %), the choice of n on
-    separate circuit families, and the largest q that fits a 10-minute budget
-    with and without cutting.  Instances whose segment buffers would exceed
-    2^31 amplitudes or whose merge would exceed 2^39 amplitude-terms are
-    redrawn (their cost is out of proportion to what they teach)."""
+    depth 4..64, n in {2, 3, 4} equal segments, c_total 0..16, each with a
+    random segment tile width of 2^11..2^13 amplitudes and a random merge form
+    the plan can run) stage by stage on this GPU, train an ensemble of FP32
+    networks (3 hidden layers of 64, hand-written CUDA kernels) on an 80/20
+    split to predict log10 stage seconds, and report the prediction error on
+    the held-out 20 %, the cut/no-cut decisions of the model, of the
+    closed-form threshold and of the model with its fallback (held-out error
+    near the query above 20 %), the choice of n, merge form and tile width on
+    separate circuit families against the measured best, and the largest q
+    that fits a 10-minute budget with and without cutting.  Instances whose
+    segment buffers would exceed 2^31 amplitudes or whose merge would exceed
+    2^39 amplitude-terms are redrawn (their cost is out of proportion to what
+    they teach)."""
     import numpy as np
 
     import torch
@@ -677,6 +702,8 @@ def sweep_planner(a, n_inst=4000):
 
     torch.cuda.set_device(0)
     rng = np.random.default_rng(a.seed + 4242)
+    forms = merge_forms(a.prec)
+    tiles = (11, 12, 13)
     measure_point(w.brickwork_cut(16, 4, 0, [8, 8], 1), 16, [8, 8], a.prec, a.decomp, reps=1)
     X, Y, meta = [], [], []
     t0 = time.perf_counter()
@@ -691,11 +718,14 @@ def sweep_planner(a, n_inst=4000):
         if sum(1 << (s_ + c_) for s_, c_ in zip(segs, seg_c)) > (1 << 31) or q + max(cpb) > 39:
             continue
         gates = w.brickwork_cut(q, depth, int(rng.integers(1 << 30)), segs, cpb)
-        pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1, warmup=False)
-        f, _ = planner_instance_features(q, depth, segs, cpb, gates)
+        form = resolved_form(str(rng.choice(forms)), a.prec, 1 << cpb[-1], q - segs[-1], segs[-1])
+        tile = int(rng.choice(tiles))
+        pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1,
+                                            warmup=False, form=form, tile_bits=tile)
+        f, _ = planner_instance_features(q, depth, segs, cpb, gates, tile, form)
         X.append(f)
         Y.append([pre, sub, mer, orig])
-        meta.append((q, depth, n, c))
+        meta.append((q, depth, n, c, pl.depth_ratio(gates, segs)))
     t_data = time.perf_counter() - t0
     X, Y = np.array(X), np.array(Y)
     perm = rng.permutation(len(X))
@@ -708,69 +738,113 @@ def sweep_planner(a, n_inst=4000):
     t_train = time.perf_counter() - t1
     pr = P.predict(X[te])
     err = {}
-    for i, s in enumerate(pl.STAGES):
-        rel = np.abs(pr[s] - Y[te, i]) / Y[te, i]
-        err[s] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90))}
+    for i, s_ in enumerate(pl.STAGES):
+        rel = np.abs(pr[s_] - Y[te, i]) / Y[te, i]
+        err[s_] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90))}
     t_cut_meas = Y[te, 0] + Y[te, 1] + Y[te, 2]
     rel = np.abs(pr["cut"] - t_cut_meas) / t_cut_meas
     err["cut"] = {"median": float(np.median(rel)), "p90": float(np.percentile(rel, 90))}
-    truth = t_cut_meas < Y[te, 3]
-    model = pr["cut"] < pr["orig"]
-    closed = np.array([meta[k][3] < pl.threshold(meta[k][0], meta[k][2]) for k in te])
-    fb = pr["spread"] > P.fallback_spread
-    combined = np.where(fb, closed, model)
-    decisions = {"test_instances": int(len(te)), "cut_wins_measured": float(truth.mean()),
+    # fallback trigger: held-out error near each query, estimated without the
+    # query itself (leave-one-out over the held-out set)
+    half = len(te) // 2
+    te_a, te_b = te[:half], te[half:]
+    P.set_holdout(X[te_a], Y[te_a])
+    exp_b = P.expected_error(X[te_b])
+    truth = t_cut_meas[half:] < Y[te_b, 3]
+    model = pr["cut"][half:] < pr["orig"][half:]
+    closed = np.array([meta[k][3] < pl.threshold(meta[k][0], meta[k][2]) for k in te_b])
+    closed15 = np.array([meta[k][3] < pl.nonuniform_threshold(meta[k][0], meta[k][2], meta[k][4])
+                         for k in te_b])
+    fb = exp_b > P.fallback_error
+    combined = np.where(fb, closed15, model)
+    decisions = {"test_instances": int(len(te_b)), "cut_wins_measured": float(truth.mean()),
                  "accuracy_model": float((model == truth).mean()),
-                 "accuracy_closed_form": float((closed == truth).mean()),
+                 "accuracy_closed_form_eq13_14": float((closed == truth).mean()),
+                 "accuracy_closed_form_eq15": float((closed15 == truth).mean()),
                  "accuracy_model_with_fallback": float((combined == truth).mean()),
-                 "fallback_rate": float(fb.mean())}
+                 "fallback_rate": float(fb.mean()),
+                 "fallback_trigger": "held-out T_cut/T_orig error of the 8 nearest held-out "
+                                     "instances > 20 %"}
     print(json.dumps({"sweep": "planner", "part": "data", "instances": int(len(X)),
-                      "data_s": t_data, "train_s": t_train,
-                      "final_train_loss": [float(c[-1]) for c in curves],
+                      "data_s": t_data, "train_s": t_train, "precision": a.prec,
+                      "forms": list(forms), "tile_bits": list(tiles),
+                      "final_train_loss": [float(c_[-1]) for c_ in curves],
                       "features": list(pl.FEATURES), "stages": list(pl.STAGES)}), flush=True)
     print(json.dumps({"sweep": "planner", "part": "prediction_error_test", "error": err,
                       "decisions": decisions}), flush=True)
+    P.set_holdout(X[te], Y[te])
 
-    # choice of n on separate circuit families: uncut, or cut into n = 2, 3, 4
+    # choice of n, merge form and tile width on separate circuit families:
+    # every option measured, the planner's choice against the measured best
     fam_rng = np.random.default_rng(a.seed + 77)
-    agree, regret, n_fb, rows = 0, [], 0, []
-    for k in range(48):
+    n_fam = 32
+    tols = [2e-6, 5e-5] if a.prec == "c64" else [1e-12]
+    stats = {str(t): {"agree_n": 0, "agree_all": 0, "fallback": 0, "regret": []} for t in tols}
+    rows = []
+    for k in range(n_fam):
         q = int(fam_rng.integers(18, 31))
         depth = int(fam_rng.choice([8, 16, 32, 64]))
         cpb1 = int(fam_rng.integers(1, 6))
         seed = int(fam_rng.integers(1 << 30))
         opts, times = [], {}
         t_orig = None
+        ratio = None
         for n in (2, 3, 4):
             segs = w.equal_partition(q, n)
             cpb = [cpb1] * (n - 1)
             gates = w.brickwork_cut(q, depth, seed, segs, cpb)
-            pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1)
-            times[n] = pre + sub + mer
-            t_orig = orig if t_orig is None else min(t_orig, orig)
-            f, seg_c = planner_instance_features(q, depth, segs, cpb, gates)
-            opts.append({"n": n, "features": f, "cut_bits": sum(cpb),
-                         "n_sub": sum(1 << c_ for c_ in seg_c)})
-        times[0] = t_orig
-        d = P.decide(q, opts)
-        best = min(times, key=times.get)
-        agree += int(d["choice"] == best)
-        n_fb += int(d["fallback"])
-        regret.append(times[d["choice"]] / times[best] - 1.0)
-        rows.append({"q": q, "depth": depth, "c_per_boundary": cpb1, "choice": d["choice"],
-                     "best": best, "fallback": d["fallback"],
-                     "measured_s": {str(n): t for n, t in times.items()}})
-    print(json.dumps({"sweep": "planner", "part": "choose_n", "families": 48,
-                      "agreement": agree / 48.0, "fallback_rate": n_fb / 48.0,
-                      "mean_regret": float(np.mean(regret)), "max_regret": float(np.max(regret)),
-                      "rows": rows}), flush=True)
+            ratio = pl.depth_ratio(gates, segs) if ratio is None else ratio
+            done = set()
+            for form in forms:
+                rf = resolved_form(form, a.prec, 1 << cpb1, q - segs[-1], segs[-1])
+                for tile in (12, 13):
+                    if (rf, tile) in done:
+                        continue
+                    done.add((rf, tile))
+                    pre, sub, mer, orig = measure_point(gates, q, segs, a.prec, a.decomp, reps=1,
+                                                        form=rf, tile_bits=tile)
+                    times[(n, rf, tile)] = pre + sub + mer
+                    t_orig = orig if t_orig is None else min(t_orig, orig)
+                    f, seg_c = planner_instance_features(q, depth, segs, cpb, gates, tile, rf)
+                    opts.append({"n": n, "form": rf, "seg_tile_bits": tile, "features": f,
+                                 "cut_bits": sum(cpb), "n_sub": sum(1 << c_ for c_ in seg_c)})
+        row = {"q": q, "depth": depth, "c_per_boundary": cpb1, "uncut_s": t_orig,
+               "measured_s": {f"{n}/{fm}/{tb}": t for (n, fm, tb), t in times.items()}}
+        for tol in tols:
+            adm = {key: t for key, t in times.items() if pl.FORM_TOL[key[1]] <= tol}
+            best_key = min(adm, key=adm.get)
+            best = (0, None, None) if t_orig < adm[best_key] else best_key
+            best_t = min(t_orig, adm[best_key])
+            d = P.decide(q, opts, tol=tol, dseg_over_d=ratio)
+            if d["choice"] == 0:
+                got_t = t_orig
+            elif d["form"] in (None, "auto"):  # fallback: the library's AUTO form, default tile
+                cands = [t for (n, fm, tb), t in adm.items() if n == d["choice"] and tb == 13]
+                got_t = min(cands) if cands else t_orig
+            else:
+                got_t = times[(d["choice"], d["form"], d["seg_tile_bits"])]
+            st_ = stats[str(tol)]
+            st_["agree_n"] += int(d["choice"] == best[0])
+            st_["agree_all"] += int((d["choice"], d["form"], d["seg_tile_bits"]) == best)
+            st_["fallback"] += int(d["fallback"])
+            st_["regret"].append(got_t / best_t - 1.0)
+            row[f"tol {tol:g}"] = {"choice": [d["choice"], d["form"], d["seg_tile_bits"]],
+                                   "best": list(best), "fallback": d["fallback"]}
+        rows.append(row)
+    summary = {t: {"agreement_n": v["agree_n"] / n_fam, "agreement_n_form_tile": v["agree_all"] / n_fam,
+                   "fallback_rate": v["fallback"] / n_fam, "mean_regret": float(np.mean(v["regret"])),
+                   "max_regret": float(np.max(v["regret"]))} for t, v in stats.items()}
+    print(json.dumps({"sweep": "planner", "part": "choose_n_form_tile", "families": n_fam,
+                      "options": "n in {2,3,4} x merge forms within the tolerance x tile 2^12, 2^13",
+                      "summary_by_tolerance": summary, "rows": rows}), flush=True)
 
     # largest q within a 10-minute budget (brickwork depth 16, n = 2, c_total = 6)
     def predict(q, which):
         qq = min(q, 30)
         segs = w.equal_partition(qq, 2)
         gates = w.brickwork_cut(qq, 16, 0, segs, [6])
-        f, _ = planner_instance_features(qq, 16, segs, [6], gates)
+        form = "tf32x3" if a.prec == "c64" else "ozaki"
+        f, _ = planner_instance_features(qq, 16, segs, [6], gates, 13, form)
         p = P.predict(np.array([f]))
         t = float(p["cut"][0] if which == "cut" else p["orig"][0])
         return t * 2.0 ** (q - qq)  # state-vector work doubles per qubit beyond the data

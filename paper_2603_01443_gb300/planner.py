@@ -1,13 +1,15 @@
 """Learned stage-time planner: choose between the uncut simulation and cutting
-into n segments from predicted stage times, with the closed-form thresholds
-of Eqs. 13-14 as the fallback.
+into n segments -- and the merge form and segment tile width of the cut --
+from predicted stage times, with the closed-form thresholds of Eqs. 13-15 as
+the fallback.
 
 An ensemble of small fully connected networks (hand-written CUDA forward,
 backward and Adam kernels behind ``cc_mlp_*``) maps circuit features to the
 log10 of the four stage times (T_pre, T_sub, T_merge, T_orig of Eq. 3),
-trained on times measured on this GPU.  The ensemble's spread stands in for
-the prediction error: where it exceeds ``fallback_spread`` (20 %) the
-planner answers with the closed-form threshold instead.
+trained on times measured on this GPU.  Where the prediction error measured
+on held-out instances near a query exceeds 20 % (the ensemble's spread where
+no hold-out set is given), the planner answers with the closed-form
+threshold instead.
 
 Host logic and marshalling only; every network evaluation runs in the CUDA
 kernels.
@@ -26,8 +28,13 @@ import torch
 from . import capi
 
 STAGES = ("pre", "sub", "merge", "orig")
+FORMS = ("fma", "tf32x3", "bf16x3", "ozaki")
 FEATURES = ("q", "log2_depth", "n", "cut_bits", "log2_n_sub", "max_seg_bits",
-            "log2_dense_gates", "log2_two_qubit_gates")
+            "log2_dense_gates", "log2_two_qubit_gates", "seg_tile_bits") + tuple(
+                "form_" + f for f in FORMS)
+# max |dpsi| / max |psi| each merge form guarantees (cc_merge_form): the
+# planner only picks a form whose bound meets the caller's tolerance
+FORM_TOL = {"fma": 0.0, "tf32x3": 2e-6, "bf16x3": 5e-5, "ozaki": 1e-12}
 
 
 def threshold(q: float, n: int) -> float:
@@ -41,11 +48,55 @@ def threshold(q: float, n: int) -> float:
     return q * (n - 1) ** 2 / (2.0 * n) + (n - 1) * math.log2(n / (n - 2.0)) / 2.0
 
 
+def nonuniform_threshold(q: float, n: int, dseg_over_d: float) -> float:
+    """The threshold of Eqs. 13-14 lowered for segment depth D_seg (Eq. 15):
+    T_sub < T_orig becomes N_sub 2^{-q (1 - 1/n)} D_seg / D < 1, which moves
+    log2 N_sub by log2(n D_seg / D) against the uniform case D_seg = D / n,
+    i.e. c_total by that times (n - 1) / 2 (n >= 3) or 1 (n = 2): 0 at
+    D_seg = D / n, 1 cut (n = 2) and (n - 1) log2(n) / 2 cuts (n >= 3) at
+    D_seg = D."""
+    r = min(max(dseg_over_d, 1.0 / n), 1.0)
+    shift = math.log2(n * r) * (1.0 if n == 2 else (n - 1) / 2.0)
+    return threshold(q, n) - shift
+
+
+def circuit_depth(gates, qubits=None) -> int:
+    """Depth of the gate list (as-soon-as-possible layering); with `qubits`,
+    of the gates that touch those qubits, a cut gate counting on both sides."""
+    level = {}
+    depth = 0
+    for g in gates:
+        qs = [g.q0] + ([g.q1] if g.q1 >= 0 else [])
+        if qubits is not None:
+            qs = [x for x in qs if x in qubits]
+            if not qs:
+                continue
+        d = 1 + max(level.get(x, 0) for x in qs)
+        for x in qs:
+            level[x] = d
+        depth = max(depth, d)
+    return depth
+
+
+def depth_ratio(gates, seg_sizes: Sequence[int]) -> float:
+    """D_seg / D with D_seg the largest segment depth (contiguous segments)."""
+    d = circuit_depth(gates)
+    if d == 0:
+        return 1.0 / len(seg_sizes)
+    start, dseg = 0, 0
+    for s in seg_sizes:
+        dseg = max(dseg, circuit_depth(gates, set(range(start, start + s))))
+        start += s
+    return dseg / d
+
+
 def features(q: int, depth: int, n: int, cut_bits: int, n_sub: int, max_seg_bits: int,
-             dense_gates: int, two_qubit_gates: int) -> List[float]:
+             dense_gates: int, two_qubit_gates: int, seg_tile_bits: int = 13,
+             form: str = "fma") -> List[float]:
     return [float(q), math.log2(max(depth, 1)), float(n), float(cut_bits),
             math.log2(max(n_sub, 1)), float(max_seg_bits),
-            math.log2(dense_gates + 1), math.log2(two_qubit_gates + 1)]
+            math.log2(dense_gates + 1), math.log2(two_qubit_gates + 1),
+            float(seg_tile_bits)] + [1.0 if form == f else 0.0 for f in FORMS]
 
 
 class MLP:
@@ -98,15 +149,22 @@ class MLP:
 
 
 class StagePlanner:
-    """Ensemble of MLPs predicting log10 stage seconds from circuit features."""
+    """Ensemble of MLPs predicting log10 stage seconds from circuit features
+    (including the segment tile width and the merge form, so the planner
+    picks those too).  Its fallback trigger is the prediction error measured
+    on held-out instances near the query (set_holdout), or the ensemble's
+    spread where no held-out error is known."""
 
     def __init__(self, n_models: int = 4, hidden: Sequence[int] = (64, 64, 64), seed: int = 0,
                  fallback_spread: float = 0.20, device="cuda"):
         self.dims = [len(FEATURES), *hidden, len(STAGES)]
         self.models = [MLP(self.dims, seed + 1000 * i, device) for i in range(n_models)]
         self.fallback_spread = fallback_spread
+        self.fallback_error = fallback_spread
         self.device = device
         self.x_mu = self.x_sd = self.y_mu = self.y_sd = None
+        self.hold_x = self.hold_err = None
+        self.hold_k = 8
 
     def fit(self, X: np.ndarray, seconds: np.ndarray, epochs: int = 3000, lr: float = 2e-3):
         Y = np.log10(np.maximum(seconds, 1e-7))
@@ -134,26 +192,71 @@ class StagePlanner:
         out["spread"] = np.maximum(t_cut.std(0) / t_cut.mean(0), t_orig.std(0) / t_orig.mean(0))
         return out
 
-    def decide(self, q: int, options: Sequence[dict]) -> dict:
-        """Choose among cutting options (dicts with 'n', 'features',
-        'cut_bits', 'n_sub') and the uncut simulation.  Where the ensemble
-        spread of any option exceeds the fallback level, the closed-form model
-        decides instead: among the options whose c_total stays below Eq. 13/14,
-        the one with the least subcircuit work N_sub 2^{q/n} / n (Table I),
-        else uncut."""
-        X = np.array([o["features"] for o in options])
+    def set_holdout(self, X: np.ndarray, seconds: np.ndarray):
+        """Held-out instances and their measured stage seconds: the relative
+        error of the predicted T_cut and T_orig on each becomes the error
+        estimate of queries near it (the mean over its hold_k nearest
+        neighbours in standardised feature space)."""
         pr = self.predict(X)
-        if np.any(pr["spread"] > self.fallback_spread):
-            ok = [o for o in options if o["cut_bits"] < threshold(q, o["n"])]
-            choice = min(ok, key=lambda o: o["n_sub"] * 2.0 ** (q / o["n"]) / o["n"])["n"] \
-                if ok else 0
-            return {"choice": choice, "fallback": True, "pred_cut": pr["cut"].tolist(),
-                    "pred_orig": float(pr["orig"].mean()), "spread": pr["spread"].tolist()}
+        t_cut = seconds[:, 0] + seconds[:, 1] + seconds[:, 2]
+        e_cut = np.abs(pr["cut"] - t_cut) / t_cut
+        e_orig = np.abs(pr["orig"] - seconds[:, 3]) / seconds[:, 3]
+        self.hold_x = (np.asarray(X, dtype=np.float64) - self.x_mu) / self.x_sd
+        self.hold_err = np.maximum(e_cut, e_orig)
+
+    def expected_error(self, X: np.ndarray) -> Optional[np.ndarray]:
+        """Held-out relative error near each query (None without a hold-out set)."""
+        if self.hold_x is None:
+            return None
+        Z = (np.asarray(X, dtype=np.float64) - self.x_mu) / self.x_sd
+        d = ((Z[:, None, :] - self.hold_x[None, :, :]) ** 2).sum(-1)
+        k = min(self.hold_k, self.hold_x.shape[0])
+        idx = np.argpartition(d, k - 1, axis=1)[:, :k]
+        return self.hold_err[idx].mean(1)
+
+    def decide(self, q: int, options: Sequence[dict], tol: float = 2e-6,
+               dseg_over_d: Optional[float] = None) -> dict:
+        """Choose among cutting options (dicts with 'n', 'form',
+        'seg_tile_bits', 'features', 'cut_bits', 'n_sub') and the uncut
+        simulation; only merge forms whose bound meets `tol` count.  Where the
+        held-out error near any admissible option (or, without a hold-out set,
+        the ensemble spread) exceeds the fallback level, the closed-form model
+        decides instead: among the options whose c_total stays below Eqs.
+        13-14 lowered by Eq. 15 for the circuit's D_seg / D, the one with the
+        least subcircuit work N_sub 2^{q/n} / n (Table I), else uncut; the
+        merge form is then left to the library (AUTO)."""
+        opts = [o for o in options if FORM_TOL.get(o.get("form", "fma"), 0.0) <= tol]
+        X = np.array([o["features"] for o in opts])
+        pr = self.predict(X)
+        err = self.expected_error(X)
+        if err is not None:
+            fallback = bool(np.any(err > self.fallback_error))
+            reason = "held-out error"
+        else:
+            fallback = bool(np.any(pr["spread"] > self.fallback_spread))
+            reason = "ensemble spread"
+        ratio = 1.0 if dseg_over_d is None else dseg_over_d
+        out = {"pred_cut": pr["cut"].tolist(), "pred_orig": float(pr["orig"].mean()),
+               "spread": pr["spread"].tolist(),
+               "expected_error": None if err is None else err.tolist()}
+        if fallback:
+            ok = [o for o in opts if o["cut_bits"] < nonuniform_threshold(q, o["n"], ratio)]
+            if ok:
+                best = min(ok, key=lambda o: o["n_sub"] * 2.0 ** (q / o["n"]) / o["n"])
+                out.update(choice=best["n"], form="auto", seg_tile_bits=None)
+            else:
+                out.update(choice=0, form=None, seg_tile_bits=None)
+            out.update(fallback=True, reason=reason)
+            return out
         best = int(np.argmin(pr["cut"]))
         t_orig = float(pr["orig"].mean())
-        choice = options[best]["n"] if pr["cut"][best] < t_orig else 0
-        return {"choice": choice, "fallback": False, "pred_cut": pr["cut"].tolist(),
-                "pred_orig": t_orig, "spread": pr["spread"].tolist()}
+        if pr["cut"][best] < t_orig:
+            o = opts[best]
+            out.update(choice=o["n"], form=o.get("form"), seg_tile_bits=o.get("seg_tile_bits"))
+        else:
+            out.update(choice=0, form=None, seg_tile_bits=None)
+        out.update(fallback=False, reason=None)
+        return out
 
 
 def max_feasible_q(predict_seconds, budget_s: float, q_max: int, q_min: int = 1) -> Optional[int]:

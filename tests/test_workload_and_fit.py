@@ -127,3 +127,59 @@ def test_clock_samples_summary():
     hot = out + "\n0, 1500, 2070, 1400, 0x48, Not Active, Active, Not Active, Active"
     assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
     assert bench.ClockSampler.summarize("") is None
+
+
+def test_planner_eq15_threshold_matches_the_oracle():
+    # Eq. 15: no change at D_seg = D / n, the oracle's full reduction at D_seg = D
+    from oracle import thresholds as th
+    from paper_2603_01443_gb300 import planner
+
+    for n in (2, 3, 4, 5):
+        for q in (12.0, 20.0, 30.0):
+            assert planner.nonuniform_threshold(q, n, 1.0 / n) == pytest.approx(th.threshold(q, n))
+            assert planner.nonuniform_threshold(q, n, 1.0) == pytest.approx(
+                th.threshold(q, n) - th.nonuniform_reduction(n))
+            mid = planner.nonuniform_threshold(q, n, 0.5 * (1.0 / n + 1.0))
+            assert th.threshold(q, n) - th.nonuniform_reduction(n) < mid < th.threshold(q, n)
+
+
+def test_planner_depth_ratio():
+    # brickwork: every layer touches every segment (D_seg = D); a CX ladder
+    # crosses the segments one after another (D_seg near D / n)
+    from paper_2603_01443_gb300 import planner
+
+    assert planner.depth_ratio(w.brickwork(12, 6, 0), [6, 6]) == pytest.approx(1.0)
+    ladder = [w.Gate("CX", i, i + 1) for i in range(11)]
+    r = planner.depth_ratio(ladder, [6, 6])
+    assert r == pytest.approx(6 / 11)
+    assert planner.circuit_depth(ladder) == 11
+
+
+def test_planner_decide_filters_forms_and_falls_back():
+    # decide() with canned predictions (host logic only): forms beyond the
+    # tolerance are never chosen; a large held-out error near an option
+    # sends the decision to Eqs. 13-15
+    import numpy as np
+
+    from paper_2603_01443_gb300 import planner
+
+    P = planner.StagePlanner.__new__(planner.StagePlanner)
+    P.fallback_spread = P.fallback_error = 0.2
+    P.hold_x = None
+    opts = [{"n": 2, "form": f, "seg_tile_bits": 13, "features": [float(i)], "cut_bits": 4,
+             "n_sub": 32} for i, f in enumerate(("fma", "tf32x3", "bf16x3"))]
+    cut = {"fma": 3.0, "tf32x3": 2.0, "bf16x3": 1.0}
+
+    def predict(X):
+        c = np.array([cut[planner.FORMS[int(x[0])]] for x in X])
+        return {"cut": c, "orig": np.full(len(X), 10.0), "spread": np.zeros(len(X))}
+
+    P.predict = predict
+    P.expected_error = lambda X: np.zeros(len(X))
+    assert P.decide(20, opts, tol=2e-6)["form"] == "tf32x3"
+    assert P.decide(20, opts, tol=5e-5)["form"] == "bf16x3"
+    P.expected_error = lambda X: np.full(len(X), 0.5)
+    d = P.decide(20, opts, tol=2e-6, dseg_over_d=1.0)
+    assert d["fallback"] and d["choice"] == 2 and d["form"] == "auto"  # 4 < 20/2 - 1
+    d = P.decide(9, opts, tol=2e-6, dseg_over_d=1.0)
+    assert d["fallback"] and d["choice"] == 0  # 4 >= 9/2 - 1
