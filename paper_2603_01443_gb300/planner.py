@@ -157,8 +157,9 @@ class StagePlanner:
 
     def __init__(self, n_models: int = 4, hidden: Sequence[int] = (64, 64, 64), seed: int = 0,
                  fallback_spread: float = 0.20, device="cuda"):
-        self.dims = [len(FEATURES), *hidden, len(STAGES)]
-        self.models = [MLP(self.dims, seed + 1000 * i, device) for i in range(n_models)]
+        self.hidden, self.seed, self.n_models = list(hidden), seed, n_models
+        self.dims = None
+        self.models = []  # built by fit() for the width of its features
         self.fallback_spread = fallback_spread
         self.fallback_error = fallback_spread
         self.device = device
@@ -167,6 +168,9 @@ class StagePlanner:
         self.hold_k = 8
 
     def fit(self, X: np.ndarray, seconds: np.ndarray, epochs: int = 3000, lr: float = 2e-3):
+        self.dims = [int(np.asarray(X).shape[1]), *self.hidden, len(STAGES)]
+        self.models = [MLP(self.dims, self.seed + 1000 * i, self.device)
+                       for i in range(self.n_models)]
         Y = np.log10(np.maximum(seconds, 1e-7))
         self.x_mu, self.x_sd = X.mean(0), X.std(0) + 1e-9
         self.y_mu, self.y_sd = Y.mean(0), Y.std(0) + 1e-9
