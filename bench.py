@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--ctotal", type=int, default=6)
     p.add_argument("--prec", choices=["c64", "c128"], default="c64")
     p.add_argument("--decomp", choices=["projector", "s_sdg"], default="projector")
-    p.add_argument("--merge-form", default="auto", choices=["auto", "fma", "tf32x3", "bf16x3", "ozaki"])
+    p.add_argument("--merge-form", default="auto", choices=["auto", "fma", "tf32x3", "bf16x3", "f16x3", "ozaki"])
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -667,13 +667,13 @@ def planner_instance_features(q, depth, segs, cpb, gates, tile_bits=13, form="fm
 
 def merge_forms(prec):
     """The merge forms a plan of this precision can run (AUTO aside)."""
-    return ("fma", "tf32x3", "bf16x3") if prec == "c64" else ("fma", "ozaki")
+    return ("fma", "tf32x3", "f16x3", "bf16x3") if prec == "c64" else ("fma", "ozaki")
 
 
 def resolved_form(form, prec, k_last, qa, qb):
     """The form a merge request runs: a tensor-core form needs both factors
     of >= 2^7 amplitudes (the library then merges on CUDA cores)."""
-    if form in ("tf32x3", "bf16x3", "ozaki") and (qa < 7 or qb < 7):
+    if form in ("tf32x3", "f16x3", "bf16x3", "ozaki") and (qa < 7 or qb < 7):
         return "fma"
     return form
 
@@ -843,7 +843,7 @@ def sweep_planner(a, n_inst=4000):
         qq = min(q, 30)
         segs = w.equal_partition(qq, 2)
         gates = w.brickwork_cut(qq, 16, 0, segs, [6])
-        form = "tf32x3" if a.prec == "c64" else "ozaki"
+        form = "f16x3" if a.prec == "c64" else "ozaki"
         f, _ = planner_instance_features(qq, 16, segs, [6], gates, 13, form)
         p = P.predict(np.array([f]))
         t = float(p["cut"][0] if which == "cut" else p["orig"][0])
@@ -1139,7 +1139,7 @@ def main(argv=None):
     # from K = 8 terms on for complex64, the Ozaki form from K = 2 on for complex128
     k_last = 1 << cpb[-1]
     tc_form = a.merge_form if a.merge_form != "auto" else (
-        ("tf32x3" if k_last >= 8 else "fma") if a.prec == "c64" else
+        ("f16x3" if k_last >= 8 else "fma") if a.prec == "c64" else
         ("ozaki" if k_last >= 2 else "fma"))
     merge_rf["traffic"] = recorded_traffic("merge_" + tc_form, a)
     if tc_form == "fma":
@@ -1150,7 +1150,7 @@ def main(argv=None):
                            "unit": "TFLOP/s",
                            "frac": fma_flops / mean["merge"] / 1e12 / alu_peak,
                            "peak_source": alu_src}
-    if tc_form in ("tf32x3", "bf16x3"):
+    if tc_form in ("tf32x3", "bf16x3", "f16x3"):
         # three split products of the real GEMM of the last (2^q-sized) merge
         # stage: 3 x 8 K_last flops per output amplitude, K_last = 2^(cuts on
         # the last boundary) (all of c_total for n = 2)

@@ -76,6 +76,15 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  * CC_MERGE_BF16X3  : tcgen05 tensor cores, kind::f16 with bf16 operands, the
  *                    same three-product split, FP32 accumulation (CC_C64,
  *                    factors >= 2^7; max|dpsi|/max|psi| <= 5e-5).
+ * CC_MERGE_F16X3   : tcgen05 tensor cores, kind::f16 with fp16 operands: each
+ *                    operand scaled by a power of two (its largest entry just
+ *                    below 1, so no entry leaves fp16's range), split
+ *                    x = hi + lo in fp16 and hi*hi + hi*lo + lo*hi accumulated
+ *                    in FP32, at most 64 terms per accumulation, the two
+ *                    scales undone in the epilogue: the significands
+ *                    of 3xTF32 (11 bits each) in half the operand bytes at
+ *                    twice the tensor rate (CC_C64 plans, both factors >= 2^7
+ *                    amplitudes; max|dpsi|/max|psi| <= 2e-6).
  * CC_MERGE_OZAKI   : complex128 on tcgen05 tensor cores (CC_C128 plans, both
  *                    factors >= 2^7 amplitudes): every operand row scaled by a
  *                    power of two and cut into 6 bf16 slices of 9 bits, the
@@ -86,7 +95,7 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  *                    64-term groups exactly through the output buffer
  *                    (max|dpsi|/max|psi| <= 1e-12; measured about 2e-13 for
  *                    K <= 64 and 2e-14 beyond).
- * CC_MERGE_AUTO    : complex64: TF32X3 where it applies and K >= 8, else FMA;
+ * CC_MERGE_AUTO    : complex64: F16X3 where it applies and K >= 8, else FMA;
  *                    complex128: OZAKI where it applies, else FMA.
  * For n_seg >= 3 the form applies to the last (2^q-sized) stage of the chain;
  * the earlier, smaller stages always use FMA. */
@@ -95,7 +104,8 @@ typedef enum {
   CC_MERGE_FMA = 1,
   CC_MERGE_TF32X3 = 2,
   CC_MERGE_BF16X3 = 3,
-  CC_MERGE_OZAKI = 4
+  CC_MERGE_OZAKI = 4,
+  CC_MERGE_F16X3 = 5
 } cc_merge_form;
 
 typedef enum {

@@ -25,7 +25,7 @@ STATUS = {
 }
 PRECISION = {"c64": 0, "c128": 1}
 DECOMP = {"projector": 0, "s_sdg": 1}
-MERGE_FORM = {"auto": 0, "fma": 1, "tf32x3": 2, "bf16x3": 3, "ozaki": 4}
+MERGE_FORM = {"auto": 0, "fma": 1, "tf32x3": 2, "bf16x3": 3, "ozaki": 4, "f16x3": 5}
 GATE_KIND = {"U3": 0, "H": 1, "X": 2, "Z": 3, "S": 4, "SDG": 5, "T": 6, "TDG": 7, "CZ": 8, "CX": 9,
              "SWAP": 10, "ISWAP": 11, "CAN": 12}
 TWO_QUBIT = ("CZ", "CX", "SWAP", "ISWAP", "CAN")

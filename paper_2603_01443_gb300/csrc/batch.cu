@@ -135,7 +135,7 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
         if (p->stages.empty()) continue;
         const auto& sg = p->stages.back();
         if (sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7 && sg.Z == 1)
-          tcb = std::max(tcb, merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, CC_MERGE_TF32X3));
+          tcb = std::max(tcb, merge_tc_workspace_bytes(sg.qa, sg.qb, sg.K, kAutoTcForm));
       }
     b->tc_off = wo * ab;
     b->tc_bytes = tcb;
@@ -312,7 +312,7 @@ cc_status run_core(const cc_batch* b, const Core& c, void* seg, void* psi, void*
       MergeStage ms{bufs[J.a_buf] + J.a_off * ab, bufs[J.b_buf] + J.b_off * ab,
                     bufs[J.out_buf] + J.out_off * ab, J.qa, J.qb, J.K, 1, J.out_stride, J.aidx,
                     J.bidx};
-      r = launch_merge_tc(ms, CC_MERGE_TF32X3, static_cast<char*>(work) + b->tc_off, b->tc_bytes,
+      r = launch_merge_tc(ms, kAutoTcForm, static_cast<char*>(work) + b->tc_off, b->tc_bytes,
                           stream);
       if (r == CC_EUNSUPPORTED) r = launch_merge_fma(ms, b->precision, stream);
       if (r != CC_OK) return r;

@@ -221,6 +221,11 @@ enum : int32_t { BUF_SEG = 0, BUF_WORK = 1, BUF_PSI = 2 };
 // CUDA-core form is store-bound through K = 4 and slower from K = 8 on
 // (K = 8: 2.03 ms FMA, 1.64 ms 3xTF32).
 constexpr int64_t kAutoTcMinTerms = 8;
+// The complex64 tensor-core form AUTO and batches use: 3xFP16 with operand
+// scales (q = 30: K = 64 1.70 ms against 2.56 ms for 3xTF32, K = 256 7.99
+// against 9.00; within 3 % of it at K = 8, 16), also the more accurate
+// (q = 30, K = 64: 2.2e-7 against 3.5e-7 of max |psi| on the oracle's samples).
+constexpr int kAutoTcForm = CC_MERGE_F16X3;
 // CC_MERGE_AUTO merges complex128 plans with the Ozaki tensor-core form from
 // this many terms on (both factors >= 2^7 amplitudes).
 constexpr int64_t kAutoOzakiMinTerms = 2;

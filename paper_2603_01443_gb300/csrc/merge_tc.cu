@@ -31,6 +31,7 @@
 // copies and MMAs in flight, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,8 +67,8 @@ constexpr int64_t kTf32GroupTerms = 64;
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc_value() {
   return (1u << 4)                                            // D format: F32
-         | ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 7)         // A format: BF16 / TF32
-         | ((KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 10)        // B format: BF16 / TF32
+         | ((KIND == CC_MERGE_F16X3 ? 0u : KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 7)   // A: F16 / BF16 / TF32
+         | ((KIND == CC_MERGE_F16X3 ? 0u : KIND == CC_MERGE_BF16X3 ? 1u : 2u) << 10)  // B format
          | ((uint32_t)(BN >> 3) << 17)                        // N / 8
          | ((uint32_t)(BM >> 4) << 24);                       // M / 16
 }
@@ -82,6 +83,11 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   const int rows = min(kBand, tiles_m - band * kBand);
   m0 = (band * kBand + r % rows) * BM;
   n0 = (r / rows) * BN;
+}
+
+// 2^e > the magnitude whose float bits are mb (e = 0 for an all-zero operand).
+__device__ __forceinline__ int f16_scale_exp(unsigned int mb) {
+  return mb ? (int)((mb >> 23) & 0xFF) - 126 : 0;
 }
 
 // Long K runs in groups of group_kb K blocks: each group accumulates into a
@@ -99,7 +105,8 @@ template <int KIND, int KBB, int NST>
 __global__ void __launch_bounds__(192, 1)
     merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
-                    int kblocks, int group_kb, int* err) {
+                    int kblocks, int group_kb, int* err,
+                    const unsigned int* __restrict__ f16_maxbits) {
   constexpr int RT = BM * KBB, CT = BN * KBB, STB = 2 * RT + 2 * CT;
   static_assert(NST * STB == STAGES * STAGE_BYTES, "operand buffers of 192 KB");
   static_assert((2 * NST + 8) * 8 <= 256, "barrier area");
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(192, 1)
         issued_parity[i] = 0;
       }
       bool ok = true;
-      const int kelem = KIND == CC_MERGE_BF16X3 ? KBB / 2 : KBB / 4;
+      const int kelem = KIND != CC_MERGE_TF32X3 ? KBB / 2 : KBB / 4;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int m0, n0;
         tile_coords(t, tiles_m, tiles_n, m0, n0);
@@ -248,6 +255,11 @@ __global__ void __launch_bounds__(192, 1)
     int buf = 0;
     int iter = 0;
     bool ok_all = true;
+    // fp16 operands: the product of the two operand scales, 2^(e_R + e_C)
+    const float osc = KIND == CC_MERGE_F16X3
+                          ? __uint_as_float((uint32_t)(127 + f16_scale_exp(f16_maxbits[0]) +
+                                                       f16_scale_exp(f16_maxbits[1])) << 23)
+                          : 1.0f;
     for (int t = blockIdx.x; t < n_tiles && ok_all; t += gridDim.x) {
       int m0, n0;
       tile_coords(t, tiles_m, tiles_n, m0, n0);
@@ -276,6 +288,10 @@ __global__ void __launch_bounds__(192, 1)
           for (int h = 0; h < 2; ++h) {
             const int c = c2 + h;
             uint32_t(&r)[32] = rr[h];
+            if (KIND == CC_MERGE_F16X3) {  // undo the operand scales (exact: a power of two)
+#pragma unroll
+              for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) * osc);
+            }
             unsigned char* sb = stg + buf * STG_BYTES;
             if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
             __syncwarp();
@@ -390,7 +406,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int kelem = KIND == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+  const int kelem = KIND != CC_MERGE_TF32X3 ? KB_BYTES / 2 : KB_BYTES / 4;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -587,6 +603,66 @@ __device__ __forceinline__ void split_store(uint32_t* hi, uint32_t* lo, float v)
   *lo = to_tf32(v - __uint_as_float(h));
 }
 
+// fp16 operands carry one power-of-two scale per operand (R, Cop), chosen so
+// that the operand's largest entry lies just below 1: every entry is within
+// fp16's range (entries below 2^-14 of the largest are subnormal, with an
+// absolute error below 2^-25 of it, far inside the complex64 tolerance, which
+// is relative to max |psi|).  A first kernel finds the two largest magnitudes
+// (atomic maxima of the non-negative float bits), the split kernel then
+// writes v 2^-e = hi + lo in fp16, and the epilogue multiplies by 2^(e_R + e_C).
+__device__ __forceinline__ float f16_operand(const float2* __restrict__ A, const float2* __restrict__ B,
+                                             int64_t NA, int64_t NB, int K,
+                                             const int32_t* __restrict__ aidx,
+                                             const int32_t* __restrict__ bidx, int64_t row, int kk) {
+  if (kk >= 2 * K) return 0.f;
+  if (row < NB) {
+    const float2 b = B[(int64_t)bidx[kk % K] * NB + row];
+    return kk < K ? b.x : b.y;
+  }
+  const int64_t n = row - NB;
+  const float2 a = A[(int64_t)aidx[kk % K] * NA + (n >> 1)];
+  if ((n & 1) == 0) return kk < K ? a.x : -a.y;
+  return kk < K ? a.y : a.x;
+}
+
+__global__ void __launch_bounds__(256)
+    operand_absmax_f16(const float2* __restrict__ A, const float2* __restrict__ B, int qa, int qb,
+                       int K, const int32_t* __restrict__ aidx, const int32_t* __restrict__ bidx,
+                       unsigned int* __restrict__ maxbits) {
+  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= NB + 2 * NA) return;
+  float mx = 0.f;
+  for (int kk = lane; kk < 2 * K; kk += 32) mx = fmaxf(mx, fabsf(f16_operand(A, B, NA, NB, K, aidx, bidx, row, kk)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.f) atomicMax(maxbits + (row < NB ? 0 : 1), __float_as_uint(mx));
+}
+
+__global__ void __launch_bounds__(256)
+    split_operands_f16(const float2* __restrict__ A, const float2* __restrict__ B, int qa, int qb,
+                       int K, int KR, const int32_t* __restrict__ aidx,
+                       const int32_t* __restrict__ bidx, __half* __restrict__ r_ops,
+                       __half* __restrict__ c_ops, const unsigned int* __restrict__ maxbits) {
+  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= NB + 2 * NA) return;
+  const bool is_r = row < NB;
+  const int e = f16_scale_exp(maxbits[is_r ? 0 : 1]);
+  const float down = __uint_as_float((uint32_t)(127 - e) << 23);  // 2^-e
+  const int64_t n = row - NB;
+  __half* hi = is_r ? r_ops + row * KR : c_ops + n * KR;
+  __half* lo = is_r ? r_ops + (NB + row) * KR : c_ops + (2 * NA + n) * KR;
+  for (int kk = lane; kk < KR; kk += 32) {
+    const float v = f16_operand(A, B, NA, NB, K, aidx, bidx, row, kk) * down;
+    const __half h = __float2half_rn(v);
+    hi[kk] = h;
+    lo[kk] = __float2half_rn(v - __half2float(h));
+  }
+}
+
 // One warp per operand row; lanes walk the padded K range.  Rows [0, NB) are
 // the row operand R, rows [NB, NB + 2 NA) the column operand Cop.
 template <typename E>
@@ -689,11 +765,11 @@ void* tc_kernel_ptr(int kbb) {
 }
 
 int kr_of(int64_t K, int form) {
-  const int kelem = form == CC_MERGE_BF16X3 ? KB_BYTES / 2 : KB_BYTES / 4;
+  const int kelem = form != CC_MERGE_TF32X3 ? KB_BYTES / 2 : KB_BYTES / 4;
   return (int)(((2 * K + kelem - 1) / kelem) * kelem);
 }
 
-int elem_bytes(int form) { return form == CC_MERGE_BF16X3 ? 2 : 4; }
+int elem_bytes(int form) { return form == CC_MERGE_TF32X3 ? 4 : 2; }
 
 }  // namespace
 
@@ -701,7 +777,9 @@ uint64_t merge_tc_workspace_bytes(int qa, int qb, int64_t K, int form) {
   if (qa < 7 || qb < 7 || K < 1 || K > (1 << 20)) return 0;
   const uint64_t kr = (uint64_t)kr_of(K, form);
   const uint64_t rows = 2 * ((uint64_t(1) << qb) + 2 * (uint64_t(1) << qa));
-  return rows * kr * elem_bytes(form) + 1024;
+  // fp16: the two operand maxima after the operands (1024-aligned)
+  const uint64_t scales = form == CC_MERGE_F16X3 ? 1024 + 1024 : 0;
+  return rows * kr * elem_bytes(form) + scales + 1024;
 }
 
 cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint64_t ws_bytes,
@@ -729,7 +807,18 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
 
   const int64_t rows = NB + 2 * NA;
   const unsigned blocks = (unsigned)((rows + 7) / 8);
-  if (form == CC_MERGE_BF16X3)
+  unsigned int* f16_maxbits = nullptr;
+  if (form == CC_MERGE_F16X3) {
+    f16_maxbits = reinterpret_cast<unsigned int*>(
+        (reinterpret_cast<uintptr_t>(ws) + (uint64_t)2 * rows * KR * eb + 1023) & ~uintptr_t(1023));
+    const cudaError_t me = cudaMemsetAsync(f16_maxbits, 0, 2 * sizeof(unsigned int), s);
+    if (me != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(me));
+    operand_absmax_f16<<<blocks, 256, 0, s>>>((const float2*)st.A, (const float2*)st.B, st.qa,
+                                              st.qb, (int)st.K, st.aidx, st.bidx, f16_maxbits);
+    split_operands_f16<<<blocks, 256, 0, s>>>(
+        (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
+        (__half*)r_ops, (__half*)c_ops, f16_maxbits);
+  } else if (form == CC_MERGE_BF16X3)
     split_operands<uint16_t><<<blocks, 256, 0, s>>>(
         (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
         (uint16_t*)r_ops, (uint16_t*)c_ops);
@@ -739,8 +828,9 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
         (uint32_t*)r_ops, (uint32_t*)c_ops);
 
   CUtensorMap map_r, map_c, map_out;
-  const CUtensorMapDataType dt =
-      form == CC_MERGE_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = form == CC_MERGE_BF16X3  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : form == CC_MERGE_F16X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint32_t box_k = (cuuint32_t)(KB_BYTES / eb);
   const cuuint32_t estr[2] = {1, 1};
   {
@@ -803,6 +893,7 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     for (int b = 32; b <= 128; b *= 2) {
       cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_BF16X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
       cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_TF32X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_F16X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     }
     attr_done[dev] = 1;
   }
@@ -819,19 +910,23 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   // blocks) leaves room for at least two 32 KB column stages.
   const int r_bytes = 2 * kblocks * R_TILE;
   const int rs_stages = std::min(RS_MAX_STAGES, (SMEM_LIMIT - 1024 - 256 - STG_TOTAL - r_bytes) / RS_C_STAGE);
-  if (rs_stages >= 2 && kblocks <= group_kb && tc_stationary_requested()) {
+  if (rs_stages >= 2 && kblocks <= group_kb && tc_stationary_requested() &&
+      form != CC_MERGE_F16X3) {
     const int smem_rs = r_bytes + rs_stages * RS_C_STAGE + STG_TOTAL + 1024 + 256;
     auto kern = form == CC_MERGE_BF16X3 ? merge_tc_rs_kernel<CC_MERGE_BF16X3>
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
     kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
   } else {
-    const void* kern = form == CC_MERGE_BF16X3 ? tc_kernel_ptr<CC_MERGE_BF16X3>(kbb)
-                                               : tc_kernel_ptr<CC_MERGE_TF32X3>(kbb);
+    const void* kern = form == CC_MERGE_BF16X3  ? tc_kernel_ptr<CC_MERGE_BF16X3>(kbb)
+                       : form == CC_MERGE_F16X3 ? tc_kernel_ptr<CC_MERGE_F16X3>(kbb)
+                                                : tc_kernel_ptr<CC_MERGE_TF32X3>(kbb);
     const int kb_n = KR * eb / kbb;
-    const int gkb = form == CC_MERGE_TF32X3 ? std::max(1, (int)(2 * kTf32GroupTerms * eb / kbb))
+    // 3xTF32 and 3xFP16 (11-bit significands): at most 64 terms per accumulation
+    const int gkb = form != CC_MERGE_BF16X3 ? std::max(1, (int)(2 * kTf32GroupTerms * eb / kbb))
                                             : kb_n;
     int a_rows = n_rows, a_cols = n_cols, a_kb = kb_n, a_gkb = std::min(gkb, kb_n);
-    void* args[] = {&map_r_k, &map_c_k, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err};
+    const unsigned int* a_mb = f16_maxbits;
+    void* args[] = {&map_r_k, &map_c_k, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err, &a_mb};
     const cudaError_t le = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(192), args, SMEM_BYTES, s);
     if (le != cudaSuccess)
       return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(le));

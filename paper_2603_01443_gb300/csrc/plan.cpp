@@ -298,8 +298,9 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
       // operands of a tensor-core form for the last (2^q-sized) stage.
       p->chain_ws_amps = u_max;
       const auto& last = p->stages.back();
-      const uint64_t tc = std::max(merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_TF32X3),
-                                   merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_BF16X3));
+      const uint64_t tc = std::max({merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_TF32X3),
+                                    merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_BF16X3),
+                                    merge_tc_workspace_bytes(last.qa, last.qb, last.K, CC_MERGE_F16X3)});
       const uint64_t oz = merge_ozaki_workspace_bytes(last.qa, last.qb, last.K);
       p->workspace_bytes = 2 * u_max * ab + (precision == CC_C64 ? tc : oz);
     }

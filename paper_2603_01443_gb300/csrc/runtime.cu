@@ -285,8 +285,9 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
     return fail(CC_EINVAL, "buffers must be 16-byte aligned");
   if (seg_bytes < p->seg_buf_bytes) return fail(CC_EBUFSIZE, "seg_buf too small");
   if (psi_bytes < p->psi_bytes) return fail(CC_EBUFSIZE, "psi too small");
-  if (form < CC_MERGE_AUTO || form > CC_MERGE_OZAKI) return fail(CC_EINVAL, "unknown merge form");
-  if ((form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3) && p->precision != CC_C64)
+  if (form < CC_MERGE_AUTO || form > CC_MERGE_F16X3) return fail(CC_EINVAL, "unknown merge form");
+  if ((form == CC_MERGE_TF32X3 || form == CC_MERGE_BF16X3 || form == CC_MERGE_F16X3) &&
+      p->precision != CC_C64)
     return fail(CC_EINVAL, "tensor-core merge forms need a complex64 plan");
   if (form == CC_MERGE_OZAKI && p->precision != CC_C128)
     return fail(CC_EINVAL, "the Ozaki merge form needs a complex128 plan");
@@ -321,13 +322,13 @@ extern "C" cc_status cc_merge(const cc_plan* p, const void* seg_buf, uint64_t se
       continue;
     }
     // AUTO: the CUDA-core form while the merge is store-bound (K below
-    // kAutoTcMinTerms), else 3xTF32 (long K summed in groups of 64 terms, see
+    // kAutoTcMinTerms), else 3xFP16 (long K summed in groups of 64 terms, see
     // merge_tc.cu).
     // complex128: the Ozaki tensor-core form wherever it applies.
     int f = form;
     if (f == CC_MERGE_AUTO) {
       if (p->precision == CC_C64)
-        f = (sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7) ? CC_MERGE_TF32X3 : CC_MERGE_FMA;
+        f = (sg.K >= kAutoTcMinTerms && sg.qa >= 7 && sg.qb >= 7) ? kAutoTcForm : CC_MERGE_FMA;
       else
         f = (sg.K >= kAutoOzakiMinTerms && sg.qa >= 7 && sg.qb >= 7) ? CC_MERGE_OZAKI
                                                                        : CC_MERGE_FMA;

@@ -106,7 +106,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 template <int KIND>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
                                      uint32_t accumulate) {
-  if (KIND == CC_MERGE_BF16X3) {
+  if (KIND == CC_MERGE_BF16X3 || KIND == CC_MERGE_F16X3) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),

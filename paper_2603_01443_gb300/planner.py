@@ -28,13 +28,13 @@ import torch
 from . import capi
 
 STAGES = ("pre", "sub", "merge", "orig")
-FORMS = ("fma", "tf32x3", "bf16x3", "ozaki")
+FORMS = ("fma", "tf32x3", "f16x3", "bf16x3", "ozaki")
 FEATURES = ("q", "log2_depth", "n", "cut_bits", "log2_n_sub", "max_seg_bits",
             "log2_dense_gates", "log2_two_qubit_gates", "seg_tile_bits") + tuple(
                 "form_" + f for f in FORMS)
 # max |dpsi| / max |psi| each merge form guarantees (cc_merge_form): the
 # planner only picks a form whose bound meets the caller's tolerance
-FORM_TOL = {"fma": 0.0, "tf32x3": 2e-6, "bf16x3": 5e-5, "ozaki": 1e-12}
+FORM_TOL = {"fma": 0.0, "tf32x3": 2e-6, "f16x3": 2e-6, "bf16x3": 5e-5, "ozaki": 1e-12}
 
 
 def threshold(q: float, n: int) -> float:

@@ -13,7 +13,7 @@ from gpu_util import FID_TOL, TOL, fidelity, rel_err
 
 pytestmark = pytest.mark.gpu
 
-FORM_TOL = {"tf32x3": TOL["c64"], "bf16x3": TOL["bf16x3"]}
+FORM_TOL = {"tf32x3": TOL["c64"], "bf16x3": TOL["bf16x3"], "f16x3": TOL["c64"]}
 
 
 def run(gates, q, segs, form, decomp="projector"):
@@ -34,7 +34,8 @@ DEEP = [([8, 8], 7), ([8, 8], 8), ([8, 8], 10), ([8, 8], 12), ([9, 10], 9)]
 
 
 @pytest.mark.parametrize("form,segs,c", [("tf32x3",) + x for x in CASES + DEEP] +
-                         [("bf16x3",) + x for x in CASES + DEEP])
+                         [("bf16x3",) + x for x in CASES + DEEP] +
+                         [("f16x3",) + x for x in CASES + DEEP])
 def test_tc_merge_vs_oracle(cuda_lib, form, segs, c):
     q = sum(segs)
     gates = w.brickwork_cut(q, 12, 21 + c, segs, c)
@@ -46,7 +47,7 @@ def test_tc_merge_vs_oracle(cuda_lib, form, segs, c):
     assert 1 - fidelity(got, ref) <= FID_TOL
 
 
-@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "f16x3"])
 def test_tc_merge_matches_fma_at_scale(cuda_lib, form):
     q, segs, c = 26, [13, 13], 6
     gates = w.brickwork_cut(q, 16, 3, segs, c)
@@ -79,10 +80,11 @@ def test_tf32x3_deep_merge_matches_fma_at_scale(cuda_lib):
     assert st["max_abs_diff"] <= TOL["c64"] * st["max_abs_b"], st
     assert 1 - st["fidelity"] <= FID_TOL
     psi_auto, _ = run(gates, q, segs, "auto")
-    assert torch.equal(psi_auto, psi_tc)  # AUTO picks 3xTF32 at K = 256
+    psi_f16, _ = run(gates, q, segs, "f16x3")
+    assert torch.equal(psi_auto, psi_f16)  # AUTO picks 3xFP16 at K = 256
 
 
-@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "auto"])
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "f16x3", "auto"])
 def test_tc_last_stage_of_chained_merge(cuda_lib, form):
     # n = 3: the last stage (2^q output, K = 2^4 terms) runs on tensor cores
     segs = [6, 7, 7]
@@ -108,7 +110,7 @@ def test_tc_forms_stationary_and_streaming(cuda_lib, monkeypatch, stationary, fo
     assert rel_err(psi.cpu().numpy(), ref) <= FORM_TOL[form]
 
 
-@pytest.mark.parametrize("form", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "f16x3"])
 @pytest.mark.parametrize("segs,c", [([7, 8], 4), ([9, 10], 6), ([10, 9], 8), ([8, 11], 5),
                                     ([9, 9], 10)])
 def test_tc_kblock_forms(cuda_lib, monkeypatch, form, segs, c):
@@ -127,3 +129,16 @@ def test_tc_kblock_forms(cuda_lib, monkeypatch, form, segs, c):
             first = psi
         else:
             assert torch.equal(psi, first), kblock
+
+
+def test_f16x3_scales_keep_tiny_rows_accurate(cuda_lib):
+    # the fp16 form scales each operand row by a power of two: factors whose
+    # amplitudes span many orders of magnitude (a basis-state-like segment
+    # next to spread ones) keep the complex64 tolerance
+    q, segs = 18, [9, 9]
+    gates = [w.Gate("X", 2), w.Gate("H", 8), w.Gate("CZ", 8, 9)]
+    gates += w.brickwork(18, 3, 77)
+    gates += [w.Gate("CZ", 8, 9), w.Gate("H", 9), w.Gate("T", 9), w.Gate("CZ", 8, 9)]
+    psi, _ = run(gates, q, segs, "f16x3")
+    ref = sv.simulate(q, gates)
+    assert rel_err(psi.cpu().numpy(), ref) <= TOL["c64"]

@@ -166,8 +166,8 @@ def test_planner_decide_filters_forms_and_falls_back():
     P = planner.StagePlanner.__new__(planner.StagePlanner)
     P.fallback_spread = P.fallback_error = 0.2
     P.hold_x = None
-    opts = [{"n": 2, "form": f, "seg_tile_bits": 13, "features": [float(i)], "cut_bits": 4,
-             "n_sub": 32} for i, f in enumerate(("fma", "tf32x3", "bf16x3"))]
+    opts = [{"n": 2, "form": f, "seg_tile_bits": 13, "features": [float(planner.FORMS.index(f))],
+             "cut_bits": 4, "n_sub": 32} for f in ("fma", "tf32x3", "bf16x3")]
     cut = {"fma": 3.0, "tf32x3": 2.0, "bf16x3": 1.0}
 
     def predict(X):
