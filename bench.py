@@ -1183,7 +1183,8 @@ def main(argv=None):
     # per step: one persistent launch for every segment pass, the earlier
     # chain stages (FMA), the last stage (split + tensor-core kernel, or FMA),
     # the uncut passes, and the two verification kernels
-    launches = 1 + (info["n_seg"] - 2) + (2 if tc_form != "fma" else 1) + n_pass + 2
+    merge_launches = {"fma": 1, "f16x3": 3}.get(tc_form, 2)  # f16x3: maxima, split, merge
+    launches = 1 + (info["n_seg"] - 2) + merge_launches + n_pass + 2
     # subcircuit stage (Algorithm 2): N_sub variants of 2^{q_i} amplitudes, 16
     # flops per amplitude per dense one-qubit gate of the segment, 6 per
     # diagonal factor (CZ inside the segment, the cut terms on its side)
