@@ -103,6 +103,58 @@ def kernel_source_hash(files):
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no measured figure; nominal)
 
+# FP32-pipe instructions per amplitude for each operation the pass kernels
+# execute on every amplitude of the vector, by gate arithmetic: a dense 2x2
+# (one complex row: a product and three multiply-adds per real), a
+# tangent-form rotation (one multiply-add per real) and a complex product (a
+# phase block's or a table term's factor: two products, two multiply-adds).
+# Double-float: y + t x costs 15 FP32 instructions (TwoProduct 2, TwoSum 6,
+# cross terms and low sums 4, Fast2Sum 3), a product 7, so a rotation costs
+# 2 x 15, a complex product 2 x 15 + 2 x 7, a dense row 2 x (3 x 15 + 7).
+PASS_INST = {"f32": {"dense": 8, "rot": 2, "cmul": 4},
+             "dfl": {"dense": 2 * (3 * 15 + 7), "rot": 2 * 15, "cmul": 2 * 15 + 2 * 7}}
+# the same operations in flops of their own precision (a multiply-add counts 2)
+PASS_FLOPS = {"dense": 14, "rot": 4, "cmul": 6}
+
+
+def program_ops(words):
+    """Per-amplitude operation counts of a gate program (its image as
+    cc_program_image lays it out): every op of every stage of every pass is
+    applied once to each of the program's 2^nq amplitudes."""
+    wd = [int(x) for x in words]
+    nq, n_pass, n_stage, n_op = wd[1], wd[3], wd[4], wd[5]
+    i = 9 + 74 * n_pass + 10 * n_stage  # header, passes, stages
+    c = {"dense": 0, "rot": 0, "cmul": 0, "nq": nq}
+    for _ in range(n_op):
+        typ, n_phase, n_table = wd[i], wd[i + 4], wd[i + 5]
+        i += 8
+        if typ == 0:
+            c["dense"] += 1
+        elif typ in (2, 3):
+            c["rot"] += 1
+        c["cmul"] += (1 if n_phase else 0) + n_table
+    return c
+
+
+def executed_work(counts, arith):
+    """(FP32-pipe instructions, flops) of a program over its whole vector."""
+    n = float(1 << counts["nq"])
+    inst = sum(PASS_INST[arith][k] * counts[k] for k in PASS_FLOPS) * n
+    flops = sum(PASS_FLOPS[k] * counts[k] for k in PASS_FLOPS) * n
+    return inst, flops
+
+
+def gate_arith(prec):
+    """The gate-pass arithmetic the library picks for a precision."""
+    if prec == "c64":
+        return "f32"
+    return "f64" if os.environ.get("CUTSIM_C128_GATES") == "fp64" else "dfl"
+
+
+def fp32_inst_rate(sm_mhz=2070.0, sms=152):
+    """FP32 instructions per second: SMs x 128 lanes x clock."""
+    return sms * 128 * sm_mhz * 1e6
+
 
 def traffic_key(kernel, a):
     return f"{kernel}@q{a.q}_d{a.depth}_n{a.n}_c{a.ctotal}_{a.prec}"
@@ -1126,14 +1178,38 @@ def main(argv=None):
     uncut_flops = 16.0 * n_dense * n_amp
     if a.prec == "c64":
         alu_peak, alu_src = fp32_peak_tflops(), "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
-    else:  # complex128 runs on the FP64 pipes
+    else:  # complex128 in native FP64 (CUTSIM_C128_GATES=fp64) runs on the FP64 pipes
         alu_peak, alu_src = FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 (no measured FP64 peak)"
+    arith = gate_arith(a.prec)
+    inst_rate = fp32_inst_rate()
+
+    def executed(inst, flops, secs):
+        # FP32-pipe instructions the program's arithmetic needs at least,
+        # against the pipes' instruction rate over the measured time
+        return {"fp32_inst_per_launch": inst, "flops_per_launch": flops,
+                "achieved_tflops": flops / secs / 1e12, "inst_per_s": inst / secs,
+                "inst_peak_per_s": inst_rate, "frac": inst / secs / inst_rate,
+                "arith": arith}
+
     pass_tf = uncut_flops / n_pass / pass_s / 1e12
     pass_rf = {"bound": "alu", "achieved": pass_tf, "peak": alu_peak, "unit": "TFLOP/s",
                "frac": pass_tf / alu_peak, "traffic": recorded_traffic("uncut_pass", a),
                "kernel": "stage_kernel (uncut passes)", "flops_per_launch": uncut_flops / n_pass,
                "launch_s": pass_s, "hbm_gbs": pass_gbs, "hbm_bytes_per_launch": pass_bytes,
                "peak_source": alu_src}
+    if arith != "f64":
+        ui, uf = executed_work(program_ops(api.program_image(gates, a.q, a.prec)[0]), arith)
+        pass_rf["executed"] = executed(ui / n_pass, uf / n_pass, pass_s)
+    if arith == "dfl":
+        # double-float: the FP32 pipes run the complex128 arithmetic; its
+        # peak is the flops of this op mix at the full FP32 instruction rate
+        ex = pass_rf["executed"]
+        pass_rf.update({"achieved": ex["achieved_tflops"], "frac": ex["frac"],
+                        "peak": ex["flops_per_launch"] / ex["fp32_inst_per_launch"] * inst_rate / 1e12,
+                        "flops_per_launch": ex["flops_per_launch"],
+                        "peak_source": "double-float on the FP32 pipes: 152 SMs x 128 lanes x "
+                                       "2070 MHz instructions, at this program's instructions "
+                                       "per flop"})
     # AUTO's rule (the library's kAutoTcMinTerms): 3xTF32 from K = 8 terms on
     # AUTO's rule (the library's kAutoTcMinTerms / kAutoOzakiMinTerms): 3xTF32
     # from K = 8 terms on for complex64, the Ozaki form from K = 2 on for complex128
@@ -1213,6 +1289,18 @@ def main(argv=None):
               "kernel": "batch_kernel (all passes of all segments, one persistent launch)",
               "flops_per_launch": seg_flops, "launch_s": mean["sub"],
               "bytes_written": float(info["seg_buf_bytes"]), "peak_source": alu_src}
+    if arith != "f64":
+        si = sf = 0.0
+        for i in range(info["n_seg"]):
+            words, _ = api.plan_program_image(gates, a.q, segs, i, a.decomp, a.prec)
+            x, y = executed_work(program_ops(words), arith)
+            si, sf = si + x, sf + y
+        seg_rf["executed"] = executed(si, sf, mean["sub"])
+        if arith == "dfl":
+            ex = seg_rf["executed"]
+            seg_rf.update({"achieved": ex["achieved_tflops"], "frac": ex["frac"],
+                           "peak": sf / si * inst_rate / 1e12, "flops_per_launch": sf,
+                           "peak_source": pass_rf["peak_source"]})
     cmp = rec["cmp"][-1]
     orc = None
     if not a.no_cpu_baseline:
@@ -1247,7 +1335,7 @@ def main(argv=None):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if a.prec == "c64" else "f64",
+        "dtype": {"f32": "f32", "dfl": "f32x2 (double-float)", "f64": "f64"}[arith],
         "data": "synthetic",
         "config": dict(cfg, l2=("not flushed explicitly: every step writes the 2^q uncut vector "
                                 "and reads both 2^q vectors (>> 129 MB L2) between merges")),

@@ -37,6 +37,7 @@ using PlanPtr = std::unique_ptr<cc_plan, PlanDeleter>;
 // Everything that depends on the tile width and the merge tile shape.
 struct Core {
   int tile_bits = 0, merge_rows = 32;
+  int arith = 0;  // gate-pass arithmetic of the plans' device images
   std::vector<PlanPtr> plans;
   void* arena = nullptr;
   const BJob* jobs = nullptr;
@@ -111,6 +112,7 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
     }
     c->plans.emplace_back(p);
   }
+  c->arith = c->plans.empty() ? gate_arith(b->precision) : c->plans[0]->arith;
 
   if (b->seg_base.empty()) {  // buffer layout: the same for every tile width
     uint64_t so = 0, po = 0, wo = 0;
@@ -269,7 +271,7 @@ cc_status build_core(cc_batch* b, int tile_bits, int merge_rows, std::unique_ptr
   c->circ_done = c->done + n_done;
   c->head = reinterpret_cast<unsigned long long*>(d + o_head);
 
-  const int occ = batch_segments_occupancy(b->precision, c->block, c->smem);
+  const int occ = batch_segments_occupancy(c->arith, c->block, c->smem);
   if (occ < 1) return fail(CC_ECUDA, "the batched gate-pass kernel does not fit on an SM");
   c->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms() * occ));
   if (!device_error_flag()) return fail(CC_ENOMEM, "device error flag allocation failed");
@@ -297,7 +299,7 @@ cc_status run_core(const cc_batch* b, const Core& c, void* seg, void* psi, void*
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
   unsigned long long* st = reinterpret_cast<unsigned long long*>(stamps);
   cc_status r = launch_batch_segments(seg, c.jobs, c.n_jobs, c.n_items, c.done, c.head, st,
-                                      b->precision, c.block, c.smem, c.grid, stream);
+                                      c.arith, c.block, c.smem, c.grid, stream);
   if (r != CC_OK) return r;
   const int ab = amp_bytes(b->precision);
   char* const bufs[3] = {static_cast<char*>(seg), static_cast<char*>(work), static_cast<char*>(psi)};

@@ -102,11 +102,23 @@ struct DPass {
   int32_t rbits;       // register bits per thread: 2^rbits amplitudes, 2^(k - rbits) threads
   int32_t n_rest;      // nq - k
   uint32_t zero_tile;  // init: tile bits that are state qubits (must be 0 for amplitude 1)
-  uint32_t pad;
+  uint32_t flags;      // PASS_LAST: the program's last pass
   uint64_t zero_rest;  // init: bits of T that are state qubits
   int8_t tile_bit[MAX_TILE_BITS];  // vector bit of tile bit t
   int8_t rest_bit[MAX_REST_BITS];  // vector bit of the r-th non-tile bit
 };
+
+// The last pass of a program stores its vector in the precision's own layout;
+// a double-float program's earlier passes store (h, l) pairs.
+constexpr uint32_t PASS_LAST = 1u;
+
+// Arithmetic of the gate passes.  Complex64 runs in FP32; complex128 runs in
+// double-float pairs on the FP32 pipes (GA_DFL, about 48 significant bits)
+// unless CUTSIM_C128_GATES=fp64 selects native FP64.  A program's device
+// image holds its reals in the arithmetic's layout: FP32, FP64, or an
+// (h, l) float pair in each 8-byte slot.
+enum GateArith : int { GA_F32 = 0, GA_F64 = 1, GA_DFL = 2 };
+int gate_arith(int precision);
 
 struct HostProgram {
   int nq = 0;       // vector bits (state qubits + variant bits)
@@ -166,17 +178,18 @@ struct DeviceProgram {
 struct ImageLayout {
   size_t base, o_pass, o_stages, o_ops, o_terms, o_mats, o_tabs, end;
 };
-// Append hp's image (reals in the plan's precision) to img, 256-byte aligned.
-ImageLayout append_program_image(const HostProgram& hp, int precision,
+// Append hp's image (reals in the layout of the gate arithmetic) to img,
+// 256-byte aligned.
+ImageLayout append_program_image(const HostProgram& hp, int arith,
                                  std::vector<unsigned char>& img);
 // Point dp at an uploaded image (dev_base = device copy of img); dp does not own it.
 void bind_program(DeviceProgram& dp, const HostProgram& hp, unsigned char* dev_base,
                   const ImageLayout& L);
-cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp);
+cc_status upload_program(const HostProgram& hp, int arith, DeviceProgram& dp);
 void free_program(DeviceProgram& dp);
 
 // Launch every pass of a program over the 2^nq-amplitude vector at `state`.
-cc_status run_program(const DeviceProgram& dp, int precision, void* state, void* stream);
+cc_status run_program(const DeviceProgram& dp, int arith, void* state, void* stream);
 
 // Largest tile (bits) a pass may use: 2^k amplitudes in shared memory.
 int max_tile_bits(int precision);
@@ -207,10 +220,10 @@ struct BJob {
 // %globaltimer value when the first item is taken.
 cc_status launch_batch_segments(void* seg_buf, const BJob* jobs, int n_jobs, int64_t n_items,
                                 int* done, unsigned long long* head,
-                                unsigned long long* stamps, int precision, int block,
+                                unsigned long long* stamps, int arith, int block,
                                 size_t smem, int grid, void* stream);
 // CTAs per SM the batched segment kernel reaches with this block and shared memory.
-int batch_segments_occupancy(int precision, int block, size_t smem);
+int batch_segments_occupancy(int arith, int block, size_t smem);
 
 // One merge stage of one circuit inside a batched merge launch; operands are
 // offsets (in amplitudes) into one of three caller buffers.

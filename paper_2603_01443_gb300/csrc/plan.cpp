@@ -123,6 +123,7 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     p->q = q;
     p->n_seg = n_seg;
     p->precision = precision;
+    p->arith = gate_arith(precision);
     p->decomp = decomp;
     int acc = 0;
     for (int i = 0; i < n_seg; ++i) {
@@ -316,7 +317,7 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     if (st != CC_OK) return st;
     std::vector<unsigned char> img;
     std::vector<ImageLayout> lay;
-    for (int i = 0; i < n_seg; ++i) lay.push_back(append_program_image(p->hprog[i], precision, img));
+    for (int i = 0; i < n_seg; ++i) lay.push_back(append_program_image(p->hprog[i], p->arith, img));
     const size_t tab_off = (img.size() + 255) & ~size_t(255);
     img.resize(tab_off + tab.size() * sizeof(int32_t));
     if (!tab.empty()) std::memcpy(img.data() + tab_off, tab.data(), tab.size() * sizeof(int32_t));
@@ -384,7 +385,7 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     p->seg_n_items = n_items;
     p->seg_block = block;
     p->seg_smem = (size_t)ab << kmax;
-    const int occ = batch_segments_occupancy(precision, block, p->seg_smem);
+    const int occ = batch_segments_occupancy(p->arith, block, p->seg_smem);
     p->seg_grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)num_sms() * std::max(occ, 1)));
     if (!device_error_flag()) return fail(CC_ENOMEM, "device error flag allocation failed");
     p->tables_dev = tab.empty() ? nullptr : dev + tab_off;
@@ -453,6 +454,7 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
     std::unique_ptr<cc_uncut> u(new cc_uncut());
     u->q = q;
     u->precision = precision;
+    u->arith = gate_arith(precision);
     std::vector<Item> items;
     items.reserve((size_t)n_gates);
     for (int g = 0; g < n_gates; ++g) {
@@ -464,7 +466,7 @@ extern "C" cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int3
     if (u->hprog.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
     st = check_device();
     if (st != CC_OK) return st;
-    st = upload_program(u->hprog, precision, u->dprog);
+    st = upload_program(u->hprog, u->arith, u->dprog);
     if (st != CC_OK) return st;
     *out = u.release();
     return CC_OK;

@@ -38,6 +38,7 @@ struct cc_plan {
   };
 
   int q = 0, n_seg = 0, c_total = 0, precision = 0, decomp = 0;
+  int arith = 0;  // gate-pass arithmetic (cc::GateArith) the device images are laid out for
   std::vector<int> seg_q, seg_start, seg_c;
   std::vector<int64_t> seg_off;
   struct Bit {
@@ -70,6 +71,7 @@ struct cc_plan {
 
 struct cc_uncut {
   int q = 0, precision = 0;
+  int arith = 0;  // gate-pass arithmetic (cc::GateArith)
   cc::HostProgram hprog;
   cc::DeviceProgram dprog;
   ~cc_uncut();

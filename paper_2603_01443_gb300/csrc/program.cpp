@@ -787,6 +787,7 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
   for (int j = 0; j < nq; ++j) all_bits[j] = j;
   if (nq <= kmax) {
     add_pass(hp, items, bits, order, all_bits, true, rb_max);
+    if (hp.nq > 0) hp.passes.back().flags |= PASS_LAST;
     return hp;
   }
   low = std::min(low, kmax);
@@ -814,6 +815,7 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
     if (hp.nq < 0) return hp;
     first = false;
   }
+  hp.passes.back().flags |= PASS_LAST;
   return hp;
 }
 

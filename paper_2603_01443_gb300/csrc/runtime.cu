@@ -160,9 +160,9 @@ int uncut_tile_bits(int precision) {
   return k;
 }
 
-ImageLayout append_program_image(const HostProgram& hp, int precision,
+ImageLayout append_program_image(const HostProgram& hp, int arith,
                                  std::vector<unsigned char>& img) {
-  const size_t rb = precision == CC_C128 ? 8 : 4;
+  const size_t rb = arith == GA_F32 ? 4 : 8;
   ImageLayout L;
   L.base = (img.size() + 255) & ~size_t(255);
   L.o_pass = 0;
@@ -180,7 +180,14 @@ ImageLayout append_program_image(const HostProgram& hp, int precision,
   std::memcpy(p0 + L.o_terms, hp.terms.data(), hp.terms.size() * sizeof(DTerm));
   auto put = [&](size_t off, const std::vector<cd>& v) {
     for (size_t i = 0; i < v.size(); ++i) {
-      if (rb == 8) {
+      if (arith == GA_DFL) {  // h = fl32(x), l = fl32(x - h)
+        float* p = reinterpret_cast<float*>(p0 + off) + 4 * i;
+        const double re = v[i].real(), im = v[i].imag();
+        p[0] = (float)re;
+        p[1] = (float)(re - (double)p[0]);
+        p[2] = (float)im;
+        p[3] = (float)(im - (double)p[2]);
+      } else if (rb == 8) {
         double* p = reinterpret_cast<double*>(p0 + off) + 2 * i;
         p[0] = v[i].real();
         p[1] = v[i].imag();
@@ -217,9 +224,9 @@ void bind_program(DeviceProgram& dp, const HostProgram& hp, unsigned char* dev_b
   dp.n_ops = (int)hp.ops.size();
 }
 
-cc_status upload_program(const HostProgram& hp, int precision, DeviceProgram& dp) {
+cc_status upload_program(const HostProgram& hp, int arith, DeviceProgram& dp) {
   std::vector<unsigned char> img;
-  const ImageLayout L = append_program_image(hp, precision, img);
+  const ImageLayout L = append_program_image(hp, arith, img);
   void* base = device_alloc_copy(img.data(), img.size());
   if (!base) return fail(CC_ENOMEM, "device allocation of a gate program failed");
   bind_program(dp, hp, static_cast<unsigned char*>(base), L);
@@ -262,7 +269,7 @@ extern "C" cc_status cc_simulate_segments(const cc_plan* p, void* seg_buf, uint6
     const int ab = amp_bytes(p->precision);
     for (int i = 0; i < p->n_seg; ++i) {
       char* base = static_cast<char*>(seg_buf) + p->seg_off[i] * ab;
-      st = run_program(p->dprog[i], p->precision, base, stream);
+      st = run_program(p->dprog[i], p->arith, base, stream);
       if (st != CC_OK) return st;
     }
     return CC_OK;
@@ -272,7 +279,7 @@ extern "C" cc_status cc_simulate_segments(const cc_plan* p, void* seg_buf, uint6
   const cudaError_t e = cudaMemsetAsync(p->seg_state, 0, p->seg_state_bytes, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
   return launch_batch_segments(seg_buf, p->seg_jobs, p->seg_n_jobs, p->seg_n_items, p->seg_done,
-                               p->seg_head, nullptr, p->precision, p->seg_block, p->seg_smem,
+                               p->seg_head, nullptr, p->arith, p->seg_block, p->seg_smem,
                                p->seg_grid, stream);
 }
 
@@ -364,7 +371,7 @@ extern "C" cc_status cc_simulate_uncut(const cc_uncut* u, void* psi, uint64_t ps
     return fail(CC_EBUFSIZE, "psi too small");
   cc_status st = check_device();
   if (st != CC_OK) return st;
-  return run_program(u->dprog, u->precision, psi, stream);
+  return run_program(u->dprog, u->arith, psi, stream);
 }
 
 extern "C" cc_status cc_compare(const void* a, const void* b, int64_t n_amp, int32_t precision,

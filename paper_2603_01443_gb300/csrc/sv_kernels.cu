@@ -19,18 +19,23 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstdio>
+#include <cstring>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace cc {
 
+// Amplitude types of the three gate-pass arithmetics: C is one amplitude in
+// registers and shared memory, V the 16-byte vector moved to and from HBM,
+// PV the amplitudes per vector.
 template <typename R>
 struct CT;
 template <>
 struct CT<float> {
   using C = float2;
   using V = float4;
-  static constexpr int PV = 2;  // amplitudes per 16-byte vector
+  static constexpr int PV = 2;
 };
 template <>
 struct CT<double> {
@@ -38,6 +43,22 @@ struct CT<double> {
   using V = double2;
   static constexpr int PV = 1;
 };
+template <>
+struct CT<dfl> {
+  using C = cdfl;
+  using V = float4;  // (re.h, re.l, im.h, im.l)
+  static constexpr int PV = 1;
+};
+
+template <typename R>
+constexpr bool is_f32() { return std::is_same<R, float>::value; }
+template <typename R>
+constexpr bool is_dfl() { return std::is_same<R, dfl>::value; }
+
+// y + t x in the pass's arithmetic (FP32 and FP64 contract it to one FMA)
+__device__ __forceinline__ float mad(float t, float x, float y) { return __fmaf_rn(t, x, y); }
+__device__ __forceinline__ double mad(double t, double x, double y) { return __fma_rn(t, x, y); }
+__device__ __forceinline__ dfl mad(dfl t, dfl x, dfl y) { return dfma(t, x, y); }
 
 namespace {
 
@@ -102,6 +123,11 @@ __device__ __forceinline__ void cmul(R& xr, R& xi, R yr, R yi) {
   xi = xr * yi + xi * yr;
   xr = t;
 }
+__device__ __forceinline__ void cmul(dfl& xr, dfl& xi, dfl yr, dfl yi) {
+  const dfl t = dfma(xr, yr, -(xi * yi));
+  xi = dfma(xr, yi, xi * yr);
+  xr = t;
+}
 
 // Slots j < 2^RB whose register bit i is set (i < 5).
 __host__ __device__ constexpr uint32_t slot_pattern(int i) {
@@ -133,7 +159,7 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
   constexpr int N = 1 << RB;
   const DTerm blk = terms[op.term_sign_end()];
   const R* tb = tabs + 8 * blk.tab;
-  const bool skip0 = sizeof(R) == 8 && !(blk.p0 & 1u);
+  const bool skip0 = !is_f32<R>() && !(blk.p0 & 1u);
   R pr = R(1), pi = R(0);
   const bool fixed = op.term_phase_end() > op.term_sign_end() + 1;
   if (fixed) {
@@ -147,13 +173,21 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
 #pragma unroll
     for (int j = 0; j < N; ++j) cmul(a[j].x, a[j].y, pr, pi);
   }
-  if constexpr (sizeof(R) == 4) {
+  if constexpr (is_f32<R>()) {
     const float4* t4 = reinterpret_cast<const float4*>(tb);
 #pragma unroll
     for (int j2 = 0; j2 < N / 2; ++j2) {
       const float4 f = __ldg(t4 + j2);
       cmul(a[2 * j2].x, a[2 * j2].y, f.x, f.y);
       cmul(a[2 * j2 + 1].x, a[2 * j2 + 1].y, f.z, f.w);
+    }
+  } else if constexpr (is_dfl<R>()) {
+    const float4* t4 = reinterpret_cast<const float4*>(tb);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      if (j == 0 && skip0) continue;
+      const float4 f = __ldg(t4 + j);
+      cmul(a[j].x, a[j].y, dfl(f.x, f.y), dfl(f.z, f.w));
     }
   } else {
     const double2* t2 = reinterpret_cast<const double2*>(tb);
@@ -218,12 +252,17 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const uint32_t m = smask << (31 - j);
-      if (sizeof(R) == 4) {
-        a[j].x = __uint_as_float(xor_sign(__float_as_uint((float)a[j].x), m));
-        a[j].y = __uint_as_float(xor_sign(__float_as_uint((float)a[j].y), m));
+      if constexpr (is_f32<R>()) {
+        a[j].x = __uint_as_float(xor_sign(__float_as_uint(a[j].x), m));
+        a[j].y = __uint_as_float(xor_sign(__float_as_uint(a[j].y), m));
+      } else if constexpr (is_dfl<R>()) {
+        a[j].x = dfl(__uint_as_float(xor_sign(__float_as_uint(a[j].x.h), m)),
+                     __uint_as_float(xor_sign(__float_as_uint(a[j].x.l), m)));
+        a[j].y = dfl(__uint_as_float(xor_sign(__float_as_uint(a[j].y.h), m)),
+                     __uint_as_float(xor_sign(__float_as_uint(a[j].y.l), m)));
       } else {
-        const long long hx = __double_as_longlong((double)a[j].x);
-        const long long hy = __double_as_longlong((double)a[j].y);
+        const long long hx = __double_as_longlong(a[j].x);
+        const long long hy = __double_as_longlong(a[j].y);
         a[j].x = __hiloint2double((int)xor_sign((uint32_t)(hx >> 32), m), (int)(uint32_t)hx);
         a[j].y = __hiloint2double((int)xor_sign((uint32_t)(hy >> 32), m), (int)(uint32_t)hy);
       }
@@ -271,11 +310,18 @@ struct Mat {
 template <typename R>
 __device__ __forceinline__ Mat<R> load_mat(const R* __restrict__ p) {
   Mat<R> m;
-  if constexpr (sizeof(R) == 4) {
+  if constexpr (is_f32<R>()) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(p));
     const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
     m.v[0] = x.x; m.v[1] = x.y; m.v[2] = x.z; m.v[3] = x.w;
     m.v[4] = y.x; m.v[5] = y.y; m.v[6] = y.z; m.v[7] = y.w;
+  } else if constexpr (is_dfl<R>()) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(p) + i);
+      m.v[2 * i] = dfl(x.x, x.y);
+      m.v[2 * i + 1] = dfl(x.z, x.w);
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -302,10 +348,17 @@ __device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const
     const int j1 = j0 | (1 << RHO);
     const C a0 = a[j0], a1 = a[j1];
     C b0, b1;
-    b0.x = u0r * a0.x - u0i * a0.y + u1r * a1.x - u1i * a1.y;
-    b0.y = u0r * a0.y + u0i * a0.x + u1r * a1.y + u1i * a1.x;
-    b1.x = u2r * a0.x - u2i * a0.y + u3r * a1.x - u3i * a1.y;
-    b1.y = u2r * a0.y + u2i * a0.x + u3r * a1.y + u3i * a1.x;
+    if constexpr (is_dfl<R>()) {
+      b0.x = mad(u0r, a0.x, mad(-u0i, a0.y, mad(u1r, a1.x, -(u1i * a1.y))));
+      b0.y = mad(u0r, a0.y, mad(u0i, a0.x, mad(u1r, a1.y, u1i * a1.x)));
+      b1.x = mad(u2r, a0.x, mad(-u2i, a0.y, mad(u3r, a1.x, -(u3i * a1.y))));
+      b1.y = mad(u2r, a0.y, mad(u2i, a0.x, mad(u3r, a1.y, u3i * a1.x)));
+    } else {
+      b0.x = u0r * a0.x - u0i * a0.y + u1r * a1.x - u1i * a1.y;
+      b0.y = u0r * a0.y + u0i * a0.x + u1r * a1.y + u1i * a1.x;
+      b1.x = u2r * a0.x - u2i * a0.y + u3r * a1.x - u3i * a1.y;
+      b1.y = u2r * a0.y + u2i * a0.x + u3r * a1.y + u3i * a1.x;
+    }
     a[j0] = b0;
     a[j1] = b1;
   }
@@ -325,7 +378,19 @@ __device__ __forceinline__ void rot_mat(typename CT<R>::C (&a)[1 << RB], R t) {
     const int j1 = j0 | (1 << RHO);
     const C a0 = a[j0], a1 = a[j1];
     C b0, b1;
-    if (COT) {
+    if constexpr (is_dfl<R>()) {
+      if (COT) {
+        b0.x = mad(t, a0.x, -a1.x);
+        b0.y = mad(t, a0.y, -a1.y);
+        b1.x = mad(t, a1.x, a0.x);
+        b1.y = mad(t, a1.y, a0.y);
+      } else {
+        b0.x = mad(-t, a1.x, a0.x);
+        b0.y = mad(-t, a1.y, a0.y);
+        b1.x = mad(t, a0.x, a1.x);
+        b1.y = mad(t, a0.y, a1.y);
+      }
+    } else if (COT) {
       b0.x = t * a0.x - a1.x;
       b0.y = t * a0.y - a1.y;
       b1.x = t * a1.x + a0.x;
@@ -520,6 +585,14 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
         }
       V v = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
       if (PV == 2 && (pl & 1u)) v = swap_pair(v);
+      if constexpr (is_dfl<R>()) {
+        if (P.flags & PASS_LAST) {  // h + l is exact in FP64
+          const float4 f = reinterpret_cast<const float4&>(v);
+          *reinterpret_cast<double2*>(vec + g) =
+              make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+          continue;
+        }
+      }
       *reinterpret_cast<V*>(vec + g) = v;
     }
   }
@@ -630,7 +703,7 @@ __global__ void __launch_bounds__(512)
         case 3: CC_BATCH_TILE(3) break;
         case 4: CC_BATCH_TILE(4) break;
         default:
-          CC_BATCH_TILE(sizeof(R) == 4 ? 5 : 4)
+          CC_BATCH_TILE(is_f32<R>() ? 5 : 4)
           break;
 #undef CC_BATCH_TILE
       }
@@ -679,7 +752,7 @@ cc_status launch_pass(const DeviceProgram& dp, int pi, void* state, cudaStream_t
     case 3: return launch_rb<R, 3>(dp, pi, state, stream);
     case 4: return launch_rb<R, 4>(dp, pi, state, stream);
     case 5:
-      return launch_rb<R, (sizeof(R) == 4 ? 5 : 4)>(dp, pi, state, stream);
+      return launch_rb<R, (is_f32<R>() ? 5 : 4)>(dp, pi, state, stream);
     default:
       break;
   }
@@ -697,13 +770,27 @@ int reg_bits_max(int precision) {
   return hi;
 }
 
-int batch_segments_occupancy(int precision, int block, size_t smem) {
-  static int attr_done[64][2] = {{0}};
+int gate_arith(int precision) {
+  if (precision != CC_C128) return GA_F32;
+  if (const char* e = std::getenv("CUTSIM_C128_GATES"))
+    if (std::strcmp(e, "fp64") == 0) return GA_F64;
+  return GA_DFL;
+}
+
+namespace {
+const void* batch_kernel_for(int arith) {
+  return arith == GA_F64   ? (const void*)batch_kernel<double>
+         : arith == GA_DFL ? (const void*)batch_kernel<dfl>
+                           : (const void*)batch_kernel<float>;
+}
+}  // namespace
+
+int batch_segments_occupancy(int arith, int block, size_t smem) {
+  static int attr_done[64][3] = {{0}};
   int dev = 0;
   cudaGetDevice(&dev);
-  const int pi = precision == CC_C128 ? 1 : 0;
-  const void* kern = precision == CC_C128 ? (const void*)batch_kernel<double>
-                                          : (const void*)batch_kernel<float>;
+  const int pi = arith;
+  const void* kern = batch_kernel_for(arith);
   if (dev >= 0 && dev < 64 && !attr_done[dev][pi]) {
     // the opt-in limit (227 KB per CTA) covers static and dynamic shared memory
     cudaFuncAttributes fa;
@@ -724,16 +811,19 @@ int batch_segments_occupancy(int precision, int block, size_t smem) {
 
 cc_status launch_batch_segments(void* seg_buf, const BJob* jobs, int n_jobs, int64_t n_items,
                                 int* done, unsigned long long* head,
-                                unsigned long long* stamps, int precision, int block,
+                                unsigned long long* stamps, int arith, int block,
                                 size_t smem, int grid, void* stream) {
   if (n_items <= 0) return CC_OK;
   int* err = device_error_flag();
   if (!err) return fail(CC_ENOMEM, "device error flag allocation failed");
-  batch_segments_occupancy(precision, block, smem);  // sets the shared-memory attribute once
+  batch_segments_occupancy(arith, block, smem);  // sets the shared-memory attribute once
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == CC_C128)
+  if (arith == GA_F64)
     batch_kernel<double><<<grid, block, smem, s>>>(static_cast<double2*>(seg_buf), jobs, n_jobs,
                                                    n_items, done, head, err, stamps);
+  else if (arith == GA_DFL)
+    batch_kernel<dfl><<<grid, block, smem, s>>>(static_cast<cdfl*>(seg_buf), jobs, n_jobs,
+                                                n_items, done, head, err, stamps);
   else
     batch_kernel<float><<<grid, block, smem, s>>>(static_cast<float2*>(seg_buf), jobs, n_jobs,
                                                   n_items, done, head, err, stamps);
@@ -743,11 +833,12 @@ cc_status launch_batch_segments(void* seg_buf, const BJob* jobs, int n_jobs, int
   return CC_OK;
 }
 
-cc_status run_program(const DeviceProgram& dp, int precision, void* state, void* stream) {
+cc_status run_program(const DeviceProgram& dp, int arith, void* state, void* stream) {
   for (int pi = 0; pi < (int)dp.passes.size(); ++pi) {
-    const cc_status st =
-        precision == CC_C128 ? launch_pass<double>(dp, pi, state, (cudaStream_t)stream)
-                             : launch_pass<float>(dp, pi, state, (cudaStream_t)stream);
+    const cudaStream_t s = (cudaStream_t)stream;
+    const cc_status st = arith == GA_F64   ? launch_pass<double>(dp, pi, state, s)
+                         : arith == GA_DFL ? launch_pass<dfl>(dp, pi, state, s)
+                                           : launch_pass<float>(dp, pi, state, s);
     if (st != CC_OK) return st;
   }
   return CC_OK;
