@@ -489,13 +489,34 @@ struct PassBuilder {
     op.type = (int8_t)type;
     op.t = (int8_t)t_reg;
     const bool attach = type == OP_DIAG || pending_touches(vp);
-    op.sign_adj = attach ? pend_adj : 0;
+    // A sign whose bits are all register bits of the stage is the same for
+    // every thread: when the op gets a phase block it joins the block's
+    // entries instead of flipping amplitudes.
+    uint64_t adj = attach ? pend_adj : 0;
+    std::vector<std::pair<int, int>> folded;  // register indices of folded signs
+    std::vector<DTerm> signs;
+    if (attach) {
+      const bool block = will_attach_block(type == OP_DIAG);
+      for (uint64_t r = adj; block && r; r &= r - 1) {
+        const int p = __builtin_ctzll(r);
+        if (p + 1 < 64 && reg_index[p] >= 0 && reg_index[p + 1] >= 0) {
+          folded.push_back({reg_index[p], reg_index[p + 1]});
+          adj &= ~(1ull << p);
+        }
+      }
+      for (const auto& d : pend_sign) {
+        if (block && reg_index[d.p0] >= 0 && reg_index[d.p1] >= 0)
+          folded.push_back({reg_index[d.p0], reg_index[d.p1]});
+        else
+          signs.push_back(d);
+      }
+    }
+    op.sign_adj = adj;
     const size_t t0 = hp.terms.size();
     op.term_begin = (int32_t)t0;
-    if (attach)
-      for (auto& d : pend_sign) hp.terms.push_back(d);
+    for (auto& d : signs) hp.terms.push_back(d);
     const size_t t1 = hp.terms.size();
-    if (attach) attach_phase_block(type == OP_DIAG);
+    if (attach) attach_phase_block(type == OP_DIAG, folded);
     const size_t t2 = hp.terms.size();
     if (attach)
       for (auto& d : pend_tab) hp.terms.push_back(d);
@@ -529,12 +550,22 @@ struct PassBuilder {
   // 32 register slots, T[j] = K prod_{i: bit i of j set} h_i, so each
   // amplitude takes one complex product; its p0 has bit 0 set unless
   // T[0] = 1 (a product the complex128 kernel skips).
-  void attach_phase_block(bool all) {
+  // Whether attach_phase_block(all) emits a block.
+  bool will_attach_block(bool all) const {
+    const bool fold = all || std::norm(pend_const) < 0x1p-48;
+    const uint64_t take = all ? ph_mask : (ph_mask & reg_mask);
+    return take || (fold && pend_const != cd(1.0));
+  }
+
+  // `signs`: pairs (i0, i1) of register indices whose sign (-1)^(j_i0 j_i1)
+  // (with i0 = i1: (-1)^(j_i0)) multiplies entry j; only passed when a block
+  // is emitted.
+  void attach_phase_block(bool all, const std::vector<std::pair<int, int>>& signs) {
     // the deferred scalar is folded in early once it is small, so the
     // amplitudes (which carry its inverse) stay far from FP32 overflow
     const bool fold = all || std::norm(pend_const) < 0x1p-48;
     const uint64_t take = all ? ph_mask : (ph_mask & reg_mask);
-    if (!take && !(fold && pend_const != cd(1.0))) return;
+    if (!will_attach_block(all)) return;
     ph_mask &= ~take;
     cd h[MAX_REG_BITS];
     for (auto& x : h) x = 1.0;
@@ -565,7 +596,9 @@ struct PassBuilder {
       cd f = K;
       for (int i = 0; i < MAX_REG_BITS; ++i)
         if ((j >> i) & 1) f *= h[i];
-      T[j] = f;
+      int neg = 0;
+      for (const auto& pr : signs) neg ^= (j >> pr.first) & (j >> pr.second) & 1;
+      T[j] = neg ? -f : f;
     }
     DTerm b{};
     b.kind = TERM_PBLOCK;

@@ -113,15 +113,19 @@ def test_program_image_arguments(host_lib):
 
 @pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c128", 4), ("c128", 13)])
 def test_phase_block_entries(host_lib, prec, tile_bits):
-    # a phase block's 32 entries are the products K prod_i h_i^(bit i of j)
-    # over the register bits, so T[j] T[0] = T[j & 1] T[j & ~1] and every
-    # entry is a unit complex number up to the common K; the complex128
-    # kernel skips slot 0 where the flag (bit 0) is clear, which needs
-    # T[0] = 1 exactly
+    # a phase block's 32 entries are K prod_i h_i^(bit i of j) over the
+    # register bits times the signs of the CZ-type factors between two
+    # register bits folded into it: (-1)^Q(j) with Q a quadratic form over
+    # GF(2) (Q(j) = sum over folded pairs of j_a j_b).  So with
+    # h_i = T[2^i] / T[0], T[j] / (T[0] prod h_i^(j_i)) is +-1 and its sign
+    # bit is the sum of the pair terms Q(2^a + 2^b) over the set bits of j;
+    # every entry is a unit complex number up to the common K.  The complex128
+    # kernel skips slot 0 where the flag (bit 0) is clear, which needs T[0] = 1
+    # exactly
     q = 10
     gates = w.random_circuit(q, 200, 9, kinds=ALL_KINDS)
     prog = interp(gates, q, prec, tile_bits)
-    blocks = 0
+    blocks = folded = 0
     for op in prog.ops:
         n_sign, n_phase = op[3], op[4]
         if not n_phase:
@@ -134,9 +138,29 @@ def test_phase_block_entries(host_lib, prec, tile_bits):
             assert blk[0] == 1
         k = abs(blk[0])
         assert np.allclose(np.abs(blk), k, rtol=1e-12)
+        h = [blk[1 << i] / blk[0] for i in range(5)]
+
+        def sign(j):
+            f = blk[0]
+            for i in range(5):
+                if (j >> i) & 1:
+                    f = f * h[i]
+            r = blk[j] / f
+            assert abs(abs(r.real) - 1) <= 1e-12 and abs(r.imag) <= 1e-12
+            return 1 if r.real < 0 else 0
+
+        pair = {(a, b): sign((1 << a) | (1 << b)) for a in range(5) for b in range(a + 1, 5)}
+        folded += any(pair.values())
         for j in range(32):
-            assert abs(blk[j] * blk[0] - blk[j & 1] * blk[j & ~1]) <= 1e-12 * k * k
+            bits = [i for i in range(5) if (j >> i) & 1]
+            want = 0
+            for x in range(len(bits)):
+                for y in range(x + 1, len(bits)):
+                    want ^= pair[(bits[x], bits[y])]
+            assert sign(j) == want
     assert blocks > 0
+    if max(P.rbits for P in prog.passes) >= 2:  # pairs of register bits exist
+        assert folded > 0
 
 
 def _mutations(prog):
