@@ -150,12 +150,16 @@ struct StageRegs {
 // precomputed products (the host folds the block's constant K into them) and
 // Phi the product of the ratios of the TERM_PFIX terms whose bit is set in
 // the thread's fixed index bits c (1 when there are none): one complex
-// product per amplitude however many phases the block holds (two with Phi).
-// The complex128 kernel skips slot 0 where T[0] = 1.
+// product per amplitude however many phases the block holds.  Phi is the same
+// for all of the thread's amplitudes, so it commutes with every op of the
+// stage: it multiplies into the thread's deferred factor F (hasF set), which
+// the stage applies once before its store.  The complex128 kernels skip slot
+// 0 where T[0] = 1.
 template <typename R, int RB>
 __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                             uint64_t c, const DTerm* __restrict__ terms,
-                                            const R* __restrict__ tabs) {
+                                            const R* __restrict__ tabs, typename CT<R>::C& F,
+                                            bool& hasF) {
   constexpr int N = 1 << RB;
   const DTerm blk = terms[op.term_sign_end()];
   const R* tb = tabs + 8 * blk.tab;
@@ -170,8 +174,8 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
         cmul(pr, pi, f[0], f[1]);
       }
     }
-#pragma unroll
-    for (int j = 0; j < N; ++j) cmul(a[j].x, a[j].y, pr, pi);
+    cmul(F.x, F.y, pr, pi);
+    hasF = true;
   }
   if constexpr (is_f32<R>()) {
     const float4* t4 = reinterpret_cast<const float4*>(tb);
@@ -216,7 +220,8 @@ template <typename R, int RB>
 __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                            uint64_t c, const StageRegs<RB>& sr,
                                            const DTerm* __restrict__ terms,
-                                           const R* __restrict__ tabs) {
+                                           const R* __restrict__ tabs, typename CT<R>::C& F,
+                                           bool& hasF) {
   constexpr int N = 1 << RB;
   constexpr uint32_t ALL = N >= 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
   uint32_t smask = 0;
@@ -268,7 +273,8 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
       }
     }
   }
-  if (op.term_phase_end() > op.term_sign_end()) apply_phase<R, RB>(a, op, c, terms, tabs);
+  if (op.term_phase_end() > op.term_sign_end())
+    apply_phase<R, RB>(a, op, c, terms, tabs, F, hasF);
   for (int t = op.term_phase_end(); t < op.term_end(); ++t) {
     const DTerm d = terms[t];
     const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
@@ -535,12 +541,17 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
       }
 
       // op o's matrix sits at mats + 8 o (the image stores one per op), so
-      // the descriptor and the matrix load independently
+      // the descriptor and the matrix load independently.  F: the deferred
+      // per-thread phase factor of the stage's TERM_PFIX terms.
+      C F;
+      F.x = R(1);
+      F.y = R(0);
+      bool hasF = false;
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const DOp op = ops[o];
         const Mat<R> m = load_mat<R>(mats + 8 * o);
         if (op.sign_adj != 0 || op.term_end() > op.term_begin)
-          apply_diag<R, RB>(a, op, cfix, sr, terms, tabs);
+          apply_diag<R, RB>(a, op, cfix, sr, terms, tabs, F, hasF);
 #define CC_OP_SWITCH(CALL)                                     \
   switch (op.t) {                                              \
     case 0: CALL(0); break;                                    \
@@ -565,6 +576,10 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
 #undef CC_OP_SWITCH
       }
 
+      if (hasF) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) cmul(a[j].x, a[j].y, F.x, F.y);
+      }
 #pragma unroll
       for (int j = 0; j < N; ++j) s[CC_SLOT_POS(j)] = a[j];
 #undef CC_SLOT_POS
