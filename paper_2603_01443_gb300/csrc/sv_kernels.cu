@@ -117,6 +117,30 @@ __device__ __forceinline__ TileMap<NVB> make_tile_map(const DPass& P, const DPas
   return m;
 }
 
+// The per-iteration parts g_b, p_b are the same for every thread of the
+// CTA: the kernels keep them in shared memory (written by thread 0 before a
+// barrier) and read them at each tile's load and store.  The volatile reads
+// keep the compiler from holding all of them in registers across the stage
+// loop, where the register-bound pass needs every register.
+__device__ __forceinline__ int64_t shared_map_g(const int64_t* s_tg, int b) {
+  return *(volatile const int64_t*)(s_tg + b);
+}
+__device__ __forceinline__ uint32_t shared_map_p(const uint32_t* s_tp, int b) {
+  return *(volatile const uint32_t*)(s_tp + b);
+}
+template <int NVB>
+__device__ __forceinline__ void publish_tile_map(const TileMap<NVB>& tm, int64_t* s_tg,
+                                                 uint32_t* s_tp) {
+  static_assert(NVB <= 4, "at most four per-iteration terms");
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int b = 0; b < NVB; ++b) {
+      s_tg[b] = tm.g_b[b];
+      s_tp[b] = tm.p_b[b];
+    }
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void cmul(R& xr, R& xi, R yr, R yi) {
   const R t = xr * yr - xi * yi;
@@ -436,7 +460,8 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
                                          const R* __restrict__ mats, const R* __restrict__ tabs,
                                          const int8_t* __restrict__ rest_bit, int64_t T,
                                          typename CT<R>::C* s, uint32_t n_active,
-                                         const TileMap<ilog2<(1 << RB) / CT<R>::PV>()>& tm) {
+                                         const TileMap<ilog2<(1 << RB) / CT<R>::PV>()>& tm,
+                                         const int64_t* s_tg, const uint32_t* s_tp) {
   using C = typename CT<R>::C;
   using V = typename CT<R>::V;
   constexpr int PV = CT<R>::PV;
@@ -462,7 +487,7 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
         int64_t g = g0;
 #pragma unroll
         for (int b = 0; b < NVB; ++b)
-          if ((it >> b) & 1) g ^= tm.g_b[b];
+          if ((it >> b) & 1) g ^= shared_map_g(s_tg, b);
         val[it] = CG ? __ldcg(reinterpret_cast<const V*>(vec + g)) : *reinterpret_cast<const V*>(vec + g);
       }
 #pragma unroll
@@ -470,7 +495,7 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
         uint32_t pl = tm.p_t;
 #pragma unroll
         for (int b = 0; b < NVB; ++b)
-          if ((it >> b) & 1) pl ^= tm.p_b[b];
+          if ((it >> b) & 1) pl ^= shared_map_p(s_tp, b);
         V v = val[it];
         if (PV == 2 && (pl & 1u)) v = swap_pair(v);  // the swizzle swapped the pair
         *reinterpret_cast<V*>(s + (pl & ~uint32_t(PV - 1))) = v;
@@ -595,8 +620,8 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
 #pragma unroll
       for (int b = 0; b < NVB; ++b)
         if ((it >> b) & 1) {
-          g ^= tm.g_b[b];
-          pl ^= tm.p_b[b];
+          g ^= shared_map_g(s_tg, b);
+          pl ^= shared_map_p(s_tp, b);
         }
       V v = *reinterpret_cast<const V*>(s + (pl & ~uint32_t(PV - 1)));
       if (PV == 2 && (pl & 1u)) v = swap_pair(v);
@@ -625,10 +650,14 @@ __global__ void __launch_bounds__(512)
   C* s = reinterpret_cast<C*>(smem_raw);
   const DPass P = *pass;
   constexpr int NVB = ilog2<(1 << RB) / CT<R>::PV>();
+  __shared__ int64_t s_tg[4];
+  __shared__ uint32_t s_tp[4];
   const TileMap<NVB> tm = make_tile_map<CT<R>::PV, NVB>(P, pass, blockDim.x);
+  publish_tile_map<NVB>(tm, s_tg, s_tp);
+  __syncthreads();
   for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x)
     run_tile<R, RB, false>(vec, P, stages, ops, terms, mats, tabs, pass->rest_bit, T, s,
-                           blockDim.x, tm);
+                           blockDim.x, tm, s_tg, s_tp);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -661,6 +690,8 @@ __global__ void __launch_bounds__(512)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ long long s_item;
+  __shared__ int64_t s_tg[4];
+  __shared__ uint32_t s_tp[4];
   __shared__ int s_job, s_ok;
   const uint32_t tid = threadIdx.x;
   for (;;) {
@@ -710,8 +741,10 @@ __global__ void __launch_bounds__(512)
   {                                                                                              \
     constexpr int NVB = ilog2<(1 << (RBV)) / CT<R>::PV>();                                       \
     const TileMap<NVB> tm = make_tile_map<CT<R>::PV, NVB>(P, J.pass, na);                       \
+    publish_tile_map<NVB>(tm, s_tg, s_tp);                                                       \
+    __syncthreads();                                                                             \
     run_tile<R, (RBV), true>(vec, P, J.stages, J.ops, J.terms, mats, tabs, J.pass->rest_bit, T, \
-                             s, na, tm);                                                         \
+                             s, na, tm, s_tg, s_tp);                                             \
   }
         case 1: CC_BATCH_TILE(1) break;
         case 2: CC_BATCH_TILE(2) break;
@@ -741,7 +774,13 @@ cc_status launch_rb(const DeviceProgram& dp, int pi, void* state, cudaStream_t s
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // the opt-in limit (227 KB per CTA) covers static and dynamic shared memory
+    cudaFuncAttributes fa;
+    size_t static_smem = 0;
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess) static_smem = fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(227 * 1024 - static_smem));
+    cudaGetLastError();
     attr_done[dev] = 1;
   }
   int occ = 1;
