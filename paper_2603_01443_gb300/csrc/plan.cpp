@@ -21,7 +21,9 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <new>
+#include <thread>
 
 #include "internal.h"
 #include "plan.h"
@@ -238,14 +240,38 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     p->seg_buf_bytes = (uint64_t)off * ab;
     p->psi_bytes = (uint64_t(1) << q) * ab;
 
-    // One shared program per segment.
-    for (int i = 0; i < n_seg; ++i) {
-      HostProgram hp = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
-                                       seg_kmax, low_tile_bits(precision),
-                                       reg_bits_max(precision));
-      if (hp.nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
-      p->hprog.push_back(std::move(hp));
+    // One shared program per segment.  The programs are independent host
+    // work, so segments after the first compile on their own threads (where
+    // a thread cannot be started, its segment compiles on this one).
+    p->hprog.resize(n_seg);
+    {
+      std::vector<std::exception_ptr> errs(n_seg);
+      auto work = [&](int i) {
+        try {
+          p->hprog[i] = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
+                                        seg_kmax, low_tile_bits(precision),
+                                        reg_bits_max(precision));
+        } catch (...) {
+          errs[i] = std::current_exception();
+        }
+      };
+      std::vector<std::thread> pool;
+      std::vector<int> inline_segs;
+      for (int i = 1; i < n_seg; ++i) {
+        try {
+          pool.emplace_back(work, i);
+        } catch (...) {
+          inline_segs.push_back(i);
+        }
+      }
+      work(0);
+      for (int i : inline_segs) work(i);
+      for (auto& t : pool) t.join();
+      for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
     }
+    for (int i = 0; i < n_seg; ++i)
+      if (p->hprog[i].nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
 
     // Merge stages: stage s absorbs segment s into the product of segments < s.
     //   U_s[z][x_s * N_{<s} + x_{<s}] = sum_k U_{s-1}[k][x_{<s}] * seg_s[r_s(k, z)][x_s]
