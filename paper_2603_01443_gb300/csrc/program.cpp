@@ -319,6 +319,9 @@ int scan(const std::vector<ItemBits>& bits, const std::vector<int>& order,
   uint64_t blocked = 0;
   int dense = 0;
   for (int i : order) {
+    // counting only: once every allowed qubit is blocked no dense item can
+    // be taken any more
+    if (!take && !(dense_ok & ~blocked)) break;
     if (applied[i]) continue;
     const ItemBits b = bits[i];
     if ((b.mask & blocked) || (b.dense & ~dense_ok)) {
@@ -591,14 +594,19 @@ struct PassBuilder {
       K = pend_const;
       pend_const = 1.0;
     }
+    // T[j] = K prod_{i in j} h_i, multiplied in ascending i: entry j is
+    // entry (j without its highest bit) times h of that bit
     cd T[32];
+    cd P[32];
+    P[0] = K;
+    for (int j = 1; j < 32; ++j) {
+      const int top = 31 - __builtin_clz((unsigned)j);
+      P[j] = P[j ^ (1 << top)] * h[top];
+    }
     for (int j = 0; j < 32; ++j) {
-      cd f = K;
-      for (int i = 0; i < MAX_REG_BITS; ++i)
-        if ((j >> i) & 1) f *= h[i];
       int neg = 0;
       for (const auto& pr : signs) neg ^= (j >> pr.first) & (j >> pr.second) & 1;
-      T[j] = neg ? -f : f;
+      T[j] = neg ? -P[j] : P[j];
     }
     DTerm b{};
     b.kind = TERM_PBLOCK;
