@@ -132,6 +132,8 @@ def program_ops(words):
             c["dense"] += 1
         elif typ in (2, 3):
             c["rot"] += 1
+        elif typ == 4:  # packed rotations: one per register bit of the mask
+            c["rot"] += bin(wd[i - 7] & 0xFF).count("1")
         c["cmul"] += (1 if n_phase else 0) + n_table
     return c
 

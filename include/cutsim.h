@@ -234,10 +234,12 @@ cc_status cc_uncut_create(const cc_gate* gates, int32_t n_gates, int32_t q, int3
  *   mats, tabs; per pass nq, k, low, init_zero, stage_begin, stage_end,
  *   rbits, n_rest, zero_tile, zero_rest, 16 tile bits, 48 rest bits; per
  *   stage op_begin, op_end, 8 register tile bits; per op type, t,
- *   term_begin, n_sign, n_phase, n_table, mat, sign_adj; per term kind, p0,
- *   p1, tab.  reals (double, HOST): the 2x2 matrices (4 complex each, the
- *   rotations' t in the first) then the tables (4 complex each), re/im
- *   interleaved.  The meaning of each field is that of the device program
+ *   term_begin, n_sign, n_phase, n_table, mat, sign_adj (type 4, a packed
+ *   rotation op: t = mask of register bits | mask of those in cotangent form
+ *   << 8); per term kind, p0, p1, tab.  reals (double, HOST): the 2x2
+ *   matrices (4 complex each; a rotation's t in the first real, a packed
+ *   op's tangent of register bit i in real i) then the tables (4 complex
+ *   each), re/im interleaved.  The meaning of each field is that of the device program
  *   the gate-pass kernels execute.
  * With words or reals NULL it only stores the sizes in *n_words, *n_reals;
  * CC_EBUFSIZE when the given capacities are too small. */

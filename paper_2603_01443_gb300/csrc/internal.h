@@ -60,14 +60,18 @@ struct DTerm {
 // their scalar factor c (or s) carried by a later phase block:
 //   OP_ROT : (a, b) <- (a - t b, b + t a),  t = s / c  (|t| <= 1)
 //   OP_ROTC: (a, b) <- (t a - b, a + t b),  t = c / s  (|t| <= 1)
-enum : int32_t { OP_DENSE = 0, OP_DIAG = 1, OP_ROT = 2, OP_ROTC = 3 };
+// OP_ROTS applies one such rotation on each register bit i set in its mask t
+// (OP_ROTC form where bit i of cot is set) with tangent mats[8*mat + i]; the
+// rotations act on distinct bits, so their order does not matter.
+enum : int32_t { OP_DENSE = 0, OP_DIAG = 1, OP_ROT = 2, OP_ROTC = 3, OP_ROTS = 4 };
 
 // Before its matrix, an op multiplies each amplitude by (-1)^s with
 //   s = popcount(v & (v >> 1) & sign_adj) + sum of the sign terms (bit pairs
 //       not adjacent in v)   (mod 2)
 // then by its phase block (if any) and every table term.  OP_DENSE then
 // applies the 2x2 matrix mats[8*mat ...] (row-major, interleaved re/im) to
-// register bit t, OP_ROT / OP_ROTC their rotation with t = mats[8*mat];
+// register bit t, OP_ROT / OP_ROTC their rotation with t = mats[8*mat],
+// OP_ROTS its rotations on the register bits of the mask t;
 // OP_DIAG stops after the diagonal factors.
 struct alignas(16) DOp {
   int8_t type, t;
@@ -77,7 +81,8 @@ struct alignas(16) DOp {
   int32_t term_begin;
   int32_t mat;
   uint64_t sign_adj;  // bit p set: a sign term on (p, p+1)
-  uint64_t pad;
+  uint8_t cot;        // OP_ROTS: register bits whose rotation is in OP_ROTC form
+  uint8_t pad[7];
   CC_HD int term_sign_end() const { return term_begin + n_sign; }
   CC_HD int term_phase_end() const { return term_sign_end() + n_phase; }
   CC_HD int term_end() const { return term_phase_end() + n_table; }

@@ -525,7 +525,9 @@ void serialize_program(const cc::HostProgram& hp, std::vector<int64_t>& w, std::
     for (int i = 0; i < 8; ++i) w.push_back(S.rb[i]);
   }
   for (const DOp& o : hp.ops) {
-    const int64_t f[8] = {o.type, o.t, o.term_begin, o.n_sign, o.n_phase, o.n_table, o.mat,
+    // OP_ROTS: the t word carries the OP_ROTC mask in bits 8..15
+    const int64_t t = o.t | (o.type == OP_ROTS ? (int64_t)o.cot << 8 : 0);
+    const int64_t f[8] = {o.type, t, o.term_begin, o.n_sign, o.n_phase, o.n_table, o.mat,
                           (int64_t)o.sign_adj};
     w.insert(w.end(), f, f + 8);
   }

@@ -487,11 +487,16 @@ struct PassBuilder {
   // matrix on a bit they do not depend on, so they stay pending until an op
   // whose bit one of them depends on (or the pass's final OP_DIAG); then all
   // of them ride on that op at once, and a layer of CZs costs one sign sweep.
-  void emit(int type, int t_reg, const cd* u, int vp) {
+  void emit(int type, int t_reg, const cd* u, int vp, uint8_t cot = 0,
+            uint64_t more_vps = 0) {
     DOp op{};
     op.type = (int8_t)type;
     op.t = (int8_t)t_reg;
-    const bool attach = type == OP_DIAG || pending_touches(vp);
+    op.cot = cot;
+    bool touches = type == OP_DIAG || pending_touches(vp);
+    for (uint64_t r = more_vps; r && !touches; r &= r - 1)
+      touches = pending_touches(__builtin_ctzll(r));
+    const bool attach = touches;
     // A sign whose bits are all register bits of the stage is the same for
     // every thread: when the op gets a phase block it joins the block's
     // entries instead of flipping amplitudes.
@@ -661,9 +666,24 @@ struct PassBuilder {
       es[n++] = e;
     }
     for (int i = 0; i < n; ++i) add_diag1(js[i], es[i].dr0, es[i].dr1);
-    for (int i = 0; i < n; ++i) {
-      const cd m[4] = {es[i].t, 0.0, 0.0, 0.0};
-      emit(es[i].rot, reg_of[js[i]], m, vpos[js[i]]);
+    if (n == 1) {
+      const cd m[4] = {es[0].t, 0.0, 0.0, 0.0};
+      emit(es[0].rot, reg_of[js[0]], m, vpos[js[0]]);
+    } else if (n > 1) {
+      // every rotation of the flush in one op: tangent of register bit i in
+      // real slot i of the op's matrix
+      double tr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      uint8_t bits = 0, cot = 0;
+      uint64_t vps = 0;
+      for (int i = 0; i < n; ++i) {
+        const int r = reg_of[js[i]];
+        bits |= (uint8_t)(1u << r);
+        if (es[i].rot == OP_ROTC) cot |= (uint8_t)(1u << r);
+        tr[r] = es[i].t;
+        vps |= 1ull << vpos[js[i]];
+      }
+      const cd m[4] = {cd(tr[0], tr[1]), cd(tr[2], tr[3]), cd(tr[4], tr[5]), cd(tr[6], tr[7])};
+      emit(OP_ROTS, bits, m, vpos[js[0]], cot, vps);
     }
     for (int i = 0; i < n; ++i) {
       add_diag1(js[i], es[i].dl0, es[i].dl1);

@@ -436,10 +436,21 @@ __device__ __forceinline__ void rot_mat(typename CT<R>::C (&a)[1 << RB], R t) {
   }
 }
 
-// Load, transform and store tile T of one pass.  n_active threads (a power
-// of two, 2^(k - rbits)) take part in the register stages; every thread of
-// the block shares the loads and stores.  CG loads through L2 only, for
-// vectors that other CTAs of the same launch wrote.
+// The rotations of an OP_ROTS op: register bit RHO.. in turn, each in its
+// tangent (or cotangent) form with its own tangent.
+template <typename R, int RB, int RHO>
+__device__ __forceinline__ void rot_run(typename CT<R>::C (&a)[1 << RB], uint32_t bits,
+                                        uint32_t cot, const Mat<R>& m) {
+  if constexpr (RHO < RB) {
+    if ((bits >> RHO) & 1u) {
+      if ((cot >> RHO) & 1u)
+        rot_mat<R, RB, RHO, true>(a, m.v[RHO]);
+      else
+        rot_mat<R, RB, RHO, false>(a, m.v[RHO]);
+    }
+    rot_run<R, RB, RHO + 1>(a, bits, cot, m);
+  }
+}
 
 template <typename V>
 __device__ __forceinline__ V swap_pair(V v) {  // (a, b) -> (b, a) for a float4 of two complex64
@@ -594,6 +605,8 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
           CC_OP_SWITCH(CC_ROT)
         } else if (op.type == OP_ROTC) {
           CC_OP_SWITCH(CC_ROTC)
+        } else if (op.type == OP_ROTS) {
+          rot_run<R, RB, 0>(a, (uint32_t)op.t, op.cot, m);
         }
 #undef CC_DENSE
 #undef CC_ROT

@@ -9,7 +9,8 @@ amplitude by its diagonal factors (adjacent-bit signs, sign terms, the phase
 block's factor of the amplitude's register slot and its TERM_PFIX factors,
 table terms)
 and then applies its 2x2 matrix or rotation to the pairs differing in one
-register bit.  It shares nothing with the CUDA path beyond that image, so a
+register bit (a packed rotation op: one rotation on each register bit of its
+mask).  It shares nothing with the CUDA path beyond that image, so a
 match with the oracle pins the host compiler (pass and stage planning,
 deferred diagonals, the Euler split and phase blocks) without a GPU.
 """
@@ -21,7 +22,7 @@ from typing import List
 
 import numpy as np
 
-OP_DENSE, OP_DIAG, OP_ROT, OP_ROTC = 0, 1, 2, 3
+OP_DENSE, OP_DIAG, OP_ROT, OP_ROTC, OP_ROTS = 0, 1, 2, 3, 4
 TERM_SIGN, TERM_TABLE, TERM_PBLOCK, TERM_PFIX = 0, 1, 2, 3
 
 
@@ -131,6 +132,27 @@ def run(prog: Program) -> np.ndarray:
                     f *= prog.tabs[4 * tab + _bit(v, p0) + 2 * _bit(v, p1)]
                 psi *= f
                 if typ == OP_DIAG:
+                    continue
+                if typ == OP_ROTS:
+                    # rotations on the register bits of t's low byte (distinct
+                    # bits: any order), the OP_ROTC form where bit i of t >> 8
+                    # is set, tangent of register bit i in real slot i
+                    reals_of = np.stack([prog.mats[4 * mat:4 * mat + 4].real,
+                                         prog.mats[4 * mat:4 * mat + 4].imag], axis=1).ravel()
+                    for i in range(P.rbits):
+                        if not (t >> i) & 1:
+                            continue
+                        vb = P.tile_bit[rb[i]]
+                        i0 = x[_bit(x, vb) == 0]
+                        i1 = i0 | (1 << vb)
+                        a0, a1 = psi[i0].copy(), psi[i1].copy()
+                        tt = reals_of[i]
+                        if (t >> (8 + i)) & 1:
+                            psi[i0] = tt * a0 - a1
+                            psi[i1] = a0 + tt * a1
+                        else:
+                            psi[i0] = a0 - tt * a1
+                            psi[i1] = a1 + tt * a0
                     continue
                 vb = P.tile_bit[rb[t]]
                 i0 = x[_bit(x, vb) == 0]

@@ -13,7 +13,8 @@ import pytest
 import workload as w
 from oracle import statevector as sv
 from paper_2603_01443_gb300 import api, capi
-from program_interp import OP_DENSE, OP_ROT, OP_ROTC, TERM_PBLOCK, TERM_SIGN, parse, run
+from program_interp import (OP_DENSE, OP_ROT, OP_ROTC, OP_ROTS, TERM_PBLOCK, TERM_SIGN, parse,
+                            run)
 
 ALL_KINDS = ["U3", "H", "X", "Z", "S", "SDG", "T", "TDG", "CZ", "CX", "SWAP", "ISWAP", "CAN"]
 
@@ -63,14 +64,18 @@ def test_fewer_register_bits(host_lib, monkeypatch, rot, prec, reg_bits, tile_bi
 @pytest.mark.parametrize("rot", ["1", "0"])
 def test_brickwork_program_and_rotation_ops(host_lib, monkeypatch, rot):
     # a brickwork's fused one-qubit matrices become tangent-form rotations
-    # (OP_ROT / OP_ROTC) with the engine on and complex 2x2 ops with it off
+    # (OP_ROT / OP_ROTC, and OP_ROTS for the rotations a stage flushes
+    # together) with the engine on and complex 2x2 ops with it off
     monkeypatch.setenv("CUTSIM_ROT", rot)
     q = 11
     gates = w.brickwork(q, 12, 5)
     prog = interp(gates, q, "c64", 6)
     types = {op[0] for op in prog.ops}
     if rot == "1":
-        assert types <= {1, 2, 3} and types & {2, 3}
+        assert types <= {1, 2, 3, 4} and types & {2, 3}
+        wide = interp(gates, q, "c64", 11)  # five register bits per stage
+        assert OP_ROTS in {op[0] for op in wide.ops}
+        assert rel(run(wide), sv.simulate(q, gates)) <= 1e-12
         assert any(op[4] for op in prog.ops)  # phase blocks
     else:
         assert types <= {0, 1}
@@ -204,6 +209,22 @@ def _mutations(prog):
         m = copy.deepcopy(prog)
         m.tabs[4 * blk[-1][3]] *= np.exp(0.3j)  # the entry of the slot with no register bit set
         out["phase block entry"] = m
+    packed = ops_of(lambda op: op[0] == OP_ROTS)
+    if packed:
+        # the lowest register bit of the last packed op: its tangent (real
+        # slot i of the op's matrix) negated, and its form flipped
+        o = packed[-1]
+        i = ((prog.ops[o][1] & 0xFF) & -(prog.ops[o][1] & 0xFF)).bit_length() - 1
+        m = copy.deepcopy(prog)
+        k = 4 * m.ops[o][6] + i // 2
+        z = m.mats[k]
+        m.mats[k] = complex(-z.real, z.imag) if i % 2 == 0 else complex(z.real, -z.imag)
+        out["packed rotation tangent"] = m
+        m = copy.deepcopy(prog)
+        op = list(m.ops[o])
+        op[1] ^= 1 << (8 + i)
+        m.ops[o] = tuple(op)
+        out["packed rotation form"] = m
     multi = [i for i, P in enumerate(prog.passes) if P.k >= 6]
     if multi:
         m = copy.deepcopy(prog)
@@ -230,6 +251,20 @@ def test_interpreter_rejects_mutated_programs(host_lib, monkeypatch, rot):
     assert expect <= set(muts), sorted(muts)
     for name, m in muts.items():
         assert rel(run(m), ref) > 1e-3, name
+
+
+def test_interpreter_rejects_mutated_packed_rotations(host_lib):
+    # stages of five register bits flush several rotations as one packed op
+    # (OP_ROTS): a changed tangent or rotation form in it must miss the oracle
+    q = 10
+    gates = w.brickwork(q, 8, 3)
+    ref = sv.simulate(q, gates)
+    prog = interp(gates, q, "c64", 10)
+    assert rel(run(prog), ref) <= 1e-12
+    muts = _mutations(prog)
+    assert {"packed rotation tangent", "packed rotation form"} <= set(muts), sorted(muts)
+    for name in ("packed rotation tangent", "packed rotation form"):
+        assert rel(run(muts[name]), ref) > 1e-3, name
 
 
 @pytest.mark.parametrize("prec,tile_bits", [("c64", 5), ("c128", 4), ("c64", 14)])
@@ -273,6 +308,10 @@ def validate(prog):
                 assert sign_adj >> max(prog.nq - 1, 0) == 0
                 if typ == OP_DIAG:
                     assert mat == -1
+                elif typ == OP_ROTS:  # register-bit mask, OP_ROTC mask within it
+                    bits, cot = t & 0xFF, t >> 8
+                    assert 0 < bits < (1 << P.rbits) and cot & ~bits == 0
+                    assert bin(bits).count("1") >= 2 and 0 <= mat < n_mat
                 else:
                     assert 0 <= t < P.rbits and 0 <= mat < n_mat
                 sec = ([TERM_SIGN] * n_sign + ([TERM_PBLOCK] if n_phase else [])
