@@ -82,7 +82,9 @@ struct alignas(16) DOp {
   int32_t mat;
   uint64_t sign_adj;  // bit p set: a sign term on (p, p+1)
   uint8_t cot;        // OP_ROTS: register bits whose rotation is in OP_ROTC form
-  uint8_t pad[7];
+  uint8_t blk_p0;     // copies of the phase block's p0 and tab (when n_phase > 0),
+  uint16_t pad;       // so the kernels read the block's table without first
+  int32_t blk_tab;    // loading its term
   CC_HD int term_sign_end() const { return term_begin + n_sign; }
   CC_HD int term_phase_end() const { return term_sign_end() + n_phase; }
   CC_HD int term_end() const { return term_phase_end() + n_table; }

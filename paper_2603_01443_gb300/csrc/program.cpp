@@ -526,6 +526,10 @@ struct PassBuilder {
     const size_t t1 = hp.terms.size();
     if (attach) attach_phase_block(type == OP_DIAG, folded);
     const size_t t2 = hp.terms.size();
+    if (t2 > t1) {
+      op.blk_p0 = hp.terms[t1].p0;
+      op.blk_tab = hp.terms[t1].tab;
+    }
     if (attach)
       for (auto& d : pend_tab) hp.terms.push_back(d);
     const size_t t3 = hp.terms.size();

@@ -185,9 +185,8 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
                                             const R* __restrict__ tabs, typename CT<R>::C& F,
                                             bool& hasF) {
   constexpr int N = 1 << RB;
-  const DTerm blk = terms[op.term_sign_end()];
-  const R* tb = tabs + 8 * blk.tab;
-  const bool skip0 = !is_f32<R>() && !(blk.p0 & 1u);
+  const R* tb = tabs + 8 * op.blk_tab;  // the block term's tab, copied into the op
+  const bool skip0 = !is_f32<R>() && !(op.blk_p0 & 1u);
   R pr = R(1), pi = R(0);
   const bool fixed = op.term_phase_end() > op.term_sign_end() + 1;
   if (fixed) {
