@@ -393,6 +393,17 @@ __device__ __forceinline__ void dense_mat(typename CT<R>::C (&a)[1 << RB], const
   }
 }
 
+// x + (-0), exact for every x (signed zeros, infinities and NaNs included).
+// Both outputs of a rotation need both inputs, so one of them is computed
+// into a fresh register and copied back into its slot's register; written
+// as this add, the copy issues on the FMA pipe instead of the ALU pipe, which
+// the pass's integer and logic work keeps the busier of the two.
+__device__ __forceinline__ float fma_pipe_copy(float x) {
+  float r;
+  asm("add.rn.f32 %0, %1, 0f80000000;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Real rotation in tangent form on register bit RHO of every held pair:
 // (a, b) <- (a - t b, b + t a), or with COT (a, b) <- (t a - b, a + t b);
 // two multiply-adds per amplitude.
@@ -429,6 +440,10 @@ __device__ __forceinline__ void rot_mat(typename CT<R>::C (&a)[1 << RB], R t) {
       b0.y = a0.y - t * a1.y;
       b1.x = a1.x + t * a0.x;
       b1.y = a1.y + t * a0.y;
+    }
+    if constexpr (is_f32<R>()) {
+      b0.x = fma_pipe_copy(b0.x);
+      b0.y = fma_pipe_copy(b0.y);
     }
     a[j0] = b0;
     a[j1] = b1;
