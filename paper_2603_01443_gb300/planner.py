@@ -227,8 +227,12 @@ class StagePlanner:
         the ensemble spread) exceeds the fallback level, the closed-form model
         decides instead: among the options whose c_total stays below Eqs.
         13-14 lowered by Eq. 15 for the circuit's D_seg / D, the one with the
-        least subcircuit work N_sub 2^{q/n} / n (Table I), else uncut; the
-        merge form is then left to the library (AUTO)."""
+        fewest cuts (then the fewest segments), else uncut; the merge form is
+        then left to the library (AUTO).  Both the merge term k^{c_max} 2^q
+        and the subcircuit count N_sub of Table I grow with the cuts, and
+        measured chains of more segments with the same cuts per boundary
+        merge far slower, so the fewest cuts is the safe pick when the model
+        cannot be trusted."""
         opts = [o for o in options if FORM_TOL.get(o.get("form", "fma"), 0.0) <= tol]
         X = np.array([o["features"] for o in opts])
         pr = self.predict(X)
@@ -246,7 +250,7 @@ class StagePlanner:
         if fallback:
             ok = [o for o in opts if o["cut_bits"] < nonuniform_threshold(q, o["n"], ratio)]
             if ok:
-                best = min(ok, key=lambda o: o["n_sub"] * 2.0 ** (q / o["n"]) / o["n"])
+                best = min(ok, key=lambda o: (o["cut_bits"], o["n"]))
                 out.update(choice=best["n"], form="auto", seg_tile_bits=None)
             else:
                 out.update(choice=0, form=None, seg_tile_bits=None)

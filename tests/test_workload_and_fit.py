@@ -183,3 +183,10 @@ def test_planner_decide_filters_forms_and_falls_back():
     assert d["fallback"] and d["choice"] == 2 and d["form"] == "auto"  # 4 < 20/2 - 1
     d = P.decide(9, opts, tol=2e-6, dseg_over_d=1.0)
     assert d["fallback"] and d["choice"] == 0  # 4 >= 9/2 - 1
+    # among admissible chains the fallback takes the fewest cuts: four
+    # segments with 4 cuts per boundary (12, below Eq. 14 at q = 30) lose to
+    # two segments with 4
+    chain = [{"n": n, "form": "fma", "seg_tile_bits": 13, "features": [0.0],
+              "cut_bits": 4 * (n - 1), "n_sub": 2 * 16 + (n - 2) * 256} for n in (4, 3, 2)]
+    d = P.decide(30, chain, tol=2e-6, dseg_over_d=0.5)
+    assert d["fallback"] and d["choice"] == 2
