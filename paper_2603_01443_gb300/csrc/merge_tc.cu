@@ -610,56 +610,99 @@ __device__ __forceinline__ void split_store(uint32_t* hi, uint32_t* lo, float v)
 // is relative to max |psi|).  A first kernel finds the two largest magnitudes
 // (atomic maxima of the non-negative float bits), the split kernel then
 // writes v 2^-e = hi + lo in fp16, and the epilogue multiplies by 2^(e_R + e_C).
-__device__ __forceinline__ float f16_operand(const float2* __restrict__ A, const float2* __restrict__ B,
-                                             int64_t NA, int64_t NB, int K,
-                                             const int32_t* __restrict__ aidx,
-                                             const int32_t* __restrict__ bidx, int64_t row, int kk) {
-  if (kk >= 2 * K) return 0.f;
-  if (row < NB) {
-    const float2 b = B[(int64_t)bidx[kk % K] * NB + row];
-    return kk < K ? b.x : b.y;
-  }
-  const int64_t n = row - NB;
-  const float2 a = A[(int64_t)aidx[kk % K] * NA + (n >> 1)];
-  if ((n & 1) == 0) return kk < K ? a.x : -a.y;
-  return kk < K ? a.y : a.x;
-}
 
+// The largest magnitude of each operand: blockIdx.y = 0 takes the row
+// operand's values (the slices B[bidx[k]], k < K), 1 the column operand's (the
+// slices A[aidx[k]]; Cop holds the same magnitudes), read in grid-stride
+// order so every warp load is contiguous; one atomic maximum per block.
 __global__ void __launch_bounds__(256)
     operand_absmax_f16(const float2* __restrict__ A, const float2* __restrict__ B, int qa, int qb,
                        int K, const int32_t* __restrict__ aidx, const int32_t* __restrict__ bidx,
                        unsigned int* __restrict__ maxbits) {
-  const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= NB + 2 * NA) return;
+  __shared__ float s_mx[8];
+  const bool is_r = blockIdx.y == 0;
+  const int qn = is_r ? qb : qa;
+  const float2* __restrict__ X = is_r ? B : A;
+  const int32_t* __restrict__ idx = is_r ? bidx : aidx;
+  const int64_t mask = (int64_t(1) << qn) - 1;
+  const int64_t total = (int64_t)K << qn;
   float mx = 0.f;
-  for (int kk = lane; kk < 2 * K; kk += 32) mx = fmaxf(mx, fabsf(f16_operand(A, B, NA, NB, K, aidx, bidx, row, kk)));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = X[((int64_t)idx[i >> qn] << qn) + (i & mask)];
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0 && mx > 0.f) atomicMax(maxbits + (row < NB ? 0 : 1), __float_as_uint(mx));
+  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, s_mx[w]);
+    if (mx > 0.f) atomicMax(maxbits + (is_r ? 0 : 1), __float_as_uint(mx));
+  }
 }
 
+// The fp16 split, through a 64 x 64 shared-memory transpose: a block takes
+// 64 operand rows (64 rows y of R, or 32 amplitudes x of A giving rows 2x and
+// 2x+1 of Cop) and walks the padded K range in chunks of 64; each warp loads
+// whole 32-amplitude runs of one slice (contiguous 256-byte reads), and the
+// rows go out as contiguous 128-byte runs of hi and of lo.
+constexpr int kSplitRows = 64;
 __global__ void __launch_bounds__(256)
     split_operands_f16(const float2* __restrict__ A, const float2* __restrict__ B, int qa, int qb,
                        int K, int KR, const int32_t* __restrict__ aidx,
                        const int32_t* __restrict__ bidx, __half* __restrict__ r_ops,
                        __half* __restrict__ c_ops, const unsigned int* __restrict__ maxbits) {
+  __shared__ float T[kSplitRows][kSplitRows + 1];
   const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= NB + 2 * NA) return;
-  const bool is_r = row < NB;
+  const int64_t r_blocks = NB / kSplitRows;
+  const bool is_r = (int64_t)blockIdx.x < r_blocks;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = f16_scale_exp(maxbits[is_r ? 0 : 1]);
   const float down = __uint_as_float((uint32_t)(127 - e) << 23);  // 2^-e
-  const int64_t n = row - NB;
-  __half* hi = is_r ? r_ops + row * KR : c_ops + n * KR;
-  __half* lo = is_r ? r_ops + (NB + row) * KR : c_ops + (2 * NA + n) * KR;
-  for (int kk = lane; kk < KR; kk += 32) {
-    const float v = f16_operand(A, B, NA, NB, K, aidx, bidx, row, kk) * down;
-    const __half h = __float2half_rn(v);
-    hi[kk] = h;
-    lo[kk] = __float2half_rn(v - __half2float(h));
+  // first operand row of the block, and the first amplitude it reads
+  const int64_t row0 = is_r ? (int64_t)blockIdx.x * kSplitRows
+                            : ((int64_t)blockIdx.x - r_blocks) * kSplitRows;
+  const int64_t amp0 = is_r ? row0 : row0 / 2;
+  __half* const hi = is_r ? r_ops : c_ops;
+  __half* const lo = is_r ? r_ops + NB * KR : c_ops + 2 * NA * KR;
+  for (int c0 = 0; c0 < KR; c0 += kSplitRows) {
+    for (int kl = warp; kl < kSplitRows; kl += 8) {
+      const int kk = c0 + kl;
+      const bool re = kk < K, used = kk < 2 * K;
+      const int k = re ? kk : kk - K;
+      if (is_r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v = 0.f;
+          if (used) {
+            const float2 b = B[((int64_t)bidx[k] << qb) + amp0 + h * 32 + lane];
+            v = re ? b.x : b.y;
+          }
+          T[h * 32 + lane][kl] = v * down;
+        }
+      } else {
+        float v0 = 0.f, v1 = 0.f;
+        if (used) {
+          const float2 a = A[((int64_t)aidx[k] << qa) + amp0 + lane];
+          v0 = re ? a.x : -a.y;  // row 2x
+          v1 = re ? a.y : a.x;   // row 2x + 1
+        }
+        T[2 * lane][kl] = v0 * down;
+        T[2 * lane + 1][kl] = v1 * down;
+      }
+    }
+    __syncthreads();
+    for (int r = warp; r < kSplitRows; r += 8) {
+      const float v0 = T[r][2 * lane], v1 = T[r][2 * lane + 1];
+      const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+      const __half l0 = __float2half_rn(v0 - __half2float(h0));
+      const __half l1 = __float2half_rn(v1 - __half2float(h1));
+      const int64_t off = (row0 + r) * KR + c0 + 2 * lane;
+      *reinterpret_cast<__half2*>(hi + off) = __halves2half2(h0, h1);
+      *reinterpret_cast<__half2*>(lo + off) = __halves2half2(l0, l1);
+    }
+    __syncthreads();
   }
 }
 
@@ -813,9 +856,13 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
         (reinterpret_cast<uintptr_t>(ws) + (uint64_t)2 * rows * KR * eb + 1023) & ~uintptr_t(1023));
     const cudaError_t me = cudaMemsetAsync(f16_maxbits, 0, 2 * sizeof(unsigned int), s);
     if (me != cudaSuccess) return fail(CC_ECUDA, std::string("memset: ") + cudaGetErrorString(me));
-    operand_absmax_f16<<<blocks, 256, 0, s>>>((const float2*)st.A, (const float2*)st.B, st.qa,
-                                              st.qb, (int)st.K, st.aidx, st.bidx, f16_maxbits);
-    split_operands_f16<<<blocks, 256, 0, s>>>(
+    const int64_t longest = st.K << std::max(st.qa, st.qb);
+    const dim3 mgrid((unsigned)std::min<int64_t>((longest + 255) / 256, (int64_t)num_sms() * 8), 2);
+    operand_absmax_f16<<<mgrid, 256, 0, s>>>((const float2*)st.A, (const float2*)st.B, st.qa,
+                                             st.qb, (int)st.K, st.aidx, st.bidx, f16_maxbits);
+    // rows: NB of R and 2 NA of Cop, 64 per block (NB, NA >= 2^7)
+    const unsigned sblocks = (unsigned)(NB / kSplitRows + 2 * NA / kSplitRows);
+    split_operands_f16<<<sblocks, 256, 0, s>>>(
         (const float2*)st.A, (const float2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
         (__half*)r_ops, (__half*)c_ops, f16_maxbits);
   } else if (form == CC_MERGE_BF16X3)
