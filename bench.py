@@ -597,9 +597,24 @@ def fit_boundary(points, iters=4000, lr=0.05):
     and slowdown points of a (q, c_total) grid: a class-balanced linear
     soft-margin SVM (hinge loss, L2 penalty) fitted by subgradient descent on
     standardised features, as the paper fits its measured boundary with a
-    weighted SVM.  Returns None when one class is empty."""
+    weighted SVM.  Only the q that have points of both classes take part: a
+    q where no c_total gives a speedup (on this GPU the smallest circuits,
+    whose every stage is a few launch-bound microseconds) has no boundary
+    to fit.  And at each q only the c_total from its smallest speedup point
+    up: the staircase's uncut time grows with its c_total gate blocks, so
+    the fewest cuts can lose too, and a line cannot separate that band's
+    lower edge together with the upper one the method's threshold is about.
+    Returns None when one class is empty."""
     import numpy as np
 
+    lo = {}
+    for q, c, d in points:
+        if d <= 0:
+            lo[q] = min(lo.get(q, c), c)
+    both = set(lo) & {p[0] for p in points if p[2] > 0}
+    points = [p for p in points if p[0] in both and p[1] >= lo[p[0]]]
+    if not points:
+        return None
     X = np.array([[p[0], p[1]] for p in points], dtype=float)
     y = np.array([1.0 if p[2] > 0 else -1.0 for p in points])
     if (y > 0).all() or (y < 0).all():
