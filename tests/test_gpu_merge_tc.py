@@ -82,6 +82,22 @@ def test_tf32x3_deep_merge_matches_fma_at_scale(cuda_lib):
     psi_auto, _ = run(gates, q, segs, "auto")
     psi_f16, _ = run(gates, q, segs, "f16x3")
     assert torch.equal(psi_auto, psi_f16)  # AUTO picks 3xFP16 at K = 256
+    # 3xFP16 at K = 256: two 128-term groups
+    st = api.compare(psi_f16, psi_fma, "c64")
+    assert st["max_abs_diff"] <= TOL["c64"] * st["max_abs_b"], st
+
+
+def test_f16x3_long_merge_in_64_term_groups(cuda_lib):
+    # K = 1024: 3xFP16 accumulates 64 terms per group (sixteen groups, the
+    # later ones added by tensor reduce-add stores) and stays within the
+    # complex64 tolerance of the FMA merge
+    q, segs, c = 24, [12, 12], 10
+    gates = w.brickwork_cut(q, 12, 4, segs, c)
+    psi_f16, _ = run(gates, q, segs, "f16x3")
+    psi_fma, _ = run(gates, q, segs, "fma")
+    st = api.compare(psi_f16, psi_fma, "c64")
+    assert st["max_abs_diff"] <= TOL["c64"] * st["max_abs_b"], st
+    assert 1 - st["fidelity"] <= FID_TOL
 
 
 @pytest.mark.parametrize("form", ["tf32x3", "bf16x3", "f16x3", "auto"])
