@@ -166,6 +166,21 @@ bool is_rank4(int kind);
 void pauli_weights(const cc_gate& g, cd c[4]);
 cc_status check_gates(const cc_gate* gates, int n_gates, int q);
 
+// One pass's part of a program, renumbered from 0 (stages, ops, terms,
+// per-op matrices, tables), small enough to travel as the kernel parameter
+// of that pass's launch: the kernel then reads its ops and tables through the
+// constant bank instead of from global memory.  Layout: a PassBlobHeader,
+// then at its offsets the DPass, the DStages, the DOps, the DTerms, the
+// matrices (8 reals per op) and the tables (8 reals per table), each 16-byte
+// aligned.
+constexpr int PASS_BLOB_BYTES = 32 * 1024 - 64;  // kernel parameters: at most 32764 bytes
+struct alignas(16) PassBlob {
+  unsigned char b[PASS_BLOB_BYTES];
+};
+struct PassBlobHeader {
+  int32_t o_pass, o_stages, o_ops, o_terms, o_mats, o_tabs, pad[2];
+};
+
 // Device image of a program: one allocation holding ops, terms, matrices and
 // tables, reals converted to the plan's precision.
 struct DeviceProgram {
@@ -179,6 +194,9 @@ struct DeviceProgram {
   const DStage* stages = nullptr;
   std::vector<DPass> passes;
   int n_ops = 0;
+  // per pass: its blob when it fits (blob_ok), for the parameter-space launch
+  std::vector<PassBlob> blobs;
+  std::vector<char> blob_ok;
 };
 
 // Device image layout of one program inside a larger table buffer.

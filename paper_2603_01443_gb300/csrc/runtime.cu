@@ -224,6 +224,76 @@ void bind_program(DeviceProgram& dp, const HostProgram& hp, unsigned char* dev_b
   dp.n_ops = (int)hp.ops.size();
 }
 
+namespace {
+// Pass pi's blob (PassBlob layout) from the host program and its image
+// (whose per-op matrices and tables already hold the arithmetic's reals,
+// rb bytes each); false when it does not fit.
+bool build_pass_blob(const HostProgram& hp, int pi, const unsigned char* p0,
+                     const ImageLayout& L, size_t rb, PassBlob& out) {
+  const DPass& P = hp.passes[pi];
+  const int sb = P.stage_begin, se = P.stage_end;
+  const int ob = se > sb ? hp.stages[sb].op_begin : 0;
+  const int oe = se > sb ? hp.stages[se - 1].op_end : 0;
+  int tb = 0, te = 0, ab = 0, ae = 0;
+  bool any_t = false, any_a = false;
+  auto tab_range = [&](int lo, int hi) {
+    if (!any_a) { ab = lo; ae = hi; any_a = true; }
+    ab = std::min(ab, lo);
+    ae = std::max(ae, hi);
+  };
+  for (int o = ob; o < oe; ++o) {
+    const DOp& op = hp.ops[o];
+    if (op.term_end() > op.term_begin) {
+      if (!any_t) { tb = op.term_begin; te = op.term_end(); any_t = true; }
+      tb = std::min(tb, op.term_begin);
+      te = std::max(te, op.term_end());
+    }
+    if (op.n_phase) tab_range(op.blk_tab, op.blk_tab + 8);
+  }
+  for (int t = tb; t < te; ++t) {
+    const DTerm& d = hp.terms[t];
+    if (d.kind == TERM_PBLOCK) tab_range(d.tab, d.tab + 8);
+    else if (d.kind != TERM_SIGN) tab_range(d.tab, d.tab + 1);
+  }
+  const size_t n_st = se - sb, n_op = oe - ob, n_t = te - tb, n_tab = ae - ab;
+  PassBlobHeader h{};
+  size_t off = align16(sizeof(PassBlobHeader));
+  h.o_pass = (int32_t)off;   off = align16(off + sizeof(DPass));
+  h.o_stages = (int32_t)off; off = align16(off + n_st * sizeof(DStage));
+  h.o_ops = (int32_t)off;    off = align16(off + n_op * sizeof(DOp));
+  h.o_terms = (int32_t)off;  off = align16(off + n_t * sizeof(DTerm));
+  h.o_mats = (int32_t)off;   off = align16(off + n_op * 8 * rb);
+  h.o_tabs = (int32_t)off;   off = align16(off + n_tab * 8 * rb);
+  if (off > sizeof(out.b)) return false;
+  std::memset(out.b, 0, sizeof(out.b));
+  std::memcpy(out.b, &h, sizeof(h));
+  DPass q = P;
+  q.stage_begin = 0;
+  q.stage_end = (int32_t)n_st;
+  std::memcpy(out.b + h.o_pass, &q, sizeof(q));
+  for (size_t i = 0; i < n_st; ++i) {
+    DStage st = hp.stages[sb + i];
+    st.op_begin -= ob;
+    st.op_end -= ob;
+    std::memcpy(out.b + h.o_stages + i * sizeof(DStage), &st, sizeof(st));
+  }
+  for (size_t i = 0; i < n_op; ++i) {
+    DOp op = hp.ops[ob + i];
+    if (op.term_end() > op.term_begin) op.term_begin -= tb;
+    if (op.n_phase) op.blk_tab -= ab;
+    std::memcpy(out.b + h.o_ops + i * sizeof(DOp), &op, sizeof(op));
+  }
+  for (size_t i = 0; i < n_t; ++i) {
+    DTerm d = hp.terms[tb + i];
+    if (d.kind != TERM_SIGN) d.tab -= ab;
+    std::memcpy(out.b + h.o_terms + i * sizeof(DTerm), &d, sizeof(d));
+  }
+  std::memcpy(out.b + h.o_mats, p0 + L.o_mats + (size_t)ob * 8 * rb, n_op * 8 * rb);
+  std::memcpy(out.b + h.o_tabs, p0 + L.o_tabs + (size_t)ab * 8 * rb, n_tab * 8 * rb);
+  return true;
+}
+}  // namespace
+
 cc_status upload_program(const HostProgram& hp, int arith, DeviceProgram& dp) {
   std::vector<unsigned char> img;
   const ImageLayout L = append_program_image(hp, arith, img);
@@ -231,6 +301,11 @@ cc_status upload_program(const HostProgram& hp, int arith, DeviceProgram& dp) {
   if (!base) return fail(CC_ENOMEM, "device allocation of a gate program failed");
   bind_program(dp, hp, static_cast<unsigned char*>(base), L);
   dp.base = base;  // owned
+  const size_t rb = arith == GA_F32 ? 4 : 8;
+  dp.blobs.resize(hp.passes.size());
+  dp.blob_ok.assign(hp.passes.size(), 0);
+  for (size_t pi = 0; pi < hp.passes.size(); ++pi)
+    dp.blob_ok[pi] = build_pass_blob(hp, (int)pi, img.data() + L.base, L, rb, dp.blobs[pi]);
   return CC_OK;
 }
 

@@ -60,6 +60,17 @@ __device__ __forceinline__ float mad(float t, float x, float y) { return __fmaf_
 __device__ __forceinline__ double mad(double t, double x, double y) { return __fma_rn(t, x, y); }
 __device__ __forceinline__ dfl mad(dfl t, dfl x, dfl y) { return dfma(t, x, y); }
 
+// Read-only load of program data: through the non-coherent global path, or
+// (PM, the parameter-space launch) a plain load, which the compiler serves
+// from the constant bank.
+template <bool PM, typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+  if constexpr (PM)
+    return *p;
+  else
+    return __ldg(p);
+}
+
 namespace {
 
 __device__ __forceinline__ uint32_t swz(uint32_t l) {
@@ -179,7 +190,7 @@ struct StageRegs {
 // stage: it multiplies into the thread's deferred factor F (hasF set), which
 // the stage applies once before its store.  The complex128 kernels skip slot
 // 0 where T[0] = 1.
-template <typename R, int RB>
+template <typename R, int RB, bool PM>
 __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                             uint64_t c, const DTerm* __restrict__ terms,
                                             const R* __restrict__ tabs, typename CT<R>::C& F,
@@ -204,7 +215,7 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
     const float4* t4 = reinterpret_cast<const float4*>(tb);
 #pragma unroll
     for (int j2 = 0; j2 < N / 2; ++j2) {
-      const float4 f = __ldg(t4 + j2);
+      const float4 f = ldro<PM>(t4 + j2);
       cmul(a[2 * j2].x, a[2 * j2].y, f.x, f.y);
       cmul(a[2 * j2 + 1].x, a[2 * j2 + 1].y, f.z, f.w);
     }
@@ -213,7 +224,7 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       if (j == 0 && skip0) continue;
-      const float4 f = __ldg(t4 + j);
+      const float4 f = ldro<PM>(t4 + j);
       cmul(a[j].x, a[j].y, dfl(f.x, f.y), dfl(f.z, f.w));
     }
   } else {
@@ -221,7 +232,7 @@ __device__ __forceinline__ void apply_phase(typename CT<R>::C (&a)[1 << RB], con
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       if (j == 0 && skip0) continue;
-      const double2 f = __ldg(t2 + j);
+      const double2 f = ldro<PM>(t2 + j);
       cmul(a[j].x, a[j].y, f.x, f.y);
     }
   }
@@ -239,7 +250,7 @@ __device__ __forceinline__ uint32_t xor_sign(uint32_t x, uint32_t m) {
 // the CZ-type sign (-1)^{popcount(v & (v>>1) & adj)} splits into a constant,
 // a part linear in r and a part quadratic in adjacent register bits, which
 // gives the sign of every slot at once as a 32-bit mask over slots.
-template <typename R, int RB>
+template <typename R, int RB, bool PM>
 __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], const DOp& op,
                                            uint64_t c, const StageRegs<RB>& sr,
                                            const DTerm* __restrict__ terms,
@@ -297,7 +308,7 @@ __device__ __forceinline__ void apply_diag(typename CT<R>::C (&a)[1 << RB], cons
     }
   }
   if (op.term_phase_end() > op.term_sign_end())
-    apply_phase<R, RB>(a, op, c, terms, tabs, F, hasF);
+    apply_phase<R, RB, PM>(a, op, c, terms, tabs, F, hasF);
   for (int t = op.term_phase_end(); t < op.term_end(); ++t) {
     const DTerm d = terms[t];
     const int i0 = sr.index_of(d.p0), i1 = sr.index_of(d.p1);
@@ -336,25 +347,25 @@ template <typename R>
 struct Mat {
   R v[8];
 };
-template <typename R>
+template <typename R, bool PM>
 __device__ __forceinline__ Mat<R> load_mat(const R* __restrict__ p) {
   Mat<R> m;
   if constexpr (is_f32<R>()) {
-    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
-    const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    const float4 x = ldro<PM>(reinterpret_cast<const float4*>(p));
+    const float4 y = ldro<PM>(reinterpret_cast<const float4*>(p) + 1);
     m.v[0] = x.x; m.v[1] = x.y; m.v[2] = x.z; m.v[3] = x.w;
     m.v[4] = y.x; m.v[5] = y.y; m.v[6] = y.z; m.v[7] = y.w;
   } else if constexpr (is_dfl<R>()) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float4 x = __ldg(reinterpret_cast<const float4*>(p) + i);
+      const float4 x = ldro<PM>(reinterpret_cast<const float4*>(p) + i);
       m.v[2 * i] = dfl(x.x, x.y);
       m.v[2 * i + 1] = dfl(x.z, x.w);
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double2 x = __ldg(reinterpret_cast<const double2*>(p) + i);
+      const double2 x = ldro<PM>(reinterpret_cast<const double2*>(p) + i);
       m.v[2 * i] = x.x;
       m.v[2 * i + 1] = x.y;
     }
@@ -477,7 +488,7 @@ __device__ __forceinline__ V swap_pair(V v) {  // (a, b) -> (b, a) for a float4 
 // of two, 2^(k - RB)) take part; each moves 2^RB amplitudes in NV 16-byte
 // vectors per phase.  CG loads through L2 only, for vectors that other CTAs
 // of the same launch wrote.
-template <typename R, int RB, bool CG>
+template <typename R, int RB, bool CG, bool PM = false>
 __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, const DPass& P,
                                          const DStage* __restrict__ stages,
                                          const DOp* __restrict__ ops,
@@ -599,9 +610,9 @@ __device__ __forceinline__ void run_tile(typename CT<R>::C* __restrict__ vec, co
       bool hasF = false;
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const DOp op = ops[o];
-        const Mat<R> m = load_mat<R>(mats + 8 * o);
+        const Mat<R> m = load_mat<R, PM>(mats + 8 * o);
         if (op.sign_adj != 0 || op.term_end() > op.term_begin)
-          apply_diag<R, RB>(a, op, cfix, sr, terms, tabs, F, hasF);
+          apply_diag<R, RB, PM>(a, op, cfix, sr, terms, tabs, F, hasF);
 #define CC_OP_SWITCH(CALL)                                     \
   switch (op.t) {                                              \
     case 0: CALL(0); break;                                    \
@@ -685,6 +696,35 @@ __global__ void __launch_bounds__(512)
   for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x)
     run_tile<R, RB, false>(vec, P, stages, ops, terms, mats, tabs, pass->rest_bit, T, s,
                            blockDim.x, tm, s_tg, s_tp);
+}
+
+// The same pass with its part of the program as the kernel parameter (a
+// PassBlob): ops, matrices and tables are read through the constant bank,
+// loads that are the same for every thread of the warp.
+template <typename R, int RB>
+__global__ void __launch_bounds__(512)
+    stage_kernel_p(typename CT<R>::C* __restrict__ vec, const __grid_constant__ PassBlob blob,
+                   int64_t n_tiles) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const PassBlobHeader* h = reinterpret_cast<const PassBlobHeader*>(blob.b);
+  const DPass* pass = reinterpret_cast<const DPass*>(blob.b + h->o_pass);
+  const DStage* stages = reinterpret_cast<const DStage*>(blob.b + h->o_stages);
+  const DOp* ops = reinterpret_cast<const DOp*>(blob.b + h->o_ops);
+  const DTerm* terms = reinterpret_cast<const DTerm*>(blob.b + h->o_terms);
+  const R* mats = reinterpret_cast<const R*>(blob.b + h->o_mats);
+  const R* tabs = reinterpret_cast<const R*>(blob.b + h->o_tabs);
+  const DPass P = *pass;
+  constexpr int NVB = ilog2<(1 << RB) / CT<R>::PV>();
+  __shared__ int64_t s_tg[4];
+  __shared__ uint32_t s_tp[4];
+  const TileMap<NVB> tm = make_tile_map<CT<R>::PV, NVB>(P, pass, blockDim.x);
+  publish_tile_map<NVB>(tm, s_tg, s_tp);
+  __syncthreads();
+  for (int64_t T = blockIdx.x; T < n_tiles; T += gridDim.x)
+    run_tile<R, RB, false, true>(vec, P, stages, ops, terms, mats, tabs, pass->rest_bit, T, s,
+                                 blockDim.x, tm, s_tg, s_tp);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -789,6 +829,13 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// CUTSIM_PARAM_PASSES=0 launches every uncut pass with its program in global
+// memory (the segment launch always reads global memory).
+bool param_launch_enabled() {
+  const char* e = std::getenv("CUTSIM_PARAM_PASSES");
+  return !(e && e[0] == '0');
+}
+
 template <typename R, int RB>
 cc_status launch_rb(const DeviceProgram& dp, int pi, void* state, cudaStream_t stream) {
   using C = typename CT<R>::C;
@@ -814,6 +861,32 @@ cc_status launch_rb(const DeviceProgram& dp, int pi, void* state, cudaStream_t s
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem);
   occ = std::max(occ, 1);
   const int64_t grid = std::min(n_tiles, (int64_t)num_sms() * occ);
+  const bool param = pi < (int)dp.blob_ok.size() && dp.blob_ok[pi] && param_launch_enabled();
+  if (param) {
+    auto kp = stage_kernel_p<R, RB>;
+    static int attr_p[64] = {0};
+    if (dev >= 0 && dev < 64 && !attr_p[dev]) {
+      cudaFuncAttributes fa;
+      size_t static_smem = 0;
+      if (cudaFuncGetAttributes(&fa, kp) == cudaSuccess) static_smem = fa.sharedSizeBytes;
+      cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(227 * 1024 - static_smem));
+      cudaGetLastError();
+      attr_p[dev] = 1;
+    }
+    int occ_p = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, kp, nt, smem);
+    occ_p = std::max(occ_p, 1);
+    const int64_t grid_p = std::min(n_tiles, (int64_t)num_sms() * occ_p);
+    C* vp = reinterpret_cast<C*>(state);
+    int64_t ntl = n_tiles;
+    void* args[] = {&vp, const_cast<PassBlob*>(&dp.blobs[pi]), &ntl};
+    const cudaError_t le = cudaLaunchKernel(reinterpret_cast<const void*>(kp), dim3((unsigned)grid_p),
+                                            dim3(nt), args, smem, stream);
+    if (le != cudaSuccess)
+      return fail(CC_ECUDA, std::string("gate pass launch: ") + cudaGetErrorString(le));
+    return CC_OK;
+  }
   const DPass* dpass = reinterpret_cast<const DPass*>(
       reinterpret_cast<const char*>(dp.passes_dev) + sizeof(DPass) * pi);
   kern<<<(unsigned)grid, nt, smem, stream>>>(
