@@ -5,7 +5,9 @@ FP64 (CUTSIM_C128_GATES=fp64).  Both must meet the complex128 tolerance on
 single-pass and multi-pass programs (the double-float passes keep (h, l)
 pairs in HBM between passes and write complex128 in the last one), on cut
 plans, on amplitudes spanning far more than FP32's exponent range, and on
-deep circuits; the switch must really change the engine."""
+deep circuits; the switch must really change the engine.  The uncut passes'
+two launch forms (program in the kernel parameter, or in global memory)
+must agree bit for bit."""
 
 import numpy as np
 import pytest
@@ -81,3 +83,18 @@ def test_deep_multi_pass_double_float(cuda_lib, monkeypatch):
     psi, up = gpu_uncut(gates, q, "c128")
     assert up.info["n_passes"] > 1
     assert_parity(psi.cpu().numpy(), sv.simulate(q, gates), "c128", "deep dfl")
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_parameter_and_global_pass_launches_agree(cuda_lib, monkeypatch, prec):
+    # an uncut pass reads its program from its kernel parameter when it fits
+    # (the default) or from global memory; the arithmetic is the same, so
+    # the vectors are bit-identical
+    q = 20
+    gates = w.brickwork(q, 14, 21)
+    monkeypatch.setenv("CUTSIM_PARAM_PASSES", "1")
+    a, _ = gpu_uncut(gates, q, prec)
+    monkeypatch.setenv("CUTSIM_PARAM_PASSES", "0")
+    b, _ = gpu_uncut(gates, q, prec)
+    assert torch.equal(a, b)
+    assert_parity(a.cpu().numpy(), sv.simulate(q, gates), prec, "parameter launch")
