@@ -844,6 +844,12 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
   HostProgram hp;
   hp.nq = nq;
   hp.n_state = n_state;
+  // rough upper bounds (an op per item, a phase block per op), so the
+  // vectors do not grow step by step
+  hp.ops.reserve(items.size() + 16);
+  hp.mats.reserve(4 * items.size() + 64);
+  hp.terms.reserve(2 * items.size() + 64);
+  hp.tabs.reserve(8 * items.size() + 256);
   const std::vector<ItemBits> bits = item_bits(items);
   std::vector<char> applied(items.size(), 0);
   std::vector<int> order(items.size());  // the items not yet in a pass, in order
