@@ -20,7 +20,9 @@
 //   warps 2..5  epilogue: tcgen05.ld of the finished accumulator in 32 x 32
 //               blocks, staged through shared memory and written by bulk
 //               tensor stores (TMA), then release of the accumulator, so the
-//               store of tile i overlaps the MMAs of tile i+1.
+//               store of tile i overlaps the MMAs of tile i+1 (3xFP16 with
+//               K <= 32: warps 2..9, two per TMEM lane quarter, with K in
+//               three 64-byte stages).
 // Forms: merge_tc_kernel (the structure above, streaming K in 128-, 64- or
 // 32-byte blocks through 2, 4 or 8 stages of the same 192 KB), the default;
 // merge_tc_rs_kernel (row operand resident in shared memory), opt-in and
@@ -106,20 +108,23 @@ __device__ __forceinline__ int f16_scale_exp(unsigned int mb) {
 // 64 x 4); narrower, more numerous stages keep more loads in flight while the
 // tensor cores read one.  Every CTA loads its own operand tiles: no load is
 // shared between CTAs.
-template <int KIND, int KBB, int NST>
-__global__ void __launch_bounds__(192, 1)
+template <int KIND, int KBB, int NST, int EW = 4>
+__global__ void __launch_bounds__(64 + 32 * EW, 1)
     merge_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                     const __grid_constant__ CUtensorMap map_out, int n_rows, int n_cols,
                     int kblocks, int group_kb, int* err,
                     const unsigned int* __restrict__ f16_maxbits) {
   constexpr int RT = BM * KBB, CT = BN * KBB, STB = 2 * RT + 2 * CT;
-  static_assert(NST * STB == STAGES * STAGE_BYTES, "operand buffers of 192 KB");
+  constexpr int STG_ALL = EW * 2 * STG_BYTES;  // epilogue staging: 2 boxes per warp
+  static_assert(EW == 4 || EW == 8, "one or two epilogue warps per TMEM lane quarter");
+  static_assert(EW == 8 || NST * STB == STAGES * STAGE_BYTES, "operand buffers of 192 KB");
+  static_assert(NST * STB + STG_ALL + 1024 + 256 <= SMEM_LIMIT, "shared memory");
   static_assert((2 * NST + 8) * 8 <= 256, "barrier area");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stg_base = smem + NST * STB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_TOTAL);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_base + STG_ALL);
   uint64_t* full = bars;                  // [NST]
   uint64_t* empty = bars + NST;           // [NST]
   uint64_t* tfull = bars + 2 * NST;       // [2]
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);
+      mbar_init(&tempty[a], EW);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -251,12 +256,16 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4.  Each 32 x 32 block
+    // epilogue warps 2..1+EW: TMEM lane quarter = warp % 4 (with EW = 8 two
+    // warps per quarter, each over half of the columns).  Each 32 x 32 block
     // of the accumulator goes TMEM -> registers -> a 128-byte-swizzled staging
     // buffer (conflict-free: a lane's row keeps its 16-byte chunks at j ^ (row & 7))
     // -> one bulk tensor store; two buffers keep one store in flight.
     const int quarter = warp & 3;
-    unsigned char* stg = stg_base + quarter * 2 * STG_BYTES;
+    const int ew = warp - 2;
+    constexpr int CB = BN / 32 / (EW / 4);  // 32-column blocks per warp
+    const int cb0 = (ew >> 2) * CB;
+    unsigned char* stg = stg_base + ew * 2 * STG_BYTES;
     int buf = 0;
     int iter = 0;
     bool ok_all = true;
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
-        for (int c2 = 0; c2 < BN / 32; c2 += 2) {
+        for (int c2 = cb0; c2 < cb0 + CB; c2 += 2) {
           uint32_t rr[2][32];
           tmem_ld32x2(tbase + (uint32_t)(c2 * 32), rr[0], rr[1]);
 #pragma unroll
@@ -812,6 +821,18 @@ void* tc_kernel_ptr(int kbb) {
   return reinterpret_cast<void*>(merge_tc_kernel<KIND, 32, 8>);
 }
 
+constexpr int kEpi8Smem = 3 * (2 * BM + 2 * BN) * 64 + 8 * 2 * STG_BYTES + 1024 + 256;
+
+// Eight epilogue warps for 3xFP16 merges whose K fits one 128-byte block
+// (K <= 32): there the output stream, not the operand stream, sets the pace
+// (q = 30, K = 16: 1.60 -> 1.50 ms), while at K = 64 the smaller operand
+// stages cost more than the wider epilogue gains (1.60 -> 1.75 ms).
+// CUTSIM_TC_EPI8 = 0 / 1 forces the choice.
+bool epi8_for(int kr_bytes) {
+  if (const char* e = std::getenv("CUTSIM_TC_EPI8")) return e[0] == '1';
+  return kr_bytes <= KB_BYTES;
+}
+
 int kr_of(int64_t K, int form) {
   const int kelem = form != CC_MERGE_TF32X3 ? KB_BYTES / 2 : KB_BYTES / 4;
   return (int)(((2 * K + kelem - 1) / kelem) * kelem);
@@ -905,7 +926,10 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
   }
 
   // The streaming form reads K blocks of kbb bytes (its own swizzle width).
-  const int kbb = tc_kblock(KR * eb / KB_BYTES);
+  // 3xFP16 with eight epilogue warps (two per TMEM lane quarter) streams K
+  // in three 64-byte stages to leave room for their staging buffers
+  const bool epi8 = form == CC_MERGE_F16X3 && epi8_for(KR * eb);
+  const int kbb = epi8 ? 64 : tc_kblock(KR * eb / KB_BYTES);
   CUtensorMap map_r_k, map_c_k;
   {
     const cuuint64_t dims[2] = {(cuuint64_t)KR, (cuuint64_t)(2 * NB)};
@@ -947,6 +971,8 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
       cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_TF32X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
       cudaFuncSetAttribute(tc_kernel_ptr<CC_MERGE_F16X3>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     }
+    cudaFuncSetAttribute(merge_tc_kernel<CC_MERGE_F16X3, 64, 3, 8>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kEpi8Smem);
     attr_done[dev] = 1;
   }
   const int n_rows = (int)NB, n_cols = (int)(2 * NA);
@@ -969,9 +995,10 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
                                         : merge_tc_rs_kernel<CC_MERGE_TF32X3>;
     kern<<<grid, 192, smem_rs, s>>>(map_r, map_c, map_out, n_rows, n_cols, kblocks, rs_stages, err);
   } else {
-    const void* kern = form == CC_MERGE_BF16X3  ? tc_kernel_ptr<CC_MERGE_BF16X3>(kbb)
-                       : form == CC_MERGE_F16X3 ? tc_kernel_ptr<CC_MERGE_F16X3>(kbb)
-                                                : tc_kernel_ptr<CC_MERGE_TF32X3>(kbb);
+    const void* kern = epi8 ? reinterpret_cast<const void*>(merge_tc_kernel<CC_MERGE_F16X3, 64, 3, 8>)
+                       : form == CC_MERGE_BF16X3 ? tc_kernel_ptr<CC_MERGE_BF16X3>(kbb)
+                       : form == CC_MERGE_F16X3  ? tc_kernel_ptr<CC_MERGE_F16X3>(kbb)
+                                                 : tc_kernel_ptr<CC_MERGE_TF32X3>(kbb);
     const int kb_n = KR * eb / kbb;
     // 3xTF32 and 3xFP16 (11-bit significands): at most 64 terms per accumulation
     const int64_t gterms = form == CC_MERGE_F16X3 ? f16_group_terms(st.K) : kTf32GroupTerms;
@@ -979,7 +1006,8 @@ cc_status launch_merge_tc(const MergeStage& st, int form, void* workspace, uint6
     int a_rows = n_rows, a_cols = n_cols, a_kb = kb_n, a_gkb = std::min(gkb, kb_n);
     const unsigned int* a_mb = f16_maxbits;
     void* args[] = {&map_r_k, &map_c_k, &map_out, &a_rows, &a_cols, &a_kb, &a_gkb, &err, &a_mb};
-    const cudaError_t le = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(192), args, SMEM_BYTES, s);
+    const cudaError_t le = cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(epi8 ? 320 : 192), args,
+                                            epi8 ? kEpi8Smem : SMEM_BYTES, s);
     if (le != cudaSuccess)
       return fail(CC_ECUDA, std::string("tensor-core merge launch: ") + cudaGetErrorString(le));
   }
