@@ -56,6 +56,23 @@ def test_fit_boundary_recovers_a_separating_line(slope, intercept):
             assert math.copysign(1, side) == math.copysign(1, d), (q, c, d, fit)
 
 
+def test_fit_boundary_takes_the_upper_edge_of_a_band():
+    # speedups only between a lower edge (the fewest cuts lose too, as on the
+    # staircase, whose uncut time grows with its cut blocks) and the line
+    # c = 0.5 q - 2; q below 12 has no speedup at all
+    slope, intercept = 0.5, -2.0
+    pts = []
+    for q in range(4, 31, 2):
+        for c in range(0, 15):
+            up = c - (slope * q + intercept)
+            if abs(up) < 1e-9:
+                continue
+            win = q >= 12 and c >= 3 and up < 0
+            pts.append((q, c, -1.0 if win else 1.0))
+    fit = bench.fit_boundary(pts)
+    assert abs(fit["slope"] - slope) < 0.1 and abs(fit["intercept"] - intercept) < 1.5, fit
+
+
 def test_fit_boundary_needs_both_classes():
     assert bench.fit_boundary([(4, 1, -0.5), (6, 2, -0.1)]) is None
 
