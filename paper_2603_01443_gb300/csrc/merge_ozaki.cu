@@ -80,77 +80,131 @@ constexpr int OZ_BAND = 16;
 constexpr int32_t OZ_ZERO_EXP = -4000;
 
 // ---------------------------------------------------------------- splitting
-__device__ __forceinline__ double ozaki_operand(const double2* __restrict__ A,
-                                                const double2* __restrict__ B, int64_t NA,
-                                                int64_t NB, int K, const int32_t* __restrict__ aidx,
-                                                const int32_t* __restrict__ bidx, int64_t row,
-                                                int kk) {
-  if (kk >= 2 * K) return 0.0;
-  if (row < NB) {
-    const double2 b = B[(int64_t)bidx[kk % K] * NB + row];
-    return kk < K ? b.x : b.y;
+// v = X 2^(e - 53) with X rounded to an integer (|v| < 2^e), cut into OZ_S
+// balanced base-2^9 digits, most significant first (|d_i| <= 256); out[i] is
+// d_i 2^(-9 i), exact in bf16.
+__device__ __forceinline__ void ozaki_digits(double v, int32_t e, float (&out)[OZ_S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ev = (int)((bits >> 52) & 0x7FF);
+  long long X = 0;
+  if (e != OZ_ZERO_EXP && (bits & 0x7FFFFFFFFFFFFFFFull) != 0) {
+    // v = mant 2^(ev - 1075), X = round(v 2^(53 - e)) = round(mant 2^(ev - 1022 - e))
+    const unsigned long long mant =
+        ev == 0 ? (bits & 0xFFFFFFFFFFFFFull) << 1 : (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e + 1022 - ev;  // >= 0 since |v| < 2^e: a right shift
+    unsigned long long m = 0;
+    if (sh == 0) m = mant;
+    else if (sh < 64) m = (mant + (1ull << (sh - 1))) >> sh;
+    X = (bits >> 63) ? -(long long)m : (long long)m;
   }
-  const int64_t n = row - NB;
-  const double2 a = A[(int64_t)aidx[kk % K] * NA + (n >> 1)];
-  if ((n & 1) == 0) return kk < K ? a.x : -a.y;
-  return kk < K ? a.y : a.x;
+  const float scale[OZ_S] = {1.0f, 0x1p-9f, 0x1p-18f, 0x1p-27f, 0x1p-36f, 0x1p-45f};
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i) {
+    const int sh = OZ_BETA * (OZ_S - 1 - i);
+    long long d = X;
+    if (sh > 0) d = (X + (1ll << (sh - 1))) >> sh;
+    X -= d << sh;
+    out[i] = (float)d * scale[i];
+  }
 }
 
-// One warp per operand row: rows [0, NB) are R (from the upper factor B),
-// rows [NB, NB + 2 NA) are Cop (from the lower factor A).  Writes the row's
-// exponent and its 6 slices (slice i of row r at sl[(i * rows_of_operand + r) * KR]).
+// The split through a shared-memory transpose.  A block takes 64 operand
+// rows: 64 rows y of R (from the upper factor B), or 32 amplitudes x of A,
+// giving rows 2x and 2x+1 of Cop.  First each row's exponent, from the
+// largest |re| and |im| of its amplitude over the K slices (2^e > that
+// maximum); then the padded K range in chunks of 32, each warp loading
+// contiguous 32-amplitude runs of one slice, and the rows' digits written as
+// contiguous runs of each slice (slice i of row r at
+// sl[(i * rows_of_operand + r) * KR]).
+constexpr int kOzRows = 64, kOzChunk = 32;
 __global__ void __launch_bounds__(256)
     ozaki_split(const double2* __restrict__ A, const double2* __restrict__ B, int qa, int qb,
                 int K, int KR, const int32_t* __restrict__ aidx, const int32_t* __restrict__ bidx,
                 __nv_bfloat16* __restrict__ r_sl, __nv_bfloat16* __restrict__ c_sl,
                 int32_t* __restrict__ e_row, int32_t* __restrict__ f_col) {
+  __shared__ double T[kOzRows][kOzChunk + 1];
+  __shared__ unsigned long long s_mx[8][kOzRows];
+  __shared__ int32_t s_e[kOzRows];
   const int64_t NA = int64_t(1) << qa, NB = int64_t(1) << qb;
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= NB + 2 * NA) return;
-  // largest magnitude of the row: |v| orders like its bits with the sign cleared
-  unsigned long long mx = 0;
-  for (int kk = lane; kk < KR; kk += 32) {
-    const double v = ozaki_operand(A, B, NA, NB, K, aidx, bidx, row, kk);
-    mx = max(mx, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  // 2^e > max |v|: a normal max = 1.m 2^(E - 1023) < 2^(E - 1022)
-  const int32_t e = mx == 0 ? OZ_ZERO_EXP : (int32_t)((mx >> 52) & 0x7FF) - 1022;
-  const bool is_r = row < NB;
-  const int64_t r = is_r ? row : row - NB;
+  const int64_t r_blocks = NB / kOzRows;
+  const bool is_r = (int64_t)blockIdx.x < r_blocks;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = is_r ? (int64_t)blockIdx.x * kOzRows
+                            : ((int64_t)blockIdx.x - r_blocks) * kOzRows;
+  const int64_t amp0 = is_r ? row0 : row0 / 2;
+  const int qn = is_r ? qb : qa;
+  const double2* __restrict__ X = is_r ? B : A;
+  const int32_t* __restrict__ idx = is_r ? bidx : aidx;
   const int64_t plane = is_r ? NB : 2 * NA;
-  __nv_bfloat16* sl = is_r ? r_sl : c_sl;
-  if (lane == 0) {
-    if (is_r) e_row[r] = e;
-    else f_col[r] = e;
+  __nv_bfloat16* const sl = is_r ? r_sl : c_sl;
+  // |v| orders like its bits with the sign cleared
+  const unsigned long long abs_mask = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long m0 = 0, m1 = 0;
+  for (int k = warp; k < K; k += 8) {
+    const int64_t base = ((int64_t)idx[k] << qn) + amp0;
+    const double2 v0 = X[base + lane];
+    m0 = max(m0, max((unsigned long long)__double_as_longlong(v0.x) & abs_mask,
+                     (unsigned long long)__double_as_longlong(v0.y) & abs_mask));
+    if (is_r) {
+      const double2 v1 = X[base + 32 + lane];
+      m1 = max(m1, max((unsigned long long)__double_as_longlong(v1.x) & abs_mask,
+                       (unsigned long long)__double_as_longlong(v1.y) & abs_mask));
+    }
   }
-  const float scale[OZ_S] = {1.0f, 0x1p-9f, 0x1p-18f, 0x1p-27f, 0x1p-36f, 0x1p-45f};
-  for (int kk = lane; kk < KR; kk += 32) {
-    const double v = ozaki_operand(A, B, NA, NB, K, aidx, bidx, row, kk);
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    const int ev = (int)((bits >> 52) & 0x7FF);
-    long long X = 0;
-    if (e != OZ_ZERO_EXP && (bits & 0x7FFFFFFFFFFFFFFFull) != 0) {
-      // v = mant 2^(ev - 1075), X = round(v 2^(53 - e)) = round(mant 2^(ev - 1022 - e))
-      const unsigned long long mant =
-          ev == 0 ? (bits & 0xFFFFFFFFFFFFFull) << 1 : (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      const int sh = e + 1022 - ev;  // >= 0 since |v| < 2^e: a right shift
-      unsigned long long m = 0;
-      if (sh == 0) m = mant;
-      else if (sh < 64) m = (mant + (1ull << (sh - 1))) >> sh;
-      X = (bits >> 63) ? -(long long)m : (long long)m;
+  s_mx[warp][lane] = m0;
+  s_mx[warp][32 + lane] = m1;
+  __syncthreads();
+  const int n_amp = is_r ? 64 : 32;
+  if ((int)threadIdx.x < n_amp) {
+    unsigned long long mx = 0;
+    for (int w = 0; w < 8; ++w) mx = max(mx, s_mx[w][threadIdx.x]);
+    // 2^e > max |v|: a normal max = 1.m 2^(E - 1023) < 2^(E - 1022)
+    const int32_t e = mx == 0 ? OZ_ZERO_EXP : (int32_t)((mx >> 52) & 0x7FF) - 1022;
+    if (is_r) {
+      s_e[threadIdx.x] = e;
+      e_row[row0 + threadIdx.x] = e;
+    } else {
+      s_e[2 * threadIdx.x] = s_e[2 * threadIdx.x + 1] = e;
+      f_col[row0 + 2 * threadIdx.x] = e;
+      f_col[row0 + 2 * threadIdx.x + 1] = e;
     }
-    // balanced base-2^9 digits, most significant first; |d_i| <= 256
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < KR; c0 += kOzChunk) {
+    for (int kl = warp; kl < kOzChunk; kl += 8) {
+      const int kk = c0 + kl;
+      const bool used = kk < 2 * K, re = kk < K;
+      const int k = re ? kk : kk - K;
+      if (is_r) {
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) {
-      const int sh = OZ_BETA * (OZ_S - 1 - i);
-      long long d = X;
-      if (sh > 0) d = (X + (1ll << (sh - 1))) >> sh;
-      X -= d << sh;
-      sl[((int64_t)i * plane + r) * KR + kk] = __float2bfloat16_rn((float)d * scale[i]);
+        for (int h = 0; h < 2; ++h) {
+          double v = 0.0;
+          if (used) {
+            const double2 b = B[((int64_t)bidx[k] << qb) + amp0 + h * 32 + lane];
+            v = re ? b.x : b.y;
+          }
+          T[h * 32 + lane][kl] = v;
+        }
+      } else {
+        double v0 = 0.0, v1 = 0.0;
+        if (used) {
+          const double2 a = A[((int64_t)aidx[k] << qa) + amp0 + lane];
+          v0 = re ? a.x : -a.y;  // row 2x
+          v1 = re ? a.y : a.x;   // row 2x + 1
+        }
+        T[2 * lane][kl] = v0;
+        T[2 * lane + 1][kl] = v1;
+      }
     }
+    __syncthreads();
+    for (int r = warp; r < kOzRows; r += 8) {
+      float d[OZ_S];
+      ozaki_digits(T[r][lane], s_e[r], d);
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i)
+        sl[((int64_t)i * plane + row0 + r) * KR + c0 + lane] = __float2bfloat16_rn(d[i]);
+    }
+    __syncthreads();
   }
 }
 
@@ -655,8 +709,9 @@ cc_status launch_merge_ozaki(const MergeStage& st, void* workspace, uint64_t ws_
   int32_t* f_col = reinterpret_cast<int32_t*>(ws + L.f_col);
   cudaStream_t s = (cudaStream_t)stream;
 
-  const int64_t rows = NB + 2 * NA;
-  ozaki_split<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(
+  // 64 operand rows per block: NB of R and 2 NA of Cop (NB, NA >= 2^7)
+  const int64_t blocks = NB / kOzRows + 2 * NA / kOzRows;
+  ozaki_split<<<(unsigned)blocks, 256, 0, s>>>(
       (const double2*)st.A, (const double2*)st.B, st.qa, st.qb, (int)st.K, KR, st.aidx, st.bidx,
       r_sl, c_sl, e_row, f_col);
 
