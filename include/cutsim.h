@@ -80,8 +80,10 @@ typedef enum { CC_DECOMP_PROJECTOR = 0, CC_DECOMP_S_SDG = 1 } cc_decomp;
  *                    operand scaled by a power of two (its largest entry just
  *                    below 1, so no entry leaves fp16's range), split
  *                    x = hi + lo in fp16 and hi*hi + hi*lo + lo*hi accumulated
- *                    in FP32, at most 64 terms per accumulation, the two
- *                    scales undone in the epilogue: the significands
+ *                    in FP32, at most 128 terms per accumulation up to
+ *                    K = 256 and 64 beyond (longer K adds the partial sums
+ *                    with FP32 tensor reduce-add stores), the two scales
+ *                    undone in the epilogue: the significands
  *                    of 3xTF32 (11 bits each) in half the operand bytes at
  *                    twice the tensor rate (CC_C64 plans, both factors >= 2^7
  *                    amplitudes; max|dpsi|/max|psi| <= 2e-6).
@@ -294,7 +296,11 @@ cc_status cc_kak_gates(const double* u, int32_t q0, int32_t q1, cc_gate* out, in
 cc_status cc_uncut_info(const cc_uncut* u, int32_t* n_passes, int32_t* n_ops, int32_t* tile_bits);
 
 /* cc_simulate_uncut -- psi = C|0...0> over the full 2^q vector (T_orig).
- * psi_bytes >= 2^q * amplitude size.  Asynchronous on `stream`. */
+ * psi_bytes >= 2^q * amplitude size.  Asynchronous on `stream`.  Complex128
+ * gate passes compute in double-float (FP32 pairs, about 48 significant
+ * bits; CUTSIM_C128_GATES=fp64 selects native FP64); the vector between
+ * passes holds the pairs in the same 16 bytes per amplitude, and the last
+ * pass writes complex128. */
 cc_status cc_simulate_uncut(const cc_uncut* u, void* psi, uint64_t psi_bytes, void* stream);
 
 void cc_uncut_destroy(cc_uncut* u);
@@ -354,7 +360,7 @@ cc_status cc_gather_static(const void* psi, int64_t n_amp, int32_t precision, co
  *     n_seg = 3, ...), each over the output tiles of every circuit's stage at
  *     that level, on CUDA cores (CC_MERGE_FMA arithmetic); a circuit's final
  *     stage with K >= 8 terms and both factors >= 2^7 amplitudes (complex64)
- *     runs instead as its own 3xTF32 tensor-core merge after its level, as
+ *     runs instead as its own tensor-core merge (3xFP16) after its level, as
  *     CC_MERGE_AUTO would run it (CUTSIM_BATCH_TC=0: all on CUDA cores).
  * The whole sequence can be captured once into a CUDA graph and replayed.
  *
