@@ -347,15 +347,31 @@ def oracle_timing_main(spec):
             t_sub = time.perf_counter() - t0
             L = 1 << segs[0]
             n_slabs_total = (1 << q) // L
+            # an untimed pass first maps every worker's view of the shared
+            # subcircuit vectors; chunks of a few slabs keep the tail of each
+            # pass (workers idle while the last chunks finish) short
+            pool.map(_ow_slab, [j * L for j in range(min(n_slabs_total, 4 * cores))], chunksize=1)
+            # each sample is timed in `reps` passes over different slabs
+            # (every pass and sample at its own offset inside the stride), the
+            # passes of the samples interleaved so that all samples see the
+            # same load on a shared host, and the median pass taken: one pass
+            # of a second or so varies by 10-20 % from one second to the next
+            reps = int(spec.get("reps", 3))
+            sizes = [min(S, n_slabs_total) for S in spec["slabs"]]
+            n_pass = reps * len(sizes)
+            passes = [[] for _ in sizes]
+            for r in range(reps):
+                for si, S in enumerate(sizes):
+                    stride = n_slabs_total // S
+                    shift = (stride * (si * reps + r)) // n_pass
+                    x0s = [(j * stride + shift) * L for j in range(S)]
+                    t0 = time.perf_counter()
+                    pool.map(_ow_slab, x0s, chunksize=max(1, S // (16 * cores)))
+                    passes[si].append(time.perf_counter() - t0)
             est = []
-            for S in spec["slabs"]:
-                S = min(S, n_slabs_total)
-                stride = n_slabs_total // S
-                x0s = [(j * stride + (stride // 2 if len(est) else 0)) * L for j in range(S)]
-                t0 = time.perf_counter()
-                pool.map(_ow_slab, x0s, chunksize=max(1, S // (4 * cores)))
-                t_s = time.perf_counter() - t0
-                est.append({"slabs": S, "slab_amplitudes": L, "seconds": t_s,
+            for S, ps in zip(sizes, passes):
+                t_s = statistics.median(ps)
+                est.append({"slabs": S, "slab_amplitudes": L, "seconds": t_s, "passes_s": ps,
                             "t_merge": t_s * n_slabs_total / S})
             if spec.get("sample_seed") is not None:
                 xs = w.sample_indices(q, 4096, spec["sample_seed"])
@@ -405,7 +421,8 @@ def cpu_record(d, a):
         "sample": (f"Algorithm 1 in full; Algorithm 2 in full ({d['n_sub']} subcircuits over "
                    f"{d['cores']} worker processes); the Algorithm 3 sum (per-amplitude form) on "
                    f"{e0['slabs']} contiguous slabs of {e0['slab_amplitudes']} amplitudes spread "
-                   f"evenly over the 2^{a.q} output, scaled by the slab count"),
+                   f"evenly over the 2^{a.q} output, scaled by the slab count (median of "
+                   f"{len(e0.get('passes_s', [0]))} passes over different slabs)"),
         "sample_seconds": d["t_pre"] + d["t_sub"] + e0["seconds"],
         "stages": {"pre_s": d["t_pre"], "sub_s": d["t_sub"], "merge_s": e0["t_merge"]},
     }

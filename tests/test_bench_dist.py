@@ -64,6 +64,8 @@ def test_oracle_timing_on_small_workload():
     assert "error" not in d, d
     assert d["n_sub"] == 8 and d["cores"] >= 1
     assert [e["slabs"] for e in d["merge_estimates"]] == [8, 16]
+    for e in d["merge_estimates"]:  # the median of three timed passes
+        assert len(e["passes_s"]) == 3 and e["seconds"] == sorted(e["passes_s"])[1]
     rec = bench.cpu_record(d, a)
     assert rec["cores"] == d["cores"] and rec["kind"] == "oracle" and rec["value"] > 0
     assert set(rec["convergence"]) == {"slabs", "t_merge_s", "ratio"}
