@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <exception>
@@ -100,6 +101,29 @@ extern "C" cc_status cc_plan_create(const cc_gate* gates, int32_t n_gates, int32
                          seg_tile_bits(precision), out);
 }
 
+namespace {
+
+// The segment compile threads of one plan: on leaving scope (a failed plan,
+// an exception) the threads still waiting are told to leave, and all joined.
+struct CompileThreads {
+  std::atomic<int>& go;
+  std::vector<std::thread> th;
+  explicit CompileThreads(std::atomic<int>& g) : go(g) {}
+  CompileThreads(const CompileThreads&) = delete;
+  CompileThreads& operator=(const CompileThreads&) = delete;
+  void join() {
+    for (auto& t : th)
+      if (t.joinable()) t.join();
+  }
+  ~CompileThreads() {
+    int wait = 0;
+    go.compare_exchange_strong(wait, 2);
+    join();
+  }
+};
+
+}  // namespace
+
 cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* seg_sizes,
                           int n_seg, int decomp, int precision, int seg_kmax, cc_plan** out,
                           bool host_only) {
@@ -145,6 +169,38 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
       for (int i = 0; i < n_seg; ++i) items[i].reserve(n_in[i]);
     }
     p->seg_cut_ids.assign(n_seg, {});
+
+    // One shared program per segment.  The programs are independent host
+    // work, so segments after the first compile on their own threads.  The
+    // threads start here, before the items are built, so that their start-up
+    // (tens of microseconds) overlaps that work: each waits for `go`, then
+    // compiles its segment, or leaves when the plan fails first.  Where a
+    // thread cannot be started, its segment compiles on this one.
+    std::vector<std::exception_ptr> errs(n_seg);
+    std::atomic<int> go{0};  // 0: wait, 1: compile, 2: leave
+    auto work = [&](int i) {
+      try {
+        p->hprog[i] = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i], seg_kmax,
+                                      low_tile_bits(precision), reg_bits_max(precision));
+      } catch (...) {
+        errs[i] = std::current_exception();
+      }
+    };
+    auto worker = [&](int i) {
+      int g;
+      while ((g = go.load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+      if (g == 1) work(i);
+    };
+    CompileThreads pool(go);
+    std::vector<int> inline_segs;
+    for (int i = 1; i < n_seg; ++i) {
+      try {
+        pool.th.emplace_back(worker, i);
+      } catch (...) {
+        inline_segs.push_back(i);
+      }
+    }
+
     for (int g = 0; g < n_gates; ++g) {
       const cc_gate& gt = gates[g];
       const bool two = is_two_qubit(gt.kind);
@@ -240,36 +296,14 @@ cc_status cc::create_plan(const cc_gate* gates, int n_gates, int q, const int* s
     p->seg_buf_bytes = (uint64_t)off * ab;
     p->psi_bytes = (uint64_t(1) << q) * ab;
 
-    // One shared program per segment.  The programs are independent host
-    // work, so segments after the first compile on their own threads (where
-    // a thread cannot be started, its segment compiles on this one).
+    // The segment programs (the threads started above take segments 1..n-1).
     p->hprog.resize(n_seg);
-    {
-      std::vector<std::exception_ptr> errs(n_seg);
-      auto work = [&](int i) {
-        try {
-          p->hprog[i] = compile_program(items[i], p->seg_q[i] + p->seg_c[i], p->seg_q[i],
-                                        seg_kmax, low_tile_bits(precision),
-                                        reg_bits_max(precision));
-        } catch (...) {
-          errs[i] = std::current_exception();
-        }
-      };
-      std::vector<std::thread> pool;
-      std::vector<int> inline_segs;
-      for (int i = 1; i < n_seg; ++i) {
-        try {
-          pool.emplace_back(work, i);
-        } catch (...) {
-          inline_segs.push_back(i);
-        }
-      }
-      work(0);
-      for (int i : inline_segs) work(i);
-      for (auto& t : pool) t.join();
-      for (auto& e : errs)
-        if (e) std::rethrow_exception(e);
-    }
+    go.store(1, std::memory_order_release);
+    work(0);
+    for (int i : inline_segs) work(i);
+    pool.join();
+    for (auto& e : errs)
+      if (e) std::rethrow_exception(e);
     for (int i = 0; i < n_seg; ++i)
       if (p->hprog[i].nq < 0) return fail(CC_ERANGE, "pass planner made no progress");
 
