@@ -233,3 +233,22 @@ def test_last_error_is_per_thread(L):
     t1.start(); t2.start(); t1.join(); t2.join()
     assert msgs["seg"] == {b"segment index out of range"}
     assert msgs["sum"] == {b"segment sizes do not sum to q"}
+
+
+def test_plans_leave_no_compile_threads(L):
+    # segments after the first compile on threads that start before the gate
+    # items are built; a plan that fails before its programs are compiled (a
+    # cut between non-adjacent segments of an 8-segment chain) releases and
+    # joins them, as does one that compiles: the process's thread count is
+    # the same afterwards
+    if not os.path.isdir("/proc/self/task"):
+        pytest.skip("needs /proc/self/task")
+    bad = [w.Gate("H", 0), w.Gate("CZ", 0, 8)]
+    good = w.brickwork_cut(16, 6, 3, [2] * 8, [1] * 7)
+    before = len(os.listdir("/proc/self/task"))
+    for _ in range(50):
+        assert _create(L, bad, 16, [2] * 8)[0] == 3
+    for seg in range(8):
+        words, _ = api.plan_program_image(good, 16, [2] * 8, seg)
+        assert len(words) > 0
+    assert len(os.listdir("/proc/self/task")) == before
