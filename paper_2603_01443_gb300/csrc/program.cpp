@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <stdexcept>
 
 #include "internal.h"
 
@@ -313,25 +314,49 @@ void drop_applied(std::vector<int>& order, const std::vector<char>& applied) {
 // Forward scan over the items listed in `order` that are not yet applied: an
 // item is taken when none of its qubits is blocked and it is diagonal or its
 // qubit is in `dense_ok`; otherwise its qubits become blocked, so no later item
-// on them can overtake it.  Returns the number of dense items taken.
-int scan(const std::vector<ItemBits>& bits, const std::vector<int>& order,
-         const std::vector<char>& applied, uint64_t dense_ok, std::vector<int>* take) {
+// on them can overtake it.  The taken items are appended to `take`.
+void scan(const std::vector<ItemBits>& bits, const std::vector<int>& order,
+          const std::vector<char>& applied, uint64_t dense_ok, std::vector<int>& take) {
   uint64_t blocked = 0;
-  int dense = 0;
   for (int i : order) {
-    // counting only: once every allowed qubit is blocked no dense item can
-    // be taken any more
-    if (!take && !(dense_ok & ~blocked)) break;
     if (applied[i]) continue;
     const ItemBits b = bits[i];
     if ((b.mask & blocked) || (b.dense & ~dense_ok)) {
       blocked |= b.mask;
       continue;
     }
-    if (b.dense) ++dense;
-    if (take) take->push_back(i);
+    take.push_back(i);
   }
-  return dense;
+}
+
+// counts[c] = the number of dense items scan() would take with dense_ok =
+// oks[c], for every candidate c in one pass over the items and without
+// branches on them: the candidates' blocked masks are independent chains, so
+// the pass runs at instruction throughput rather than at the latency of one
+// chain.  Once every allowed qubit of a candidate is blocked no dense item
+// can be taken for it any more (such an item's qubit is blocked), so the pass
+// stops when that holds for all of them.
+constexpr int kMaxCands = 66;  // the earliest-items set and up to 64 windows
+
+void count_dense(const std::vector<ItemBits>& bits, const std::vector<int>& order,
+                 const std::vector<char>& applied, const uint64_t* oks, int nc, int* counts) {
+  uint64_t blocked[kMaxCands];
+  for (int c = 0; c < nc; ++c) {
+    blocked[c] = 0;
+    counts[c] = 0;
+  }
+  for (int i : order) {
+    const ItemBits b = bits[i];
+    const uint64_t live = applied[i] ? 0ull : ~0ull;
+    uint64_t open = 0;
+    for (int c = 0; c < nc; ++c) {
+      const uint64_t hit = ((b.mask & blocked[c]) | (b.dense & ~oks[c])) ? ~0ull : 0ull;
+      blocked[c] |= b.mask & hit & live;
+      counts[c] += (int)((b.dense & ~hit & live) != 0);
+      open |= oks[c] & ~blocked[c];
+    }
+    if (!open) break;
+  }
 }
 
 // Choose `width` qubits out of `pool` (ascending) for the dense items to act
@@ -376,15 +401,17 @@ uint64_t choose_set(const std::vector<ItemBits>& bits, const std::vector<int>& o
     for (int w = 0; w < width; ++w) m |= 1ull << pool[s + w];
     cands.push_back(m);
   }
+  const int nc = (int)cands.size();  // <= 65: a pool holds at most 64 qubits
+  if (nc > kMaxCands) throw std::length_error("candidate qubit sets");
+  int counts[kMaxCands];
+  count_dense(bits, order, applied, cands.data(), nc, counts);
   uint64_t best = cands[0];
   int best_d = -1;
-  for (uint64_t m : cands) {
-    const int d = scan(bits, order, applied, m, nullptr);
-    if (d > best_d) {
-      best_d = d;
-      best = m;
+  for (int c = 0; c < nc; ++c)
+    if (counts[c] > best_d) {
+      best_d = counts[c];
+      best = cands[c];
     }
-  }
   return best;
 }
 
@@ -612,11 +639,13 @@ struct PassBuilder {
       const int top = 31 - __builtin_clz((unsigned)j);
       P[j] = P[j ^ (1 << top)] * h[top];
     }
-    for (int j = 0; j < 32; ++j) {
-      int neg = 0;
-      for (const auto& pr : signs) neg ^= (j >> pr.first) & (j >> pr.second) & 1;
-      T[j] = neg ? -P[j] : P[j];
-    }
+    // entry j is negated once for each sign pair whose two bits are both set
+    // in j: bit j of slot_bit[i] is bit i of j
+    static constexpr uint32_t slot_bit[MAX_REG_BITS] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u,
+                                                        0xFF00FF00u, 0xFFFF0000u};
+    uint32_t neg = 0;
+    for (const auto& pr : signs) neg ^= slot_bit[pr.first] & slot_bit[pr.second];
+    for (int j = 0; j < 32; ++j) T[j] = ((neg >> j) & 1u) ? -P[j] : P[j];
     DTerm b{};
     b.kind = TERM_PBLOCK;
     b.p0 = (uint8_t)(K != cd(1.0) ? 1 : 0);
@@ -813,7 +842,7 @@ void add_pass(HostProgram& hp, const std::vector<Item>& items, const std::vector
       if (regs & (1ull << j)) qubits.push_back(j);
     std::vector<int> st_items;
     st_items.reserve(rest.size());
-    scan(bits, rest, done, regs, &st_items);
+    scan(bits, rest, done, regs, st_items);
     DStage st{};
     pb.begin_stage(qubits, st);
     for (int i : st_items) {
@@ -874,7 +903,7 @@ HostProgram compile_program(const std::vector<Item>& items, int nq, int n_state,
       if (tile & (1ull << j)) tile_bits.push_back(j);
     std::vector<int> take;
     take.reserve(order.size());
-    scan(bits, order, applied, tile, &take);
+    scan(bits, order, applied, tile, take);
     if (take.empty() && left > 0) {  // cannot happen: the first pending item always fits
       hp.nq = -1;
       return hp;
