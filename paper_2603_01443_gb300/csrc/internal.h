@@ -144,6 +144,10 @@ struct Item {
   int kind = IT_DENSE;
   int a = -1, b = -1;  // qubits (IT_CZ, IT_DIAG2: the second qubit; IT_VAR: the variant bit)
   cd u[4];             // IT_DENSE: matrix; IT_DIAG1: u[0], u[3] diagonal
+  // IT_DENSE from a U3 gate: the angles (theta, phi, lambda), the matrix is
+  // built where the item is applied (u3_matrix), on the thread compiling it
+  bool u3 = false;
+  double ang[3] = {0.0, 0.0, 0.0};
   int slot = -1;       // IT_VAR: variant bit number (b = n_state + slot)
   bool var_sign = false;  // IT_VAR: factor is Z^b (a sign term)
   cd d[2][2];             // IT_VAR: factor d[b][x] for variant bit b, index bit x of a;

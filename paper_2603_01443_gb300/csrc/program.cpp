@@ -32,6 +32,16 @@ namespace {
 
 inline bool is_zero(cd z) { return z.real() == 0.0 && z.imag() == 0.0; }
 
+// U3(theta, phi, lambda) = [[cos t/2, -e^{i lambda} sin t/2],
+//                            [e^{i phi} sin t/2, e^{i (phi + lambda)} cos t/2]]
+void u3_matrix(const double* ang, cd* u) {
+  const double c = std::cos(0.5 * ang[0]), s = std::sin(0.5 * ang[0]);
+  u[0] = c;
+  u[1] = -std::polar(1.0, ang[2]) * s;
+  u[2] = std::polar(1.0, ang[1]) * s;
+  u[3] = std::polar(1.0, ang[1] + ang[2]) * c;
+}
+
 void mat_h(cd* u) {
   const double r = 1.0 / std::sqrt(2.0);
   u[0] = r; u[1] = r; u[2] = r; u[3] = -r;
@@ -183,13 +193,12 @@ cc_status gate_items(const cc_gate& g, int qoff, std::vector<Item>& out) {
   const int a = g.q0 - qoff;
   switch (g.kind) {
     case CC_GATE_U3: {
-      const double c = std::cos(0.5 * g.theta), s = std::sin(0.5 * g.theta);
       it.kind = IT_DENSE;
       it.a = a;
-      it.u[0] = c;
-      it.u[1] = -std::polar(1.0, g.lambda) * s;
-      it.u[2] = std::polar(1.0, g.phi) * s;
-      it.u[3] = std::polar(1.0, g.phi + g.lambda) * c;
+      it.u3 = true;
+      it.ang[0] = g.theta;
+      it.ang[1] = g.phi;
+      it.ang[2] = g.lambda;
       out.push_back(it);
       return CC_OK;
     }
@@ -727,14 +736,21 @@ struct PassBuilder {
   void add(const Item& it) {
     switch (it.kind) {
       case IT_DENSE:
-      case IT_DIAG1:
+      case IT_DIAG1: {
+        cd m[4];
+        const cd* u = it.u;
+        if (it.u3) {
+          u3_matrix(it.ang, m);
+          u = m;
+        }
         if (!pend_has[it.a]) {
           pend_has[it.a] = true;
-          std::memcpy(pend_u[it.a], it.u, sizeof(it.u));
+          std::memcpy(pend_u[it.a], u, sizeof(it.u));
         } else {
-          mat_lmul(it.u, pend_u[it.a]);
+          mat_lmul(u, pend_u[it.a]);
         }
         return;
+      }
       case IT_CZ:
         flush(it.a);
         flush(it.b);
