@@ -252,3 +252,16 @@ def test_plans_leave_no_compile_threads(L):
         words, _ = api.plan_program_image(good, 16, [2] * 8, seg)
         assert len(words) > 0
     assert len(os.listdir("/proc/self/task")) == before
+
+
+def test_segment_programs_do_not_depend_on_thread_timing(L):
+    # segments compile on concurrent threads: repeated plans of the same
+    # circuit give byte-identical images for every segment
+    segs = [4, 5, 4, 5]
+    g = w.brickwork_cut(18, 10, 11, segs, [2, 3, 2])
+    first = [api.plan_program_image(g, 18, segs, s) for s in range(4)]
+    for _ in range(10):
+        for s in range(4):
+            words, reals = api.plan_program_image(g, 18, segs, s)
+            assert words.tobytes() == first[s][0].tobytes()
+            assert reals.tobytes() == first[s][1].tobytes()
