@@ -175,6 +175,9 @@ typedef struct {
  * the uncut program) these gates run as X/Y/Z-basis changes around diagonal
  * ZZ phases.
  * The plan's tables are uploaded to the current device (synchronously).
+ * Segments 2..n_seg compile on threads the call starts and joins before it
+ * returns (a segment whose thread cannot be started compiles on the calling
+ * thread); the programs do not depend on the threads' timing.
  * Errors: CC_EINVAL (NULL, bad enum, bad qubit, sizes not summing to q),
  * CC_ERANGE (q, n_seg or c_total too large, a segment too large to simulate),
  * CC_EUNSUPPORTED (for n_seg >= 3, a cut between non-adjacent segments),
