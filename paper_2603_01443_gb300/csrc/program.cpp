@@ -443,6 +443,8 @@ struct PassBuilder {
   bool overflow = false;  // an op with more than 65535 terms of one kind
   int js[64];             // flush_all's open matrices and their splits
   EulerSplit es[64];
+  std::vector<std::pair<int, int>> folded_buf;  // emit's working lists, kept between ops
+  std::vector<DTerm> signs_buf;
 
   PassBuilder(HostProgram& h, int nq_, const std::vector<int>& tile_bits) : hp(h), nq(nq_) {
     const int k = (int)tile_bits.size();
@@ -537,8 +539,11 @@ struct PassBuilder {
     // every thread: when the op gets a phase block it joins the block's
     // entries instead of flipping amplitudes.
     uint64_t adj = attach ? pend_adj : 0;
-    std::vector<std::pair<int, int>> folded;  // register indices of folded signs
-    std::vector<DTerm> signs;
+    // register indices of folded signs, and the signs left as terms
+    std::vector<std::pair<int, int>>& folded = folded_buf;
+    std::vector<DTerm>& signs = signs_buf;
+    folded.clear();
+    signs.clear();
     if (attach) {
       const bool block = will_attach_block(type == OP_DIAG);
       for (uint64_t r = adj; block && r; r &= r - 1) {
@@ -658,8 +663,8 @@ struct PassBuilder {
     DTerm b{};
     b.kind = TERM_PBLOCK;
     b.p0 = (uint8_t)(K != cd(1.0) ? 1 : 0);
-    b.tab = add_table(T);
-    for (int q4 = 1; q4 < 8; ++q4) add_table(T + 4 * q4);  // consecutive: entries 4..31
+    b.tab = (int)(hp.tabs.size() / 4);  // the 32 entries as 8 consecutive tables
+    hp.tabs.insert(hp.tabs.end(), T, T + 32);
     hp.terms.push_back(b);
     for (auto& d : fix) hp.terms.push_back(d);
   }
